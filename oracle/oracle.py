@@ -1,0 +1,176 @@
+"""ctypes marshalling for the FP64 oracle (``pvg_oracle.c``).
+
+Test infrastructure only: see the package docstring.  Inputs are the scene
+and camera dicts of ``paper_2311_18561_gb300.synth`` (any float type); they
+are converted to float64 here and every output is float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pvg_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libpvg_oracle.so")
+
+# Options (3DGS conventions the paper inherits): EWA dilation h [px^2],
+# alpha cap, alpha gate, transmittance stop, frustum clamp factor.
+DEFAULT_OPTS = dict(h=0.3, alpha_cap=0.99, alpha_min=1.0 / 255.0, t_stop=1e-4, fov_clamp=1.3)
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        P = C.c_void_p
+        lib.pvgo_time_eval.argtypes = [C.c_int64] + [P] * 6 + [C.c_double, P, P]
+        lib.pvgo_sh_basis.argtypes = [C.c_int, C.c_int64, P, P, P]
+        lib.pvgo_preprocess.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 9
+        lib.pvgo_render.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + [P] * 6
+        lib.pvgo_render_bwd.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 3 + [P] * 10
+        lib.pvgo_num_threads.argtypes = []
+        for f in (lib.pvgo_time_eval, lib.pvgo_sh_basis, lib.pvgo_preprocess, lib.pvgo_render,
+                  lib.pvgo_render_bwd, lib.pvgo_num_threads):
+            f.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    return int(load().pvgo_num_threads())
+
+
+def cam_array(cam) -> np.ndarray:
+    """viewmat[12], fx, fy, cx, cy, width, height, t, z_near, bg[3]."""
+    vm = np.asarray(cam["viewmat"], np.float64).reshape(12)
+    rest = [cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"],
+            cam["t"], cam["z_near"]]
+    return np.concatenate([vm, np.asarray(rest, np.float64), np.asarray(cam["bg"], np.float64).reshape(3)])
+
+
+def opt_array(opts=None) -> np.ndarray:
+    o = dict(DEFAULT_OPTS)
+    if opts:
+        o.update(opts)
+    return np.asarray([o["h"], o["alpha_cap"], o["alpha_min"], o["t_stop"], o["fov_clamp"]], np.float64)
+
+
+def _scene_args(scene):
+    k = scene["sh"].shape[1]
+    deg = int(round(np.sqrt(k))) - 1
+    arrs = [_d(scene[name]) for name in ("mu", "vel", "tau", "beta", "period", "scale", "quat",
+                                         "opacity", "sh")]
+    return int(scene["mu"].shape[0]), deg, arrs
+
+
+def time_eval(scene, t):
+    """Eq. 6 and Eq. 7: (mu~(t) [N,3], o~(t) [N])."""
+    n = int(np.asarray(scene["mu"]).shape[0])
+    arrs = [_d(scene[k]) for k in ("mu", "vel", "tau", "beta", "period", "opacity")]
+    mut = np.zeros((n, 3))
+    ot = np.zeros(n)
+    load().pvgo_time_eval(n, *[_p(a) for a in arrs], float(t), _p(mut), _p(ot))
+    return mut, ot
+
+
+def sh_basis(degree, dirs):
+    """Real SH basis values [n, K] and polynomial gradients [n, K, 3]."""
+    dirs = _d(dirs).reshape(-1, 3)
+    k = (degree + 1) ** 2
+    Y = np.zeros((dirs.shape[0], k))
+    dY = np.zeros((dirs.shape[0], k, 3))
+    rc = load().pvgo_sh_basis(int(degree), dirs.shape[0], _p(dirs), _p(Y), _p(dY))
+    if rc != 0:
+        raise ValueError("bad SH degree")
+    return Y, dY
+
+
+def preprocess(scene, cam, opts=None):
+    """Steps 1-4 per Gaussian: dict of valid, mut, ot, pcam, uv, cov2, conic,
+    rgb, box (rx, ry)."""
+    n, deg, arrs = _scene_args(scene)
+    out = dict(valid=np.zeros(n, np.int32), mut=np.zeros((n, 3)), ot=np.zeros(n),
+               pcam=np.zeros((n, 3)), uv=np.zeros((n, 2)), cov2=np.zeros((n, 3)),
+               conic=np.zeros((n, 3)), rgb=np.zeros((n, 3)), box=np.zeros((n, 2)))
+    ca, oa = cam_array(cam), opt_array(opts)
+    rc = load().pvgo_preprocess(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa),
+                                *[_p(out[k]) for k in ("valid", "mut", "ot", "pcam", "uv", "cov2",
+                                                       "conic", "rgb", "box")])
+    if rc != 0:
+        raise ValueError("oracle preprocess rejected its inputs")
+    return out
+
+
+def render(scene, cam, opts=None, mode="brute", pixels=None):
+    """Steps 5/6.  mode 'brute' or 'culled'.  pixels: None for the full
+    image (outputs shaped [H, W, ...]) or an int array [P, 2] of (px, py)
+    (outputs shaped [P, ...]).  Returns dict rgb, depth, alpha, T, nblend,
+    flag."""
+    n, deg, arrs = _scene_args(scene)
+    W, H = int(cam["width"]), int(cam["height"])
+    if pixels is None:
+        P = W * H
+        pix = None
+    else:
+        pix = np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+        P = pix.shape[0]
+    out = dict(rgb=np.zeros((P, 3)), depth=np.zeros(P), alpha=np.zeros(P), T=np.zeros(P),
+               nblend=np.zeros(P, np.int32), flag=np.zeros(P, np.int32))
+    ca, oa = cam_array(cam), opt_array(opts)
+    m = {"brute": 0, "culled": 1}[mode]
+    rc = load().pvgo_render(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, P, _p(pix),
+                            *[_p(out[k]) for k in ("rgb", "depth", "alpha", "T", "nblend", "flag")])
+    if rc != 0:
+        raise ValueError("oracle render rejected its inputs")
+    if pixels is None:
+        out = {k: v.reshape((H, W) + v.shape[1:]) for k, v in out.items()}
+    return out
+
+
+GRAD_NAMES = ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh")
+
+
+def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=False):
+    """Gradients of sum(dL_rgb*rgb) + sum(dL_depth*depth) + sum(dL_alpha*alpha)
+    (full image, brute force; dL_rgb [H,W,3], others [H,W]) w.r.t. every
+    parameter, as a dict keyed like the scene."""
+    n, deg, arrs = _scene_args(scene)
+    k = (deg + 1) ** 2
+    g = dict(mu=np.zeros((n, 3)), vel=np.zeros((n, 3)), tau=np.zeros(n), beta=np.zeros(n),
+             period=np.zeros(n), scale=np.zeros((n, 3)), quat=np.zeros((n, 4)), opacity=np.zeros(n),
+             sh=np.zeros((n, k, 3)))
+    g2d = np.zeros((n, 10))
+    ca, oa = cam_array(cam), opt_array(opts)
+    gr, gd, ga = _d(dL_rgb), _d(dL_depth), _d(dL_alpha)
+    rc = load().pvgo_render_bwd(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), _p(gr), _p(gd), _p(ga),
+                                *[_p(g[name]) for name in GRAD_NAMES], _p(g2d))
+    if rc != 0:
+        raise ValueError("oracle backward rejected its inputs")
+    if return_g2d:
+        return g, g2d
+    return g

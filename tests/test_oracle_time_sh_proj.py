@@ -1,0 +1,271 @@
+"""Pins of the oracle's per-Gaussian steps against facts the paper and the
+mathematics fix (no GPU).
+
+* Eq. 6 / Eq. 7 (Sec. 3.2): mu~(tau) = mu, periodicity in l, the amplitude
+  bound l|v|/(2 pi), the mean over whole periods (E[mu~] = mu), the velocity
+  at the life peak (v = d mu~/dt at t = tau), o~(tau) = o, the constant
+  (l -> 0) and linear (l -> inf) limits of the dynamics ablation (Sec. 4.4,
+  Tab. "ablation on cycle length").
+* Colour basis: orthonormal on the sphere, equal to scipy's complex SH
+  converted to the real basis, and gradients matching finite differences.
+* EWA (Sec. 3.1, Eq. 2): for a small Gaussian the projected covariance is
+  J_num Sigma J_num^T with J_num the numerical Jacobian of the exact pinhole
+  map and Sigma built by scipy from the quaternion; isotropic closed form on
+  the optical axis; the projected mean back-projects onto mu~.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_18561_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_settings.json")
+
+
+def _scene(n=64, seed=3):
+    return synth.make_plain_scene(seed=seed, n=n)
+
+
+# --------------------------------------------------------------------------
+# Eq. 6 / Eq. 7
+# --------------------------------------------------------------------------
+
+def test_mean_at_life_peak_is_mu():
+    sc = _scene()
+    for k in range(5):
+        t = float(sc["tau"][k])
+        s1 = {key: v.copy() for key, v in sc.items()}
+        s1["tau"][:] = t  # every point peaks at t
+        mut, ot = oracle.time_eval(s1, t)
+        np.testing.assert_array_equal(mut, sc["mu"].astype(np.float64))
+        np.testing.assert_array_equal(ot, sc["opacity"].astype(np.float64))
+
+
+def test_periodic_in_cycle_length():
+    sc = _scene()
+    l = json.load(open(GOLDEN))["cycle_length_l"]["value"]
+    sc["period"] = np.full(sc["period"].shape, l)  # float64, so t + l is exact
+    a, _ = oracle.time_eval(sc, 0.3)
+    b, _ = oracle.time_eval(sc, 0.3 + l)
+    c, _ = oracle.time_eval(sc, 0.3 + 5 * l)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+    np.testing.assert_allclose(a, c, atol=1e-12)
+
+
+def test_period_spans_ten_frames_at_paper_settings():
+    # l = 0.2 and a frame spacing of 0.02: a point returns to the same place
+    # every 10 frames and is back at mu after 5 frames (half a period).
+    g = json.load(open(GOLDEN))
+    l, df = g["cycle_length_l"]["value"], g["frame_spacing"]["value"]
+    sc = _scene()
+    sc["period"] = np.full(sc["period"].shape, l)
+    sc["tau"][:] = 0.0
+    m0, _ = oracle.time_eval(sc, 0.0)
+    m5, _ = oracle.time_eval(sc, 5 * df)
+    m10, _ = oracle.time_eval(sc, 10 * df)
+    np.testing.assert_allclose(m5, sc["mu"], atol=1e-7)
+    np.testing.assert_allclose(m10, m0, atol=1e-12)
+
+
+def test_amplitude_bound():
+    sc = _scene(n=400)
+    bound = sc["period"].astype(np.float64) * np.linalg.norm(sc["vel"].astype(np.float64), axis=1) / (2 * math.pi)
+    worst = np.zeros(400)
+    for t in np.linspace(-3, 3, 101):
+        mut, _ = oracle.time_eval(sc, t)
+        worst = np.maximum(worst, np.linalg.norm(mut - sc["mu"], axis=1))
+    assert np.all(worst <= bound * (1 + 1e-12))
+    assert np.all(worst >= 0.95 * bound)  # the bound is reached (|sin| = 1)
+
+
+def test_mean_over_a_period_is_mu():
+    sc = _scene()
+    sc["period"] = np.full(sc["period"].shape, 0.37)
+    ts = 0.1 + 0.37 * np.arange(64) / 64.0  # equispaced over one period
+    acc = np.zeros_like(sc["mu"], dtype=np.float64)
+    for t in ts:
+        acc += oracle.time_eval(sc, t)[0]
+    np.testing.assert_allclose(acc / len(ts), sc["mu"], atol=1e-12)
+
+
+def test_velocity_at_life_peak():
+    sc = _scene()
+    tau = 0.41
+    sc["tau"][:] = tau
+    h = 1e-6
+    a, _ = oracle.time_eval(sc, tau + h)
+    b, _ = oracle.time_eval(sc, tau - h)
+    np.testing.assert_allclose((a - b) / (2 * h), sc["vel"], rtol=1e-6, atol=1e-8)
+
+
+def test_opacity_decay():
+    sc = _scene()
+    tau = sc["tau"].astype(np.float64)
+    beta = sc["beta"].astype(np.float64)
+    for k in range(3):
+        t = float(tau[k] + beta[k])
+        _, ot = oracle.time_eval(sc, t)
+        assert ot[k] == pytest.approx(float(sc["opacity"][k]) * math.exp(-0.5), rel=1e-12)
+    big = {key: v.copy() for key, v in sc.items()}
+    big["beta"][:] = 1e8
+    _, ot = oracle.time_eval(big, 0.9)
+    np.testing.assert_allclose(ot, sc["opacity"], rtol=1e-12)
+
+
+def test_constant_and_linear_limits():
+    sc = _scene()
+    t = 0.77
+    small = {key: v.copy() for key, v in sc.items()}
+    small["period"][:] = 1e-9  # "constant" model: mu~ = mu
+    mut, _ = oracle.time_eval(small, t)
+    np.testing.assert_allclose(mut, sc["mu"], atol=1e-9)
+    large = {key: v.copy() for key, v in sc.items()}
+    large["period"][:] = 1e6  # "linear" model: mu~ = mu + v (t - tau)
+    mut, _ = oracle.time_eval(large, t)
+    lin = sc["mu"].astype(np.float64) + sc["vel"].astype(np.float64) * (t - sc["tau"].astype(np.float64))[:, None]
+    np.testing.assert_allclose(mut, lin, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# colour basis
+# --------------------------------------------------------------------------
+
+def _sphere_quadrature(n_theta=24, n_phi=48):
+    x, w = np.polynomial.legendre.leggauss(n_theta)  # x = cos(theta)
+    phi = 2 * np.pi * np.arange(n_phi) / n_phi
+    ct = np.repeat(x, n_phi)
+    st = np.sqrt(1 - ct ** 2)
+    ph = np.tile(phi, n_theta)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=1)
+    weights = np.repeat(w, n_phi) * (2 * np.pi / n_phi)
+    return dirs, weights
+
+
+def test_sh_orthonormal():
+    dirs, w = _sphere_quadrature()
+    Y, _ = oracle.sh_basis(3, dirs)
+    gram = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
+
+
+def test_sh_matches_scipy_real_basis():
+    special = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(0)
+    d = rng.normal(size=(50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta = np.arccos(d[:, 2])
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    Y, _ = oracle.sh_basis(3, d)
+    for l in range(4):
+        for m in range(-l, l + 1):
+            ylm = special.sph_harm_y(l, abs(m), theta, phi)  # Condon-Shortley phase included
+            if m > 0:
+                ref = math.sqrt(2) * ylm.real
+            elif m < 0:
+                ref = math.sqrt(2) * ylm.imag
+            else:
+                ref = ylm.real
+            np.testing.assert_allclose(Y[:, l * l + l + m], ref, atol=1e-12, err_msg=f"l={l} m={m}")
+
+
+def test_sh_gradients_fd():
+    rng = np.random.default_rng(1)
+    p = rng.normal(size=(20, 3))
+    _, dY = oracle.sh_basis(3, p)
+    h = 1e-6
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        a, _ = oracle.sh_basis(3, p + e)
+        b, _ = oracle.sh_basis(3, p - e)
+        np.testing.assert_allclose((a - b) / (2 * h), dY[:, :, c], atol=1e-7)
+
+
+# --------------------------------------------------------------------------
+# projection / EWA
+# --------------------------------------------------------------------------
+
+def _pinhole(cam, X):
+    V = np.asarray(cam["viewmat"], np.float64)
+    P = X @ V[:, :3].T + V[:, 3]
+    return np.stack([cam["fx"] * P[:, 0] / P[:, 2] + cam["cx"], cam["fy"] * P[:, 1] / P[:, 2] + cam["cy"]], axis=1)
+
+
+def _single(mu, scale, quat, opacity=0.8, rgb=(0.5, 0.5, 0.5)):
+    y00 = 0.5 / math.sqrt(math.pi)
+    return dict(mu=np.asarray([mu], np.float64), vel=np.zeros((1, 3)), tau=np.zeros(1) + 0.5,
+                beta=np.ones(1), period=np.ones(1), scale=np.asarray([scale], np.float64),
+                quat=np.asarray([quat], np.float64), opacity=np.asarray([opacity], np.float64),
+                sh=((np.asarray(rgb, np.float64) - 0.5) / y00).reshape(1, 1, 3))
+
+
+def test_ewa_matches_numerical_jacobian():
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(2)
+    cam = synth.plain_camera()
+    for _ in range(20):
+        mu = rng.uniform(-0.8, 0.8, 3)
+        q = rng.normal(size=4)  # (w, x, y, z)
+        s = np.exp(rng.normal(-3, 0.5, 3))
+        sc = _single(mu, s, q)
+        pp = oracle.preprocess(sc, cam, opts=dict(h=0.0))
+        assert pp["valid"][0] == 1
+        R = Rot.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy: scalar last
+        Sigma = R @ np.diag(s ** 2) @ R.T
+        h = 1e-6
+        J = np.zeros((2, 3))
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = h
+            J[:, c] = (_pinhole(cam, (mu + e)[None]) - _pinhole(cam, (mu - e)[None]))[0] / (2 * h)
+        ref = J @ Sigma @ J.T
+        A, B, Cc = pp["cov2"][0]
+        np.testing.assert_allclose([A, B, Cc], [ref[0, 0], ref[0, 1], ref[1, 1]], rtol=1e-6,
+                                   atol=1e-9 * abs(ref).max())
+        np.testing.assert_allclose(pp["uv"][0], _pinhole(cam, mu[None])[0], rtol=1e-12)
+        # conic is the inverse of cov2
+        a, b, c = pp["conic"][0]
+        np.testing.assert_allclose(np.array([[a, b], [b, c]]) @ np.array([[A, B], [B, Cc]]), np.eye(2),
+                                   atol=1e-9)
+
+
+def test_ewa_isotropic_on_axis_closed_form():
+    cam = synth.plain_camera()
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        sigma = float(np.exp(rng.normal(-3, 0.3)))
+        q = rng.normal(size=4)
+        zc = float(rng.uniform(2.5, 5.5))
+        mu = np.array([0.0, 0.0, zc - 4.0])  # the plain camera sits at z = -4 on the axis
+        for h in (0.0, 0.3):
+            pp = oracle.preprocess(_single(mu, [sigma] * 3, q), cam, opts=dict(h=h))
+            expect = (cam["fx"] * sigma / zc) ** 2 + h
+            np.testing.assert_allclose(pp["cov2"][0], [expect, 0.0, expect], rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(pp["uv"][0], [cam["cx"], cam["cy"]], atol=1e-12)
+            assert pp["pcam"][0, 2] == pytest.approx(zc, rel=1e-12)
+
+
+def test_projected_mean_back_projects_to_mu():
+    cam = synth.plain_camera()
+    sc = synth.make_plain_scene(seed=5, n=200)
+    pp = oracle.preprocess(sc, cam)
+    V = np.asarray(cam["viewmat"], np.float64)
+    R, t = V[:, :3], V[:, 3]
+    ok = pp["valid"] == 1
+    u, v = pp["uv"][ok, 0], pp["uv"][ok, 1]
+    z = pp["pcam"][ok, 2]
+    Pc = np.stack([(u - cam["cx"]) / cam["fx"] * z, (v - cam["cy"]) / cam["fy"] * z, z], axis=1)
+    X = (Pc - t) @ R  # R^T (P - t)
+    np.testing.assert_allclose(X, pp["mut"][ok], atol=1e-10)
+
+
+def test_near_plane_and_opacity_culls():
+    cam = synth.plain_camera()
+    behind = _single([0.0, 0.0, -4.1], [0.05] * 3, [1, 0, 0, 0])
+    assert oracle.preprocess(behind, cam)["valid"][0] == 0
+    faint = _single([0.0, 0.0, 0.0], [0.05] * 3, [1, 0, 0, 0], opacity=0.5 / 255)
+    assert oracle.preprocess(faint, cam)["valid"][0] == 0
