@@ -1,0 +1,215 @@
+/*
+ * pvg.h -- C ABI of the GB300-native PVG rasterizer.
+ *
+ * The library renders a set of Periodic Vibration Gaussians (PVG, arXiv
+ * 2311.18561) seen by one or more pinhole cameras at given times into RGB,
+ * depth and opacity images, and computes the adjoint of that map.  Every
+ * step runs in CUDA kernels written for sm_103a; this header is the only
+ * way in.  All signatures use plain pointers and sizes.
+ *
+ * Method (the passage each part follows):
+ *   - time evaluation of every point (Sec. 3.2, Eq. 6 and Eq. 7):
+ *       mu~(t) = mu + l/(2 pi) sin(2 pi (t - tau)/l) v,
+ *       o~(t)  = o exp(-(t - tau)^2 / (2 beta^2));
+ *   - the state H(t) = {mu~(t), q, s, o~(t), c} is rendered like a static
+ *     3D Gaussian scene (Sec. 3.2, Eq. 8): EWA projection
+ *     Sigma' = J W Sigma W^T J^T (Sec. 3.1, Eq. 2) with
+ *     Sigma = R(q) diag(s)^2 R(q)^T, sorting by camera depth and per-tile
+ *     front-to-back alpha blending C = sum_i T_i alpha_i c_i (Sec. 3.1,
+ *     Eq. 3), plus the depth and opacity channels of "flexible rendering"
+ *     (Sec. 3.1) and O = sum T_i alpha_i (Sec. 3.4, sky refinement);
+ *   - the render function is differentiable (Sec. 3.1, Eq. 4): the backward
+ *     entry point returns gradients for mu, v, tau, beta, l, s, q, o and
+ *     the SH colour coefficients.
+ *
+ * Conventions the paper leaves open (3DGS conventions it inherits), fixed
+ * here: alpha = min(0.99, o~ G_2D); a Gaussian with alpha < 1/255 at a
+ * pixel is skipped; blending stops before a Gaussian that would leave the
+ * transmittance below 1e-4; EWA dilation h = 0.3 px^2 (configurable);
+ * x/z and y/z clamped to 1.3 x the half field of view inside J; pixel
+ * (px, py) is sampled at (px + 0.5, py + 0.5); camera axes are OpenCV
+ * (+x right, +y down, +z forward); depth ties are broken by Gaussian index;
+ * colour = max(0, sum_k sh_k Y_k(d) + 0.5) with real spherical harmonics
+ * (orthonormal, Condon-Shortley phase, index k = l^2 + l + m) at the unit
+ * direction d from the camera centre to mu~(t).
+ *
+ * Memory: every pointer inside pvg_scene_t, pvg_image_t, pvg_image_grad_t
+ * and pvg_scene_grad_t is a DEVICE pointer owned by the caller.  Camera
+ * arrays are HOST memory.  The library owns its workspace (pvg_ctx_t) and
+ * the saved state of a forward pass (pvg_frame_t).  All calls are
+ * asynchronous on the given stream unless stated otherwise; a NULL stream
+ * is the legacy default stream.
+ *
+ * Errors: every call returns a pvg_status_t; no exception crosses the ABI.
+ * On an error nothing has been enqueued unless the status is PVG_ERR_CUDA
+ * (a CUDA call failed; the message is in pvg_last_error()).
+ */
+#ifndef PVG_H
+#define PVG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PVG_OK = 0,
+    PVG_ERR_INVALID = 1,   /* bad argument (NULL pointer, size, degree...) */
+    PVG_ERR_OOM = 2,       /* a device allocation failed */
+    PVG_ERR_BUSY = 3,      /* serving: request not admitted now, retry later */
+    PVG_ERR_TIMEOUT = 4,   /* a bounded wait gave up */
+    PVG_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+    PVG_ERR_OVERFLOW = 6,  /* more tile/Gaussian pairs than the fixed capacity */
+    PVG_ERR_NOT_FOUND = 7  /* unknown scene or request id */
+} pvg_status_t;
+
+/* Human-readable name of a status. */
+const char *pvg_status_str(pvg_status_t s);
+/* Last CUDA error message recorded on this thread ("" if none). */
+const char *pvg_last_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int pvg_version(void);
+
+/* ------------------------------------------------------------------ */
+/* data                                                                */
+/* ------------------------------------------------------------------ */
+
+/* A PVG scene: N points, structure of arrays, float32, device memory,
+ * row-major.  The learnable per-point set of Sec. 3.2:
+ *   mu      [N,3]  mean position
+ *   vel     [N,3]  v, vibration direction / velocity at the life peak
+ *   tau     [N]    life peak
+ *   beta    [N]    lifespan (> 0)
+ *   period  [N]    cycle length l (> 0); the paper fixes l = 0.2
+ *   scale   [N,3]  s (> 0, linear, not log)
+ *   quat    [N,4]  q = (w, x, y, z), need not be normalised (not all zero)
+ *   opacity [N]    o in [0, 1] (physical, not a logit)
+ *   sh      [N,(D+1)^2,3] colour coefficients, D = sh_degree in 0..3
+ * Every array must be 4-byte aligned; mu, vel, scale, quat and sh may be
+ * any alignment of float.  N = 0 is allowed (renders the background). */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t reserved;
+    const float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opacity, *sh;
+} pvg_scene_t;
+
+/* A pinhole camera at time t (host memory). */
+typedef struct {
+    float viewmat[12];  /* world->camera, row-major 3x4 [R | t], OpenCV axes */
+    float fx, fy, cx, cy;
+    int32_t width, height; /* 1..16384 each */
+    float t;            /* render time (Sec. 3.2: normalised timestamps) */
+    float z_near;       /* points with camera depth <= z_near are culled */
+    float bg[3];        /* constant background colour (C += T_final bg) */
+    float reserved;
+} pvg_camera_t;
+
+/* Output images of one view (device memory, caller-owned):
+ *   rgb   [3,H,W] planar, required
+ *   depth [H,W]  sum_i T_i alpha_i z_i (not normalised; divide by alpha
+ *                for the normalised depth of Sec. 3.1), may be NULL
+ *   alpha [H,W]  O = sum_i T_i alpha_i, may be NULL */
+typedef struct {
+    float *rgb, *depth, *alpha;
+} pvg_image_t;
+
+/* dL/d(output) of one view, same layouts as pvg_image_t; NULL = zero. */
+typedef struct {
+    const float *rgb, *depth, *alpha;
+} pvg_image_grad_t;
+
+/* Parameter gradients, same layouts as pvg_scene_t (device, caller-owned).
+ * pvg_render_bwd zeroes them and then writes dL/dparam summed over all
+ * views.  A NULL array is neither zeroed nor written. */
+typedef struct {
+    float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opacity, *sh;
+} pvg_scene_grad_t;
+
+/* ------------------------------------------------------------------ */
+/* context and saved state                                             */
+/* ------------------------------------------------------------------ */
+
+typedef struct pvg_ctx pvg_ctx_t;
+typedef struct pvg_frame pvg_frame_t;
+
+typedef struct {
+    int32_t tile_w, tile_h; /* 16x16 by default; supported: 8x8, 16x8, 16x16, 32x8, 32x16 */
+    int32_t sync_sizes;     /* 1 (default): pvg_render_fwd reads the pair count
+                             * back to the host once per call and grows the
+                             * workspace; 0: never synchronises, uses the
+                             * capacities below and fails with
+                             * PVG_ERR_OVERFLOW (reported by the next call or
+                             * pvg_frame_status) if they are exceeded */
+    int32_t reserved0;
+    int64_t pair_capacity;  /* pairs per frame when sync_sizes = 0 */
+    float dilation;         /* EWA low-pass h in px^2 (default 0.3) */
+    float fov_clamp;        /* J clamp factor (default 1.3) */
+    float reserved[6];
+} pvg_config_t;
+
+/* Fill *cfg with the defaults. */
+void pvg_config_default(pvg_config_t *cfg);
+
+/* Create a context on the CURRENT CUDA device.  cfg may be NULL
+ * (defaults).  The context owns scratch memory that grows on demand; it is
+ * used by one stream at a time (calls on one context must not overlap). */
+pvg_status_t pvg_create(pvg_ctx_t **ctx, const pvg_config_t *cfg);
+void pvg_destroy(pvg_ctx_t *ctx);
+/* Change tile shape / dilation / clamp of an existing context. */
+pvg_status_t pvg_set_config(pvg_ctx_t *ctx, const pvg_config_t *cfg);
+
+/* Saved state of one forward pass (depth-sorted visible Gaussians, their
+ * projected records, per-tile lists, per-pixel final transmittance and last
+ * blended position), needed by pvg_render_bwd.  A frame belongs to the
+ * device that was current at creation. */
+pvg_status_t pvg_frame_create(pvg_frame_t **frame);
+void pvg_frame_destroy(pvg_frame_t *frame);
+/* Counters of the last forward into `frame` (synchronises `frame`'s last
+ * stream): visible (view, Gaussian) pairs, tile/Gaussian pairs and the
+ * overflow status. */
+pvg_status_t pvg_frame_stats(pvg_frame_t *frame, int64_t *n_visible, int64_t *n_pairs,
+                             int32_t *overflowed);
+
+/* ------------------------------------------------------------------ */
+/* rendering                                                           */
+/* ------------------------------------------------------------------ */
+
+/* Render `scene` from `n_views` cameras (host array) into out[0..n_views)
+ * (host array of device image pointers).  If `frame` is non-NULL the state
+ * needed by pvg_render_bwd is kept in it (NULL: inference only).
+ * Returns PVG_ERR_INVALID for NULL/size errors, PVG_ERR_OOM if the
+ * workspace cannot grow. */
+pvg_status_t pvg_render_fwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_camera_t *cams,
+                            int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame, void *stream);
+
+/* Adjoint of the forward pass saved in `frame` (which must have been
+ * rendered from the same scene values and cameras): zeroes `grads` and
+ * writes dL/dparam for L = sum over views of <dL[v], image[v]>.
+ * dL is a host array of n_views device-gradient descriptors. */
+pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_camera_t *cams,
+                            int32_t n_views, pvg_frame_t *frame, const pvg_image_grad_t *dL,
+                            const pvg_scene_grad_t *grads, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* introspection (tests)                                               */
+/* ------------------------------------------------------------------ */
+
+/* Copy device-side intermediate results of the last forward into
+ * caller-owned DEVICE buffers (any may be NULL), for parity testing:
+ *   sorted_gid [n_visible]   (view * N + index) in (view-major via tiles, depth, index) order
+ *   depth_key  [n_visible]   float32 bits of the camera depth, same order
+ *   rect       [n_visible*4] tile rectangle (tx0, ty0, tx1, ty1), half-open, int32
+ *   records    [n_visible*12] u, v, conic a, b, c, o~, z, 0, r, g, b, 0 (float32)
+ *   pair_vals  [n_pairs]     position in the depth order, sorted by (tile, depth, index)
+ *   ranges     [total_tiles*2] [start, end) per tile, tiles of view 0 first
+ * Synchronises the frame's stream. */
+pvg_status_t pvg_frame_export(pvg_frame_t *frame, uint32_t *sorted_gid, uint32_t *depth_key,
+                              int32_t *rect, float *records, uint32_t *pair_vals, uint32_t *ranges);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PVG_H */

@@ -1,0 +1,545 @@
+// api.cu -- the C ABI of include/pvg.h: contexts, frames and the forward /
+// backward orchestration of the four stages.
+//
+// Forward pass on one stream (no host round trip except the optional pair
+// count read-back that sizes the pair buffers):
+//   a  k_project_count      items -> tile count, depth bits
+//      compact_visible      visible items in gid order -> (zbits, gid), M
+//   b  radix sort           by depth bits (4 passes of <= 8 bits)
+//   a  k_finalize           records, rects, counts in depth order
+//   b  scan + emit          (tile, m) pairs in depth order, K
+//      radix sort           by tile id (ceil(log2 tiles) bits)
+//      k_ranges             [start, end) per tile
+//   c  k_composite          images + per-pixel T and last position
+// Backward: k_composite_bwd (image-space gradients per record) and
+// k_preprocess_bwd (parameter gradients).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pvg.h"
+#include "pvg_internal.cuh"
+
+using namespace pvg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// grow to at least `bytes` (x1.25 headroom); contents are not kept
+pvg_status_t ensure(DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return PVG_OK;
+    release(b);
+    const size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return PVG_ERR_OOM;
+        }
+        b.bytes = bytes;
+        return PVG_OK;
+    }
+    b.bytes = want;
+    return PVG_OK;
+}
+
+template <class T>
+T *ptr(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+pvg_status_t cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return PVG_OK;
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return PVG_ERR_CUDA;
+}
+
+#define PVG_TRY(expr)                              \
+    do {                                           \
+        pvg_status_t _s = (expr);                  \
+        if (_s != PVG_OK) return _s;               \
+    } while (0)
+
+#define PVG_CUDA(expr) PVG_TRY(cuda_status((expr), #expr))
+
+}  // namespace
+
+struct pvg_frame {
+    int device = -1;
+    DevBuf counters;            // u32 [4]: M, K, overflow
+    DevBuf sgid, szkey;         // [NV]
+    DevBuf rec;                 // [NV * 3] float4
+    DevBuf rect, vis_cnt;       // [NV]
+    DevBuf pair_vals;           // [K]
+    DevBuf ranges;              // [tiles]
+    DevBuf pix_T, pix_last;     // [pixels]
+    DevBuf g2d;                 // [NV * 10]
+    std::vector<ViewDesc> views;
+    uint32_t n_items = 0, total_tiles = 0, total_pix = 0, pair_capacity = 0;
+    int tile_w = 0, tile_h = 0;
+    int64_t n = -1;
+    int sh_degree = -1;
+    float dilation = 0.f;
+    cudaStream_t stream = nullptr;
+    bool valid = false;
+    uint32_t *h_counters = nullptr;  // pinned
+};
+
+struct pvg_ctx {
+    int device = -1;
+    pvg_config_t cfg;
+    DevBuf views;
+    DevBuf item_cnt, item_zkey;  // [NV]
+    DevBuf alt_keys, alt_vals;   // [NV] depth sort ping-pong
+    DevBuf pair_keys, pair_keys2, pair_vals2;  // [K]
+    DevBuf temp;
+    uint32_t *h_pinned = nullptr;
+    pvg_frame *own_frame = nullptr;
+};
+
+// ------------------------------------------------------------------ misc
+
+extern "C" const char *pvg_status_str(pvg_status_t s) {
+    switch (s) {
+        case PVG_OK: return "PVG_OK";
+        case PVG_ERR_INVALID: return "PVG_ERR_INVALID";
+        case PVG_ERR_OOM: return "PVG_ERR_OOM";
+        case PVG_ERR_BUSY: return "PVG_ERR_BUSY";
+        case PVG_ERR_TIMEOUT: return "PVG_ERR_TIMEOUT";
+        case PVG_ERR_CUDA: return "PVG_ERR_CUDA";
+        case PVG_ERR_OVERFLOW: return "PVG_ERR_OVERFLOW";
+        case PVG_ERR_NOT_FOUND: return "PVG_ERR_NOT_FOUND";
+    }
+    return "PVG_ERR_UNKNOWN";
+}
+
+extern "C" const char *pvg_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int pvg_version(void) { return 100; }
+
+extern "C" void pvg_config_default(pvg_config_t *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->sync_sizes = 1;
+    cfg->pair_capacity = 1 << 24;
+    cfg->dilation = 0.3f;
+    cfg->fov_clamp = 1.3f;
+}
+
+static pvg_status_t check_config(const pvg_config_t *c) {
+    if (!composite_supported(c->tile_w, c->tile_h)) return PVG_ERR_INVALID;
+    if (!(c->dilation >= 0.f) || !(c->fov_clamp > 0.f)) return PVG_ERR_INVALID;
+    if (!c->sync_sizes && (c->pair_capacity <= 0 || c->pair_capacity > 0xfffffff0LL)) return PVG_ERR_INVALID;
+    return PVG_OK;
+}
+
+extern "C" pvg_status_t pvg_frame_create(pvg_frame_t **frame) {
+    if (!frame) return PVG_ERR_INVALID;
+    pvg_frame *f = new pvg_frame();
+    PVG_CUDA(cudaGetDevice(&f->device));
+    if (cudaMallocHost(&f->h_counters, 4 * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete f;
+        return PVG_ERR_OOM;
+    }
+    if (ensure(f->counters, 4 * sizeof(uint32_t)) != PVG_OK) {
+        cudaFreeHost(f->h_counters);
+        delete f;
+        return PVG_ERR_OOM;
+    }
+    *frame = f;
+    return PVG_OK;
+}
+
+extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
+    if (!f) return;
+    if (f->stream) cudaStreamSynchronize(f->stream);
+    for (DevBuf *b : {&f->counters, &f->sgid, &f->szkey, &f->rec, &f->rect, &f->vis_cnt, &f->pair_vals,
+                      &f->ranges, &f->pix_T, &f->pix_last, &f->g2d})
+        release(*b);
+    if (f->h_counters) cudaFreeHost(f->h_counters);
+    delete f;
+}
+
+extern "C" pvg_status_t pvg_create(pvg_ctx_t **ctx, const pvg_config_t *cfg) {
+    if (!ctx) return PVG_ERR_INVALID;
+    pvg_config_t c;
+    if (cfg) c = *cfg; else pvg_config_default(&c);
+    PVG_TRY(check_config(&c));
+    pvg_ctx *x = new pvg_ctx();
+    x->cfg = c;
+    if (cudaGetDevice(&x->device) != cudaSuccess || set_sh_constants() != cudaSuccess) {
+        g_last_error = cudaGetErrorString(cudaGetLastError());
+        delete x;
+        return PVG_ERR_CUDA;
+    }
+    if (cudaMallocHost(&x->h_pinned, 16) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return PVG_ERR_OOM;
+    }
+    if (ensure(x->temp, sort_temp_bytes(0)) != PVG_OK || pvg_frame_create(&x->own_frame) != PVG_OK) {
+        cudaFreeHost(x->h_pinned);
+        release(x->temp);
+        delete x;
+        return PVG_ERR_OOM;
+    }
+    *ctx = x;
+    return PVG_OK;
+}
+
+extern "C" void pvg_destroy(pvg_ctx_t *x) {
+    if (!x) return;
+    cudaDeviceSynchronize();
+    for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->alt_keys, &x->alt_vals, &x->pair_keys,
+                      &x->pair_keys2, &x->pair_vals2, &x->temp})
+        release(*b);
+    if (x->h_pinned) cudaFreeHost(x->h_pinned);
+    pvg_frame_destroy(x->own_frame);
+    delete x;
+}
+
+extern "C" pvg_status_t pvg_set_config(pvg_ctx_t *x, const pvg_config_t *cfg) {
+    if (!x || !cfg) return PVG_ERR_INVALID;
+    PVG_TRY(check_config(cfg));
+    x->cfg = *cfg;
+    return PVG_OK;
+}
+
+// ------------------------------------------------------------------ views
+
+static bool finite3x4(const float *m) {
+    for (int k = 0; k < 12; k++)
+        if (!std::isfinite(m[k])) return false;
+    return true;
+}
+
+static pvg_status_t validate_scene(const pvg_scene_t *sc) {
+    if (!sc || sc->n < 0 || sc->sh_degree < 0 || sc->sh_degree > 3) return PVG_ERR_INVALID;
+    if (sc->n > 0 && (!sc->mu || !sc->vel || !sc->tau || !sc->beta || !sc->period || !sc->scale || !sc->quat ||
+                      !sc->opacity || !sc->sh))
+        return PVG_ERR_INVALID;
+    return PVG_OK;
+}
+
+static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *sc, const pvg_camera_t *cams, int nv,
+                                std::vector<ViewDesc> &out, uint32_t *n_items, uint32_t *total_tiles,
+                                uint32_t *total_pix) {
+    if (!cams || nv < 1 || nv > kMaxViewsPerCall) return PVG_ERR_INVALID;
+    const int TW = x->cfg.tile_w, TH = x->cfg.tile_h;
+    const uint64_t nitems = (uint64_t)sc->n * (uint64_t)nv;
+    if (nitems >= (1ull << 31)) return PVG_ERR_INVALID;
+    out.assign(nv, ViewDesc());
+    uint64_t tiles = 0, pix = 0;
+    for (int v = 0; v < nv; v++) {
+        const pvg_camera_t &c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return PVG_ERR_INVALID;
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.fx) || !std::isfinite(c.fy) ||
+            !std::isfinite(c.cx) || !std::isfinite(c.cy) || !std::isfinite(c.t) || !(c.z_near >= 0.f) ||
+            !std::isfinite(c.z_near) || !finite3x4(c.viewmat))
+            return PVG_ERR_INVALID;
+        ViewDesc &d = out[v];
+        for (int r = 0; r < 3; r++) {
+            for (int k = 0; k < 3; k++) d.R[3 * r + k] = c.viewmat[4 * r + k];
+            d.T[r] = c.viewmat[4 * r + 3];
+        }
+        for (int k = 0; k < 3; k++)
+            d.campos[k] = -(d.R[k] * d.T[0] + d.R[3 + k] * d.T[1] + d.R[6 + k] * d.T[2]);
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        d.t = c.t; d.znear = c.z_near;
+        d.bg[0] = c.bg[0]; d.bg[1] = c.bg[1]; d.bg[2] = c.bg[2];
+        d.limx = x->cfg.fov_clamp * 0.5f * (float)c.width / c.fx;
+        d.limy = x->cfg.fov_clamp * 0.5f * (float)c.height / c.fy;
+        d.W = c.width; d.H = c.height;
+        d.tiles_x = (c.width + TW - 1) / TW;
+        d.tiles_y = (c.height + TH - 1) / TH;
+        d.tile_base = (uint32_t)tiles;
+        d.pix_base = (uint32_t)pix;
+        d.item_base = (uint32_t)((uint64_t)v * (uint64_t)sc->n);
+        d.n = (uint32_t)sc->n;
+        d.sh_degree = sc->sh_degree;
+        d.mu = sc->mu; d.vel = sc->vel; d.tau = sc->tau; d.beta = sc->beta; d.period = sc->period;
+        d.scale = sc->scale; d.quat = sc->quat; d.opac = sc->opacity; d.sh = sc->sh;
+        tiles += (uint64_t)d.tiles_x * d.tiles_y;
+        pix += (uint64_t)c.width * c.height;
+    }
+    if (tiles >= (1ull << 31) || pix >= (1ull << 32)) return PVG_ERR_INVALID;
+    *n_items = (uint32_t)nitems;
+    *total_tiles = (uint32_t)tiles;
+    *total_pix = (uint32_t)pix;
+    return PVG_OK;
+}
+
+static int bits_for(uint32_t n) {
+    if (n <= 1) return 1;
+    int b = 0;
+    while ((1ull << b) < n) b++;
+    return b;
+}
+
+// ------------------------------------------------------------------ forward
+
+extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cams,
+                                       int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame,
+                                       void *stream_) {
+    if (!x || !out) return PVG_ERR_INVALID;
+    PVG_TRY(validate_scene(scene));
+    for (int v = 0; v < n_views; v++)
+        if (!out[v].rgb) return PVG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream_;
+    pvg_frame *f = frame ? frame : x->own_frame;
+    std::vector<ViewDesc> views;
+    uint32_t NV, tiles, pix;
+    PVG_TRY(build_views(x, scene, cams, n_views, views, &NV, &tiles, &pix));
+    for (int v = 0; v < n_views; v++) {
+        views[v].out_rgb = out[v].rgb;
+        views[v].out_depth = out[v].depth;
+        views[v].out_alpha = out[v].alpha;
+    }
+    // workspace
+    PVG_TRY(ensure(x->views, sizeof(ViewDesc) * n_views));
+    PVG_TRY(ensure(x->item_cnt, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(x->item_zkey, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(x->alt_keys, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(x->alt_vals, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(f->sgid, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(f->szkey, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(f->rec, sizeof(float4) * 3 * (size_t)NV));
+    PVG_TRY(ensure(f->rect, sizeof(uint2) * NV));
+    PVG_TRY(ensure(f->vis_cnt, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(f->ranges, sizeof(uint2) * tiles));
+    PVG_TRY(ensure(f->pix_T, sizeof(float) * pix));
+    PVG_TRY(ensure(f->pix_last, sizeof(uint32_t) * pix));
+    uint32_t pair_cap;
+    if (x->cfg.sync_sizes) {
+        pair_cap = (uint32_t)(f->pair_vals.bytes / sizeof(uint32_t));
+    } else {
+        pair_cap = (uint32_t)x->cfg.pair_capacity;
+        PVG_TRY(ensure(f->pair_vals, sizeof(uint32_t) * (size_t)pair_cap));
+        PVG_TRY(ensure(x->pair_keys, sizeof(uint32_t) * (size_t)pair_cap));
+        PVG_TRY(ensure(x->pair_keys2, sizeof(uint32_t) * (size_t)pair_cap));
+        PVG_TRY(ensure(x->pair_vals2, sizeof(uint32_t) * (size_t)pair_cap));
+    }
+    f->views = views;
+    f->n_items = NV;
+    f->total_tiles = tiles;
+    f->total_pix = pix;
+    f->tile_w = x->cfg.tile_w;
+    f->tile_h = x->cfg.tile_h;
+    f->n = scene->n;
+    f->sh_degree = scene->sh_degree;
+    f->dilation = x->cfg.dilation;
+    f->stream = s;
+    f->valid = false;
+
+    PVG_CUDA(cudaMemcpyAsync(x->views.p, views.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice, s));
+    PVG_CUDA(cudaMemsetAsync(f->counters.p, 0, 4 * sizeof(uint32_t), s));
+
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.views = ptr<ViewDesc>(x->views);
+    p.n_views = n_views;
+    p.tile_w = x->cfg.tile_w;
+    p.tile_h = x->cfg.tile_h;
+    p.dilation = x->cfg.dilation;
+    p.n_items = NV;
+    p.total_tiles = tiles;
+    p.counters = ptr<uint32_t>(f->counters);
+    p.item_cnt = ptr<uint32_t>(x->item_cnt);
+    p.item_zkey = ptr<uint32_t>(x->item_zkey);
+    p.sgid = ptr<uint32_t>(f->sgid);
+    p.szkey = ptr<uint32_t>(f->szkey);
+    p.rec = ptr<float4>(f->rec);
+    p.rect = ptr<uint2>(f->rect);
+    p.vis_cnt = ptr<uint32_t>(f->vis_cnt);
+    p.ranges = ptr<uint2>(f->ranges);
+    p.pix_T = ptr<float>(f->pix_T);
+    p.pix_last = ptr<uint32_t>(f->pix_last);
+
+    if (NV > 0) {
+        // (a) project + count, (b) depth sort of the visible items
+        launch_project_count(p, s);
+        compact_visible(p, p.szkey, p.sgid, x->temp.p, s);
+        bool in_alt = false;
+        radix_sort_pairs(p.szkey, p.sgid, ptr<uint32_t>(x->alt_keys), ptr<uint32_t>(x->alt_vals), &p.counters[0], NV,
+                         0, 31, x->temp.p, s, &in_alt);
+        if (in_alt) {  // 31 bits = 4 passes: never taken, kept for safety
+            PVG_CUDA(cudaMemcpyAsync(p.szkey, x->alt_keys.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
+            PVG_CUDA(cudaMemcpyAsync(p.sgid, x->alt_vals.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
+        }
+        // (a) records in depth order, (b) pair count
+        launch_finalize(p, s);
+        p.pair_capacity = x->cfg.sync_sizes ? 0xffffffffu : pair_cap;
+        scan_count_pairs(p, x->temp.p, s);
+        if (x->cfg.sync_sizes) {
+            PVG_CUDA(cudaMemcpyAsync(x->h_pinned, &p.counters[1], sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            PVG_CUDA(cudaStreamSynchronize(s));
+            const uint32_t K = x->h_pinned[0];
+            PVG_TRY(ensure(f->pair_vals, sizeof(uint32_t) * (size_t)K));
+            PVG_TRY(ensure(x->pair_keys, sizeof(uint32_t) * (size_t)K));
+            PVG_TRY(ensure(x->pair_keys2, sizeof(uint32_t) * (size_t)K));
+            PVG_TRY(ensure(x->pair_vals2, sizeof(uint32_t) * (size_t)K));
+            pair_cap = K;
+        }
+        p.pair_capacity = pair_cap;
+        // emission target so that an odd/even number of tile passes ends in f->pair_vals
+        const int tbits = bits_for(tiles);
+        const int tpasses = (tbits + 7) / 8;
+        uint32_t *E_keys = ptr<uint32_t>(x->pair_keys), *F_keys = ptr<uint32_t>(x->pair_keys2);
+        uint32_t *E_vals, *F_vals;
+        if (tpasses % 2 == 0) {
+            E_vals = ptr<uint32_t>(f->pair_vals);
+            F_vals = ptr<uint32_t>(x->pair_vals2);
+        } else {
+            E_vals = ptr<uint32_t>(x->pair_vals2);
+            F_vals = ptr<uint32_t>(f->pair_vals);
+        }
+        p.pair_keys = E_keys;
+        p.pair_vals = E_vals;
+        scan_emit_pairs(p, x->temp.p, s);
+        bool t_alt = false;
+        radix_sort_pairs(E_keys, E_vals, F_keys, F_vals, &p.counters[1], pair_cap, 0, tbits, x->temp.p, s, &t_alt);
+        p.pair_keys = t_alt ? F_keys : E_keys;
+        p.pair_vals = ptr<uint32_t>(f->pair_vals);
+        launch_ranges(p, s);
+    } else {
+        PVG_CUDA(cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * tiles, s));
+    }
+    f->pair_capacity = pair_cap;
+    p.pair_vals = ptr<uint32_t>(f->pair_vals);
+    launch_composite(p, s);
+    PVG_CUDA(cudaGetLastError());
+    f->valid = true;
+    return PVG_OK;
+}
+
+// ------------------------------------------------------------------ backward
+
+__global__ static void k_zero_g2d(float *g2d, const uint32_t *d_m) {
+    const size_t n = 10 * (size_t)*d_m;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        g2d[k] = 0.f;
+}
+
+extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cams,
+                                       int32_t n_views, pvg_frame_t *frame, const pvg_image_grad_t *dL,
+                                       const pvg_scene_grad_t *grads, void *stream_) {
+    if (!x || !dL || !grads) return PVG_ERR_INVALID;
+    PVG_TRY(validate_scene(scene));
+    pvg_frame *f = frame ? frame : x->own_frame;
+    if (!f->valid || f->n != scene->n || f->sh_degree != scene->sh_degree || (int)f->views.size() != n_views)
+        return PVG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream_;
+    std::vector<ViewDesc> views = f->views;
+    for (int v = 0; v < n_views; v++) {
+        if (!cams || cams[v].width != views[v].W || cams[v].height != views[v].H) return PVG_ERR_INVALID;
+        ViewDesc &d = views[v];
+        d.mu = scene->mu; d.vel = scene->vel; d.tau = scene->tau; d.beta = scene->beta; d.period = scene->period;
+        d.scale = scene->scale; d.quat = scene->quat; d.opac = scene->opacity; d.sh = scene->sh;
+        d.dl_rgb = dL[v].rgb; d.dl_depth = dL[v].depth; d.dl_alpha = dL[v].alpha;
+        d.g_mu = grads->mu; d.g_vel = grads->vel; d.g_tau = grads->tau; d.g_beta = grads->beta;
+        d.g_period = grads->period; d.g_scale = grads->scale; d.g_quat = grads->quat; d.g_opac = grads->opacity;
+        d.g_sh = grads->sh;
+    }
+    const size_t N = (size_t)scene->n, K = (size_t)(scene->sh_degree + 1) * (scene->sh_degree + 1);
+    struct { float *p; size_t n; } zero[] = {
+        {grads->mu, 3 * N}, {grads->vel, 3 * N}, {grads->tau, N}, {grads->beta, N}, {grads->period, N},
+        {grads->scale, 3 * N}, {grads->quat, 4 * N}, {grads->opacity, N}, {grads->sh, 3 * K * N}};
+    for (auto &z : zero)
+        if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
+    if (f->n_items == 0) return PVG_OK;
+    PVG_TRY(ensure(x->views, sizeof(ViewDesc) * n_views));
+    PVG_TRY(ensure(f->g2d, sizeof(float) * 10 * (size_t)f->n_items));
+    PVG_CUDA(cudaMemcpyAsync(x->views.p, views.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice, s));
+
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.views = ptr<ViewDesc>(x->views);
+    p.n_views = n_views;
+    p.tile_w = f->tile_w;
+    p.tile_h = f->tile_h;
+    p.dilation = f->dilation;
+    p.n_items = f->n_items;
+    p.total_tiles = f->total_tiles;
+    p.pair_capacity = f->pair_capacity;
+    p.counters = ptr<uint32_t>(f->counters);
+    p.sgid = ptr<uint32_t>(f->sgid);
+    p.szkey = ptr<uint32_t>(f->szkey);
+    p.rec = ptr<float4>(f->rec);
+    p.rect = ptr<uint2>(f->rect);
+    p.vis_cnt = ptr<uint32_t>(f->vis_cnt);
+    p.pair_vals = ptr<uint32_t>(f->pair_vals);
+    p.ranges = ptr<uint2>(f->ranges);
+    p.pix_T = ptr<float>(f->pix_T);
+    p.pix_last = ptr<uint32_t>(f->pix_last);
+    p.g2d = ptr<float>(f->g2d);
+    k_zero_g2d<<<152 * 4, 256, 0, s>>>(p.g2d, &p.counters[0]);
+    launch_composite_bwd(p, s);
+    launch_preprocess_bwd(p, n_views > 1, s);
+    PVG_CUDA(cudaGetLastError());
+    return PVG_OK;
+}
+
+// ------------------------------------------------------------------ introspection
+
+extern "C" pvg_status_t pvg_frame_stats(pvg_frame_t *f, int64_t *n_visible, int64_t *n_pairs, int32_t *overflowed) {
+    if (!f) return PVG_ERR_INVALID;
+    PVG_CUDA(cudaMemcpyAsync(f->h_counters, f->counters.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, f->stream));
+    PVG_CUDA(cudaStreamSynchronize(f->stream));
+    if (n_visible) *n_visible = f->h_counters[0];
+    if (n_pairs) *n_pairs = f->h_counters[1];
+    if (overflowed) *overflowed = (int32_t)f->h_counters[2];
+    return PVG_OK;
+}
+
+__global__ static void k_export_rect(const uint2 *rect, const uint32_t *d_m, int32_t *out) {
+    const uint32_t M = *d_m;
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const uint2 r = rect[m];
+        out[4 * m + 0] = (int32_t)(r.x & 0xffffu);
+        out[4 * m + 1] = (int32_t)(r.x >> 16);
+        out[4 * m + 2] = (int32_t)(r.y & 0xffffu);
+        out[4 * m + 3] = (int32_t)(r.y >> 16);
+    }
+}
+
+extern "C" pvg_status_t pvg_frame_export(pvg_frame_t *f, uint32_t *sorted_gid, uint32_t *depth_key, int32_t *rect,
+                                         float *records, uint32_t *pair_vals, uint32_t *ranges) {
+    if (!f || !f->valid) return PVG_ERR_INVALID;
+    int64_t M, K;
+    int32_t ov;
+    PVG_TRY(pvg_frame_stats(f, &M, &K, &ov));
+    if (K > (int64_t)f->pair_capacity) K = f->pair_capacity;
+    cudaStream_t s = f->stream;
+    if (sorted_gid && M)
+        PVG_CUDA(cudaMemcpyAsync(sorted_gid, f->sgid.p, 4 * M, cudaMemcpyDeviceToDevice, s));
+    if (depth_key && M)
+        PVG_CUDA(cudaMemcpyAsync(depth_key, f->szkey.p, 4 * M, cudaMemcpyDeviceToDevice, s));
+    if (records && M)
+        PVG_CUDA(cudaMemcpyAsync(records, f->rec.p, 48 * M, cudaMemcpyDeviceToDevice, s));
+    if (pair_vals && K)
+        PVG_CUDA(cudaMemcpyAsync(pair_vals, f->pair_vals.p, 4 * K, cudaMemcpyDeviceToDevice, s));
+    if (ranges && f->total_tiles)
+        PVG_CUDA(cudaMemcpyAsync(ranges, f->ranges.p, 8 * (size_t)f->total_tiles, cudaMemcpyDeviceToDevice, s));
+    if (rect && M) k_export_rect<<<152, 256, 0, s>>>(ptr<uint2>(f->rect), ptr<uint32_t>(f->counters), rect);
+    PVG_CUDA(cudaGetLastError());
+    PVG_CUDA(cudaStreamSynchronize(s));
+    return PVG_OK;
+}

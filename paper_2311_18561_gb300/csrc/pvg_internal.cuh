@@ -1,0 +1,137 @@
+// pvg_internal.cuh -- device-side data layout shared by the kernels of the
+// PVG rasterizer (sm_103a).  Not part of the ABI.
+//
+// Layout in HBM (per forward pass):
+//   items     (view, Gaussian) pairs, gid = item_base[view] + i      [NV]
+//   visible   depth-sorted visible items, position m                 [M]
+//     sgid[m]   gid of the m-th visible item in (depth, gid) order
+//     rec[m]    3 x float4 record read by the compositor:
+//               (u, v, conic a, conic b) (conic c, o~, z, 0) (r, g, b, 0)
+//     rect[m]   tile rectangle, packed (tx0 | ty0 << 16, tx1 | ty1 << 16)
+//   pairs     (tile, m) pairs sorted by (tile, depth, gid)             [K]
+//   ranges    [start, end) into the pairs per global tile             [tiles]
+//   pixels    final transmittance and last blended list position      [sum HW]
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pvg {
+
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip gate
+constexpr float kAlphaCap = 0.99f;          // alpha cap
+constexpr float kTStop = 1e-4f;             // transmittance stop
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e): e^x = 2^(x log2 e)
+constexpr int kMaxViewsPerCall = 4096;
+
+// Per-view description, uploaded once per call.
+struct ViewDesc {
+    float R[9], T[3];  // world->camera
+    float fx, fy, cx, cy;
+    float t, znear;
+    float bg[3];
+    float campos[3];   // camera centre in world space, -R^T T
+    float limx, limy;  // J clamp on x/z and y/z
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    uint32_t tile_base;  // first global tile id of this view
+    uint32_t pix_base;   // first pixel of this view in the per-pixel state
+    uint32_t item_base;  // first gid of this view
+    uint32_t n;          // Gaussians of this view's scene
+    int32_t sh_degree;
+    int32_t pad0;
+    // scene
+    const float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opac, *sh;
+    // outputs
+    float *out_rgb, *out_depth, *out_alpha;
+    // backward inputs / outputs
+    const float *dl_rgb, *dl_depth, *dl_alpha;
+    float *g_mu, *g_vel, *g_tau, *g_beta, *g_period, *g_scale, *g_quat, *g_opac, *g_sh;
+};
+
+// Launch-wide parameters.
+struct Params {
+    const ViewDesc *views;
+    int32_t n_views;
+    int32_t tile_w, tile_h;
+    float dilation;
+    uint32_t n_items;        // NV
+    uint32_t total_tiles;
+    uint32_t pair_capacity;
+    // device counters: [0] visible M, [1] pairs K, [2] overflow flag
+    uint32_t *counters;
+    // per-item scratch
+    uint32_t *item_cnt;      // [NV] tiles touched (0 = invisible)
+    uint32_t *item_zkey;     // [NV] depth bits (valid where item_cnt > 0)
+    // visible
+    uint32_t *sgid;          // [M]
+    uint32_t *szkey;         // [M]
+    float4 *rec;             // [M*3]
+    uint2 *rect;             // [M]
+    uint32_t *vis_cnt;       // [M] tiles per visible item
+    // pairs
+    uint32_t *pair_keys;     // [K] tile ids (sorted in place via ping-pong)
+    uint32_t *pair_vals;     // [K]
+    uint2 *ranges;           // [total_tiles]
+    float *pix_T;            // [sum HW]
+    uint32_t *pix_last;      // [sum HW]
+    // backward
+    float *g2d;              // [M*10]
+};
+
+// view of a global item / tile by binary search over the per-view bases
+__device__ __forceinline__ int view_of_item(const ViewDesc *views, int nv, uint32_t gid) {
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].item_base <= gid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int view_of_tile(const ViewDesc *views, int nv, uint32_t tile) {
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// 2^x on the SFU (PTX ex2.approx.ftz.f32)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Gaussian falloff exponent in base-2 units for the record's prescaled
+// conic (a', b', c') = -log2(e) (a/2, b, c/2): the pixel weight is
+// 2^(a' dx^2 + b' dx dy + c' dy^2).  Written with explicit roundings so
+// every kernel that calls it gets bit-identical results.
+__device__ __forceinline__ float falloff_exp2(float ap, float bp, float cp, float dx, float dy) {
+    const float t = __fmaf_rn(bp, dy, __fmul_rn(ap, dx));
+    return __fmaf_rn(__fmul_rn(cp, dy), dy, __fmul_rn(dx, t));
+}
+
+}  // namespace pvg
+
+// host-side launchers (one translation unit each)
+namespace pvg {
+cudaError_t set_sh_constants();
+void launch_project_count(const Params &p, cudaStream_t s);
+void launch_finalize(const Params &p, cudaStream_t s);
+void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s);
+// sort / scan
+size_t sort_temp_bytes(uint32_t capacity);
+void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);
+void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                      const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
+                      cudaStream_t s, bool *result_in_alt);
+void scan_count_pairs(const Params &p, void *temp, cudaStream_t s);
+void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
+void launch_ranges(const Params &p, cudaStream_t s);
+// raster
+bool composite_supported(int tw, int th);
+void launch_composite(const Params &p, cudaStream_t s);
+void launch_composite_bwd(const Params &p, cudaStream_t s);
+}  // namespace pvg

@@ -1,0 +1,400 @@
+// sort.cu -- device-wide scans, stream compaction, pair emission and a
+// stable LSD radix sort of (u32 key, u32 value) pairs, all with the element
+// count read from device memory so that no host round trip is needed.
+//
+// Role in the method: "sorting the Gaussians according to their depth in
+// camera space" (Sec. 3.1) for every tile of the tile-based rasterizer.
+// The sort is done in two stages:
+//   1. the visible (view, Gaussian) items are sorted by the float32 bits of
+//      their camera depth (4 digit passes over M items; the items start in
+//      gid order and the sort is stable, so equal depths keep gid order);
+//   2. each item, in that depth order, emits one (tile id, depth position)
+//      pair per covered tile, and the K pairs are sorted stably by tile id
+//      alone (ceil(log2 tiles) bits, 2-3 passes).
+// The result is ordered by (tile, depth, gid) -- the per-tile front-to-back
+// lists -- while the wide K-sized sort only moves the tile bits.
+//
+// Partitioning: a fixed grid of G blocks; block b owns the contiguous
+// segment [b*seg, (b+1)*seg) with seg = ceil(n / G) rounded up to the tile
+// size, so a block's output for a digit always precedes block b+1's
+// (stability across blocks); inside a block, tiles are taken in order and
+// ranked stably within each warp with __match_any_sync.
+#include "pvg_internal.cuh"
+
+namespace pvg {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;  // 1024
+constexpr int kMaxScanBlocks = 1024;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+constexpr int kRadix = 256;
+constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// inclusive warp scan
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// exclusive block scan over blockDim.x (multiple of 32, <= 1024) values;
+// returns the exclusive prefix, *total receives the block sum.  Uses
+// 33 words of shared memory.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *smem, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) smem[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? smem[lane] : 0;
+        const uint32_t wi = warp_incl_scan(w);
+        if (lane < nw) smem[lane] = wi - w;
+        if (lane == 31) smem[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = smem[warp] + incl - v;
+    *total = smem[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void segment_of(uint32_t n, int G, int align, uint32_t *b0, uint32_t *b1) {
+    uint32_t seg = (n + G - 1) / G;
+    seg = (seg + align - 1) / align * align;
+    const uint64_t s = (uint64_t)blockIdx.x * seg;
+    *b0 = (uint32_t)(s < n ? s : n);
+    const uint64_t e = s + seg;
+    *b1 = (uint32_t)(e < n ? e : n);
+}
+
+// ---------------------------------------------------------------- scans
+
+// Functor protocol: n() element count, value(i) item's count,
+// apply(i, offset) consumes the exclusive prefix.
+struct CompactF {
+    const uint32_t *cnt, *zkey;
+    uint32_t *keys_out, *vals_out;
+    uint32_t n_items;
+    __device__ uint32_t n() const { return n_items; }
+    __device__ uint32_t value(uint32_t i) const { return cnt[i] > 0u ? 1u : 0u; }
+    __device__ void apply(uint32_t i, uint32_t off, uint32_t v) const {
+        if (v) {
+            keys_out[off] = zkey[i];
+            vals_out[off] = i;
+        }
+    }
+};
+
+struct EmitF {
+    const uint32_t *d_m;
+    const uint32_t *vis_cnt;
+    const uint2 *rect;
+    const uint32_t *sgid;
+    const ViewDesc *views;
+    int nv;
+    uint32_t *keys, *vals;
+    uint32_t capacity;
+    __device__ uint32_t n() const { return *d_m; }
+    __device__ uint32_t value(uint32_t m) const { return vis_cnt[m]; }
+    __device__ void apply(uint32_t m, uint32_t off, uint32_t v) const {
+        if (v == 0) return;
+        const uint2 r = rect[m];
+        const uint32_t tx0 = r.x & 0xffffu, ty0 = r.x >> 16, tx1 = r.y & 0xffffu, ty1 = r.y >> 16;
+        const int view = view_of_item(views, nv, sgid[m]);
+        const uint32_t tb = views[view].tile_base;
+        const uint32_t tw = (uint32_t)views[view].tiles_x;
+        uint32_t j = off;
+        for (uint32_t ty = ty0; ty < ty1; ty++)
+            for (uint32_t tx = tx0; tx < tx1; tx++, j++)
+                if (j < capacity) {
+                    keys[j] = tb + ty * tw + tx;
+                    vals[j] = m;
+                }
+    }
+};
+
+template <class F>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, uint32_t *partials) {
+    __shared__ uint32_t smem[33];
+    uint32_t b0, b1;
+    segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
+    uint32_t acc = 0;
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kScanThreads) acc += f.value(i);
+    uint32_t total;
+    block_excl_scan(acc, smem, &total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+// exclusive scan of G partials in place (one block of 1024 threads);
+// *total = sum; if cap_flag != NULL and total > capacity, set *cap_flag.
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int G, uint32_t *total,
+                                                        uint32_t capacity, uint32_t *cap_flag) {
+    __shared__ uint32_t smem[33];
+    const uint32_t v = threadIdx.x < (unsigned)G ? partials[threadIdx.x] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, smem, &tot);
+    if (threadIdx.x < (unsigned)G) partials[threadIdx.x] = ex;
+    if (threadIdx.x == 0) {
+        *total = tot;
+        if (cap_flag && tot > capacity) *cap_flag = 1u;
+    }
+}
+
+template <class F>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, const uint32_t *partials) {
+    __shared__ uint32_t smem[33];
+    uint32_t b0, b1;
+    segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
+    uint32_t base = partials[blockIdx.x];
+    for (uint32_t c0 = b0; c0 < b1; c0 += kScanChunk) {
+        // blocked arrangement: thread t owns items c0 + t*4 .. +3
+        uint32_t v[kScanItems];
+        uint32_t sum = 0;
+        const uint32_t first = c0 + threadIdx.x * kScanItems;
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const uint32_t i = first + k;
+            v[k] = i < b1 ? f.value(i) : 0u;
+            sum += v[k];
+        }
+        uint32_t total;
+        uint32_t off = base + block_excl_scan(sum, smem, &total);
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const uint32_t i = first + k;
+            if (i < b1) f.apply(i, off, v[k]);
+            off += v[k];
+        }
+        base += total;
+    }
+}
+
+int scan_blocks(uint32_t capacity) {
+    uint32_t g = (capacity + kScanChunk - 1) / kScanChunk;
+    if (g < 1) g = 1;
+    if (g > kMaxScanBlocks) g = kMaxScanBlocks;
+    return (int)g;
+}
+
+int sort_blocks(uint32_t capacity) {
+    uint32_t g = (capacity + kSortTile - 1) / kSortTile;
+    if (g < 1) g = 1;
+    if (g > kMaxSortBlocks) g = kMaxSortBlocks;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------- radix
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *keys, const uint32_t *d_n,
+                                                                uint32_t cap, int shift, uint32_t mask,
+                                                                uint32_t *hist) {
+    __shared__ uint32_t sh[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) sh[d] = 0;
+    __syncthreads();
+    uint32_t b0, b1;
+    segment_of(min(*d_n, cap), gridDim.x, kSortTile, &b0, &b1);
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kSortThreads) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * gridDim.x + blockIdx.x] = sh[d];
+}
+
+// exclusive scan of the digit-major histogram (kRadix * G entries)
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int entries) {
+    __shared__ uint32_t smem[33];
+    const int per = (entries + 1023) / 1024;
+    const int s = threadIdx.x * per;
+    uint32_t acc = 0;
+    for (int k = 0; k < per; k++)
+        if (s + k < entries) acc += hist[s + k];
+    uint32_t total;
+    uint32_t run = block_excl_scan(acc, smem, &total);
+    for (int k = 0; k < per; k++)
+        if (s + k < entries) {
+            const uint32_t c = hist[s + k];
+            hist[s + k] = run;
+            run += c;
+        }
+}
+
+static_assert(kSortThreads == kRadix, "one thread per digit in the downsweep");
+
+struct SortSmem {
+    uint32_t base[kRadix];                // running global offset per digit
+    uint32_t warp_hist[kSortWarps][kRadix];
+    uint32_t tile_start[kRadix];
+    uint32_t keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t scan[33];
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
+                                                                  const uint32_t *__restrict__ vals_in,
+                                                                  uint32_t *__restrict__ keys_out,
+                                                                  uint32_t *__restrict__ vals_out,
+                                                                  const uint32_t *d_n, uint32_t cap, int shift,
+                                                                  uint32_t mask, const uint32_t *hist) {
+    __shared__ SortSmem S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int d = tid; d < kRadix; d += kSortThreads) S.base[d] = hist[d * gridDim.x + blockIdx.x];
+    uint32_t b0, b1;
+    segment_of(min(*d_n, cap), gridDim.x, kSortTile, &b0, &b1);
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t t0 = b0; t0 < b1; t0 += kSortTile) {
+        for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&S.warp_hist[0][0])[k] = 0;
+        __syncthreads();
+        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+        bool valid[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            const uint32_t pos = t0 + warp * (32 * kSortItems) + j * 32 + lane;
+            valid[j] = pos < b1;
+            key[j] = valid[j] ? keys_in[pos] : 0u;
+            val[j] = valid[j] ? vals_in[pos] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            const uint32_t d = (key[j] >> shift) & mask;
+            const uint32_t peers = __match_any_sync(0xffffffffu, valid[j] ? d : 0xffffffffu);
+            uint32_t before = 0;
+            if (valid[j]) before = S.warp_hist[warp][d];
+            __syncwarp();
+            if (valid[j] && (peers & lt) == 0) S.warp_hist[warp][d] = before + __popc(peers);
+            __syncwarp();
+            rank[j] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+        // per digit: exclusive offsets across warps, tile count, tile start
+        uint32_t tile_cnt = 0;
+        {
+            const int d = tid;  // kSortThreads == kRadix
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) {
+                const uint32_t c = S.warp_hist[w][d];
+                S.warp_hist[w][d] = tile_cnt;
+                tile_cnt += c;
+            }
+            uint32_t tot;
+            S.tile_start[d] = block_excl_scan(tile_cnt, S.scan, &tot);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortItems; j++) {
+            if (!valid[j]) continue;
+            const uint32_t d = (key[j] >> shift) & mask;
+            const uint32_t p = S.tile_start[d] + S.warp_hist[warp][d] + rank[j];
+            S.keys[p] = key[j];
+            S.vals[p] = val[j];
+        }
+        __syncthreads();
+        const uint32_t nvalid = (b1 - t0) < (uint32_t)kSortTile ? (b1 - t0) : (uint32_t)kSortTile;
+        for (uint32_t p = tid; p < nvalid; p += kSortThreads) {
+            const uint32_t k = S.keys[p];
+            const uint32_t d = (k >> shift) & mask;
+            const uint32_t dst = S.base[d] + (p - S.tile_start[d]);
+            keys_out[dst] = k;
+            vals_out[dst] = S.vals[p];
+        }
+        __syncthreads();
+        S.base[tid] += tile_cnt;
+        __syncthreads();
+    }
+}
+
+__global__ void k_ranges(const uint32_t *keys, const uint32_t *d_k, uint32_t capacity, uint2 *ranges) {
+    uint32_t K = *d_k;
+    if (K > capacity) K = capacity;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
+        const uint32_t t = keys[j];
+        if (j == 0 || keys[j - 1] != t) ranges[t].x = j;
+        if (j == K - 1 || keys[j + 1] != t) ranges[t].y = j + 1;
+    }
+}
+
+struct TempLayout {
+    uint32_t *hist;      // kRadix * kMaxSortBlocks
+    uint32_t *partials;  // kMaxScanBlocks
+};
+
+TempLayout temp_layout(void *temp) {
+    TempLayout t;
+    t.hist = (uint32_t *)temp;
+    t.partials = t.hist + kRadix * kMaxSortBlocks;
+    return t;
+}
+
+}  // namespace
+
+size_t sort_temp_bytes(uint32_t) { return sizeof(uint32_t) * ((size_t)kRadix * kMaxSortBlocks + kMaxScanBlocks); }
+
+void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s) {
+    TempLayout t = temp_layout(temp);
+    CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, p.n_items};
+    const int G = scan_blocks(p.n_items);
+    k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[0], 0xffffffffu, nullptr);
+    k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
+}
+
+void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                      const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
+                      cudaStream_t s, bool *result_in_alt) {
+    TempLayout t = temp_layout(temp);
+    const int G = sort_blocks(capacity);
+    bool alt = false;
+    for (int b = begin_bit; b < end_bit;) {
+        const int nb = (end_bit - b) >= 8 ? 8 : (end_bit - b);
+        const uint32_t mask = (1u << nb) - 1u;
+        const uint32_t *ki = alt ? keys_alt : keys;
+        const uint32_t *vi = alt ? vals_alt : vals;
+        uint32_t *ko = alt ? keys : keys_alt;
+        uint32_t *vo = alt ? vals : vals_alt;
+        k_radix_upsweep<<<G, kSortThreads, 0, s>>>(ki, d_count, capacity, b, mask, t.hist);
+        k_radix_scan<<<1, 1024, 0, s>>>(t.hist, kRadix * G);
+        k_radix_downsweep<<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist);
+        alt = !alt;
+        b += nb;
+    }
+    *result_in_alt = alt;
+}
+
+// scan of the per-visible tile counts: K -> counters[1], overflow flag ->
+// counters[2]; then emission of the (tile, m) pairs in depth order.
+void scan_count_pairs(const Params &p, void *temp, cudaStream_t s) {
+    TempLayout t = temp_layout(temp);
+    EmitF f{&p.counters[0], p.vis_cnt, p.rect, p.sgid, p.views, p.n_views, p.pair_keys, p.pair_vals,
+            p.pair_capacity};
+    const int G = scan_blocks(p.n_items);
+    k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[1], p.pair_capacity, &p.counters[2]);
+}
+
+void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
+    TempLayout t = temp_layout(temp);
+    EmitF f{&p.counters[0], p.vis_cnt, p.rect, p.sgid, p.views, p.n_views, p.pair_keys, p.pair_vals,
+            p.pair_capacity};
+    const int G = scan_blocks(p.n_items);
+    k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
+}
+
+void launch_ranges(const Params &p, cudaStream_t s) {
+    cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * (size_t)p.total_tiles, s);
+    k_ranges<<<152 * 8, 256, 0, s>>>(p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
+}
+
+}  // namespace pvg

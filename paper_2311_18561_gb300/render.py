@@ -1,0 +1,231 @@
+"""PyTorch-facing API of the rasterizer.
+
+PyTorch supplies device memory and the stream; every step of the render and
+of its adjoint runs in the CUDA library through :mod:`.abi`.
+
+``render(scene, cams)`` renders N-view images; ``PVGRender`` is the
+``torch.autograd.Function`` whose backward calls ``pvg_render_bwd``
+(Sec. 3.1, Eq. 4: the render function is differentiable; gradients for
+every learnable parameter of Sec. 3.2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import abi
+
+PARAM_NAMES = ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh")
+
+
+def scene_to_device(scene, device="cuda"):
+    """numpy scene dict -> dict of contiguous float32 CUDA tensors."""
+    return {k: torch.as_tensor(np.ascontiguousarray(scene[k], dtype=np.float32)).to(device)
+            for k in PARAM_NAMES}
+
+
+def sh_degree(scene_t) -> int:
+    k = scene_t["sh"].shape[1]
+    d = int(round(k ** 0.5)) - 1
+    if (d + 1) ** 2 != k or not 0 <= d <= 3:
+        raise ValueError("sh must be [N, (D+1)^2, 3] with D in 0..3")
+    return d
+
+
+def _check_scene(scene_t):
+    n = scene_t["mu"].shape[0]
+    shapes = dict(mu=(n, 3), vel=(n, 3), tau=(n,), beta=(n,), period=(n,), scale=(n, 3), quat=(n, 4),
+                  opacity=(n,))
+    for k, s in shapes.items():
+        t = scene_t[k]
+        if tuple(t.shape) != s or t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("scene[%r] must be a contiguous float32 CUDA tensor of shape %s" % (k, s))
+    sh = scene_t["sh"]
+    if sh.dim() != 3 or sh.shape[0] != n or sh.shape[2] != 3 or sh.dtype != torch.float32 or not sh.is_contiguous():
+        raise ValueError("scene['sh'] must be a contiguous float32 CUDA tensor [N, K, 3]")
+    return n
+
+
+def abi_scene(scene_t) -> abi.Scene:
+    n = _check_scene(scene_t)
+    s = abi.Scene()
+    s.n = n
+    s.sh_degree = sh_degree(scene_t)
+    for k in PARAM_NAMES:
+        setattr(s, k, scene_t[k].data_ptr() if n > 0 else None)
+    return s
+
+
+def _stream_ptr(stream=None):
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(st.cuda_stream)
+
+
+class Renderer:
+    """Owns one ``pvg_ctx_t`` (workspace) on the current CUDA device."""
+
+    def __init__(self, tile=(16, 16), sync_sizes=True, pair_capacity=1 << 24, dilation=0.3, fov_clamp=1.3):
+        self._lib = abi.lib()
+        self.cfg = abi.config(tile, sync_sizes, pair_capacity, dilation, fov_clamp)
+        h = C.c_void_p()
+        abi.check(self._lib.pvg_create(C.byref(h), C.byref(self.cfg)), "pvg_create")
+        self.handle = h
+        self.device = torch.cuda.current_device()
+
+    def close(self):
+        if self.handle:
+            self._lib.pvg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, tile):
+        self.cfg.tile_w, self.cfg.tile_h = int(tile[0]), int(tile[1])
+        abi.check(self._lib.pvg_set_config(self.handle, C.byref(self.cfg)), "pvg_set_config")
+
+    def alloc_images(self, cams, device="cuda"):
+        outs = []
+        for cam in cams:
+            H, W = int(cam["height"]), int(cam["width"])
+            outs.append(dict(rgb=torch.empty(3, H, W, device=device), depth=torch.empty(H, W, device=device),
+                             alpha=torch.empty(H, W, device=device)))
+        return outs
+
+    def forward(self, scene_t, cams, outs=None, frame=None, stream=None):
+        """Render into ``outs`` (list of dicts rgb [3,H,W], depth, alpha);
+        returns ``outs``.  ``frame`` (a :class:`Frame`) keeps the state the
+        backward pass needs."""
+        if outs is None:
+            outs = self.alloc_images(cams)
+        sc = abi_scene(scene_t)
+        ca = abi.cameras(cams)
+        imgs = (abi.Image * len(cams))()
+        for k, o in enumerate(outs):
+            imgs[k].rgb = o["rgb"].data_ptr()
+            imgs[k].depth = o["depth"].data_ptr() if o.get("depth") is not None else None
+            imgs[k].alpha = o["alpha"].data_ptr() if o.get("alpha") is not None else None
+        st = self._lib.pvg_render_fwd(self.handle, C.byref(sc), ca, len(cams), imgs,
+                                      frame.handle if frame is not None else None, _stream_ptr(stream))
+        abi.check(st, "pvg_render_fwd")
+        return outs
+
+    def backward(self, scene_t, cams, frame, grads_out, stream=None, grads=None):
+        """dL/d(images) ``grads_out`` (list of dicts, entries may be None) ->
+        dict of parameter gradients (allocated if ``grads`` is None)."""
+        sc = abi_scene(scene_t)
+        ca = abi.cameras(cams)
+        if grads is None:
+            grads = {k: torch.empty_like(scene_t[k]) for k in PARAM_NAMES}
+        g = abi.SceneGrad()
+        for k in PARAM_NAMES:
+            setattr(g, k, grads[k].data_ptr() if (grads.get(k) is not None and grads[k].numel()) else None)
+        dl = (abi.ImageGrad * len(cams))()
+        for k, d in enumerate(grads_out):
+            for name in ("rgb", "depth", "alpha"):
+                t = d.get(name)
+                setattr(dl[k], name, t.contiguous().data_ptr() if t is not None else None)
+        st = self._lib.pvg_render_bwd(self.handle, C.byref(sc), ca, len(cams), frame.handle, dl, C.byref(g),
+                                      _stream_ptr(stream))
+        abi.check(st, "pvg_render_bwd")
+        return grads
+
+
+class Frame:
+    """Saved state of one forward pass (``pvg_frame_t``)."""
+
+    def __init__(self):
+        self._lib = abi.lib()
+        h = C.c_void_p()
+        abi.check(self._lib.pvg_frame_create(C.byref(h)), "pvg_frame_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self._lib.pvg_frame_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self):
+        m, k, ov = C.c_int64(), C.c_int64(), C.c_int32()
+        abi.check(self._lib.pvg_frame_stats(self.handle, C.byref(m), C.byref(k), C.byref(ov)), "pvg_frame_stats")
+        return int(m.value), int(k.value), int(ov.value)
+
+    def export(self, total_tiles):
+        """Device intermediates of the last forward as CPU numpy arrays."""
+        m, k, _ = self.stats()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        sg = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        zk = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        rect = torch.empty(max(m, 1), 4, dtype=torch.int32, device=dev)
+        rec = torch.empty(max(m, 1), 12, dtype=torch.float32, device=dev)
+        pv = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+        rg = torch.empty(max(total_tiles, 1), 2, dtype=torch.int32, device=dev)
+        abi.check(self._lib.pvg_frame_export(self.handle, sg.data_ptr(), zk.data_ptr(), rect.data_ptr(),
+                                             rec.data_ptr(), pv.data_ptr(), rg.data_ptr()), "pvg_frame_export")
+        u32 = lambda t, n: t.cpu().numpy().view(np.uint32)[:n].copy()
+        return dict(sorted_gid=u32(sg, m), depth_key=u32(zk, m), rect=rect.cpu().numpy()[:m],
+                    records=rec.cpu().numpy()[:m], pair_vals=u32(pv, k),
+                    ranges=rg.cpu().numpy().view(np.uint32)[:total_tiles].copy())
+
+
+def tiles_of(cam, tile=(16, 16)):
+    tw, th = tile
+    return (int(cam["width"]) + tw - 1) // tw, (int(cam["height"]) + th - 1) // th
+
+
+_DEFAULT = {}
+
+
+def default_renderer():
+    dev = torch.cuda.current_device()
+    if dev not in _DEFAULT:
+        _DEFAULT[dev] = Renderer()
+    return _DEFAULT[dev]
+
+
+def render(scene_t, cams, renderer=None, frame=None):
+    """Render a list of cameras; returns a list of dicts (rgb, depth, alpha)."""
+    r = renderer or default_renderer()
+    return r.forward(scene_t, cams, frame=frame)
+
+
+class PVGRender(torch.autograd.Function):
+    """images = Render({H_i(t)}; E, I) (Sec. 3.2, Eq. 8) for one camera,
+    differentiable w.r.t. all nine parameter arrays."""
+
+    @staticmethod
+    def forward(ctx, cam, renderer, mu, vel, tau, beta, period, scale, quat, opacity, sh):
+        scene_t = dict(mu=mu.contiguous(), vel=vel.contiguous(), tau=tau.contiguous(), beta=beta.contiguous(),
+                       period=period.contiguous(), scale=scale.contiguous(), quat=quat.contiguous(),
+                       opacity=opacity.contiguous(), sh=sh.contiguous())
+        frame = Frame()
+        out = renderer.forward(scene_t, [cam], frame=frame)[0]
+        ctx.cam, ctx.renderer, ctx.frame = cam, renderer, frame
+        ctx.save_for_backward(*[scene_t[k] for k in PARAM_NAMES])
+        return out["rgb"], out["depth"], out["alpha"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_alpha):
+        saved = ctx.saved_tensors
+        scene_t = dict(zip(PARAM_NAMES, saved))
+        grads = ctx.renderer.backward(scene_t, [ctx.cam], ctx.frame,
+                                      [dict(rgb=g_rgb, depth=g_depth, alpha=g_alpha)])
+        ctx.frame.close()
+        return (None, None) + tuple(grads[k] for k in PARAM_NAMES)
+
+
+def render_differentiable(params, cam, renderer=None):
+    """params: dict of tensors (may require grad).  Returns rgb, depth, alpha."""
+    r = renderer or default_renderer()
+    return PVGRender.apply(cam, r, *[params[k] for k in PARAM_NAMES])

@@ -1,0 +1,109 @@
+"""Parity of the CUDA backward path (stage d) with the oracle's FP64
+reverse mode, through the C ABI and through torch.autograd.  GPU only.
+
+Tolerance: per parameter group, ||g - g_ref|| / ||g_ref|| <= 1e-2, and
+per element |g - g_ref| <= 1e-2 max|g_ref| (FP32 accumulation order and
+rare gate decisions that FP32 takes differently from FP64 stay inside it).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_18561_gb300 import render as R
+from paper_2311_18561_gb300 import synth
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+NAMES = R.PARAM_NAMES
+
+
+def _compare_grads(got, ref, rel=1e-2):
+    report = {}
+    for k in NAMES:
+        g = got[k].detach().cpu().numpy().astype(np.float64).reshape(-1)
+        r = ref[k].reshape(-1)
+        nr = np.linalg.norm(r)
+        if nr == 0:
+            assert np.abs(g).max(initial=0) == 0, k
+            continue
+        report[k] = (float(np.linalg.norm(g - r) / nr), float(np.abs(g - r).max() / np.abs(r).max()))
+    for k, (nrm, mx) in report.items():
+        assert nrm <= rel and mx <= rel, (k, report)
+    return report
+
+
+def _weights(H, W, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(3, H, W)), rng.normal(size=(H, W)) * 0.1, rng.normal(size=(H, W))
+
+
+@pytest.mark.parametrize("deg", [0, 3])
+def test_backward_matches_oracle_fd_subcase(deg):
+    """The 500-Gaussian, 64x48 sub-case of the training config."""
+    scene = synth.make_fd_scene(seed=0, n=500, sh_degree=deg)
+    cam = synth.fd_camera(64, 48, t=0.45)
+    cam["bg"] = np.array([0.2, 0.5, 0.8], np.float32)
+    H, W = cam["height"], cam["width"]
+    w_rgb, w_d, w_a = _weights(H, W, 1)
+    r = R.Renderer()
+    fr = R.Frame()
+    st = R.scene_to_device(scene)
+    r.forward(st, [cam], frame=fr)
+    dl = dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"),
+              depth=torch.tensor(w_d, dtype=torch.float32, device="cuda"),
+              alpha=torch.tensor(w_a, dtype=torch.float32, device="cuda"))
+    grads = r.backward(st, [cam], fr, [dl])
+    torch.cuda.synchronize()
+    ref = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), w_d, w_a)
+    _compare_grads(grads, ref)
+
+
+def test_autograd_l1_training_step():
+    """L1 loss against a random target (the training config's loss) through
+    torch.autograd; gradients against the oracle's with dL/dimage = sign/n."""
+    scene = synth.make_fd_scene(seed=3, n=500, sh_degree=3)
+    cam = synth.fd_camera(64, 48, t=0.6)
+    target = synth.random_image(48, 64, seed=1)
+    st = R.scene_to_device(scene)
+    params = {k: v.clone().requires_grad_(True) for k, v in st.items()}
+    rgb, depth, alpha = R.render_differentiable(params, cam)
+    tgt = torch.tensor(target, device="cuda")
+    loss = (rgb - tgt).abs().mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    dl = torch.sign(rgb.detach() - tgt).cpu().numpy() / rgb.numel()
+    ref = oracle.render_bwd(scene, cam, np.transpose(dl, (1, 2, 0)), np.zeros((48, 64)), np.zeros((48, 64)))
+    _compare_grads({k: params[k].grad for k in NAMES}, ref)
+
+
+def test_multi_view_backward_sums_views():
+    scene = synth.make_fd_scene(seed=4, n=400, sh_degree=1)
+    cams = [synth.fd_camera(48, 40, t=0.2), synth.fd_camera(64, 48, t=0.7)]
+    st = R.scene_to_device(scene)
+    r = R.Renderer()
+    fr = R.Frame()
+    r.forward(st, cams, frame=fr)
+    dls, ref = [], None
+    for k, cam in enumerate(cams):
+        w_rgb, w_d, w_a = _weights(cam["height"], cam["width"], 10 + k)
+        dls.append(dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"),
+                        depth=torch.tensor(w_d, dtype=torch.float32, device="cuda"),
+                        alpha=torch.tensor(w_a, dtype=torch.float32, device="cuda")))
+        g = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), w_d, w_a)
+        ref = g if ref is None else {n: ref[n] + g[n] for n in NAMES}
+    grads = r.backward(st, cams, fr, dls)
+    torch.cuda.synchronize()
+    _compare_grads(grads, ref)
+
+
+def test_backward_of_empty_scene_is_empty():
+    empty = {k: v[:0] for k, v in synth.make_plain_scene(seed=0, n=4).items()}
+    st = R.scene_to_device(empty)
+    cam = synth.plain_camera(width=32, height=24)
+    r = R.Renderer()
+    fr = R.Frame()
+    r.forward(st, [cam], frame=fr)
+    grads = r.backward(st, [cam], fr, [dict(rgb=torch.ones(3, 24, 32, device="cuda"))])
+    assert all(g.numel() == 0 for g in grads.values())
