@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the PVG rasterizer on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one synthetic frame: the
+forward render (time evaluation, projection, depth + tile sort,
+compositing), the L1 loss against a target image, and the backward pass
+(compositing adjoint and chain rule to every PVG parameter).  Workload: the
+urban scene of 1.5M Gaussians (SH degree 3) seen at 1920x1280 from frame
+25 of the 50-frame street path.  ``value`` is whole-job Mpix/s of such
+steps; the forward-only render rate is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 launch one process per GPU (torchrun): each rank renders its
+own frame of the same scene (replicas, no collective on the data path).
+``--impl reference`` times the FP64 CPU oracle on a bounded pixel sample of
+the same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "render Mpix/s & fwd+bwd step ms at 1.5M Gaussians 1920x1280; served p50/p99 latency"
+FRAME = 25
+# name: (Gaussians, width, height, focal or None (hfov 50 deg), description)
+WORKLOADS = {
+    "urban": (1_500_000, 1920, 1280, None,
+              "urban scene, 1.5M Gaussians, SH-3, 1920x1280, street-path frame 25 (t=25/49), 16x16 tiles: "
+              "forward render + L1 loss + backward"),
+    "training": (1_000_000, 1242, 375, 720.0,
+                 "training config: urban-distribution scene, 1M Gaussians, SH-3, 1242x375 (f=720), "
+                 "street-path frame 25, 16x16 tiles: forward render + L1 loss + backward"),
+}
+N_GAUSS, W_PIX, H_PIX, FOCAL, WORKLOAD = WORKLOADS["urban"]
+
+
+def select_workload(name):
+    global N_GAUSS, W_PIX, H_PIX, FOCAL, WORKLOAD
+    N_GAUSS, W_PIX, H_PIX, FOCAL, WORKLOAD = WORKLOADS[name]
+
+
+def workload_camera(frame):
+    from paper_2311_18561_gb300 import synth
+
+    if FOCAL is None:
+        return synth.urban_frame_camera(frame, W_PIX, H_PIX)
+    return synth.street_camera(frame / 49.0, W_PIX, H_PIX, fx=FOCAL)
+
+
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# FP32 FMA-pipe lane-instructions per list-entry evaluation in the
+# compositor: 2 FADD (dx, dy), 4 FMUL + 2 FFMA (falloff exponent, o~ G)
+OPS_PER_EVAL = 8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="urban")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="wall-clock budget of the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=float(d.get("sm_max_mhz", SM_MAX_MHZ)))
+    except Exception:
+        return dict(hbm_gbs=6800.0, source="fallback", sm_max_mhz=SM_MAX_MHZ)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2311_18561_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2311_18561_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        return d["kernels"][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2311_18561_gb300 import render as R
+    from paper_2311_18561_gb300 import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    scene = synth.make_urban_scene(N_GAUSS, seed=0)
+    frame_idx = (FRAME + rank) % 50
+    cam = workload_camera(frame_idx)
+    st = R.scene_to_device(scene, dev)
+    target_host = torch.from_numpy(synth.random_image(H_PIX, W_PIX, seed=1)).pin_memory()
+    target = target_host.to(dev)
+    r = R.Renderer()
+    fr = R.Frame()
+    outs = r.alloc_images([cam])
+    grads = {k: torch.empty_like(st[k]) for k in R.PARAM_NAMES}
+    dl = torch.empty(3, H_PIX, W_PIX, device=dev)
+    loss = torch.empty(1, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step():
+        r.forward(st, [cam], outs=outs, frame=fr)
+        R.l1_loss(outs[0]["rgb"], target, dl=dl, loss=loss)
+        r.backward(st, [cam], fr, [dict(rgb=dl)], grads=grads)
+
+    def fwd_only():
+        r.forward(st, [cam], outs=outs, frame=fr)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        """Per-step CUDA events around fn (L2 flushed before each step, outside
+        the events); returns the summed step milliseconds."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+
+    # ---- timed region: K full steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    R.profile_enable(r, True)
+    R.profile_read(r)
+    l0 = R.kernel_launches()
+    barrier()
+    t0 = time.perf_counter()
+    step_ms = timed(step, args.steps)
+    barrier()
+    wall = time.perf_counter() - t0
+    launches = R.kernel_launches() - l0
+    stages = R.profile_read(r)
+    R.profile_enable(r, False)
+    # forward-only rate (same protocol)
+    fwd_ms = timed(fwd_only, args.steps) / args.steps
+    clk = clocks.stop()
+
+    M, K, ov = fr.stats()
+    r.forward(st, [cam], outs=outs, frame=fr)
+    E = R.eval_count(fr)
+    ms_step = step_ms / args.steps
+    t = torch.tensor([ms_step, fwd_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step, fwd_ms = float(t[0]), float(t[1])
+    mpix = W_PIX * H_PIX / 1e6
+
+    # ---- end to end through the public API: pinned host target in, loss out
+    loss_host = torch.empty(1, pin_memory=True)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        target.copy_(target_host, non_blocking=True)
+        step()
+        loss_host.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = (time.perf_counter() - e0) / args.steps
+    te = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te[0])
+
+    # ---- roofline of the dominant stage
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
+    dominant = max(stage_ms, key=stage_ms.get)
+    pk = peaks()
+    roof = None
+    if dominant in ("composite", "composite_bwd"):
+        alu_peak = SM_COUNT * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x clock, lane-instr/s
+        ach = E * OPS_PER_EVAL / (stage_ms[dominant] * 1e-3)
+        roof = {"kernel": "k_composite" if dominant == "composite" else "k_composite_bwd",
+                "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak / 1e12,
+                "unit": "T FP32-lane-instr/s", "frac": ach / alu_peak,
+                "traffic": ncu_traffic("k_composite" if dominant == "composite" else "k_composite_bwd"),
+                "work": "E=%d list-entry evaluations x %d FP32 instructions" % (E, OPS_PER_EVAL),
+                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (derived)" % pk["sm_max_mhz"]}
+    else:
+        # HBM-bound stages: algorithmic bytes per launch
+        algo = {"project": N_GAUSS * 68 + N_GAUSS * 8, "finalize": M * (68 + 192 + 48 + 8 + 4),
+                "preprocess_bwd": M * (260 + 40 + 260), "depth_sort": M * 4 * 20,
+                "pairs": M * 12 + K * 8, "tile_sort": K * 40}
+        b = algo.get(dominant, 0)
+        ach = b / (stage_ms[dominant] * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic(dominant)}
+    roof["peak_kind"] = pk["source"]
+
+    out = {
+        "metric": METRIC, "value": world * mpix / (ms_step * 1e-3), "unit": "Mpix/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded urban-shaped PVG scene, random-init parameters)",
+        "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": W_PIX, "height": H_PIX,
+                   "name": args.workload, "sh_degree": 3, "tile": "16x16",
+                   "l2": "flushed before every step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fwd_bwd_step_ms": ms_step,
+        "render_fwd": {"ms": fwd_ms, "mpix_s": world * mpix / (fwd_ms * 1e-3)},
+        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "visible": M, "pairs": K, "evals": E, "overflow": ov,
+        "wall_s_timed_region": wall,
+        "roofline": roof,
+        "e2e": {"value": world * mpix / e2e_s, "unit": "Mpix/s", "h2d_bytes_per_step": target_host.numel() * 4,
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene, cam, args.cpu_seconds)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- oracle
+
+def oracle_sample_step(scene, cam, pixels, w_rgb):
+    """One bounded-sample step of the FP64 oracle: forward on the sampled
+    pixels (culled mode) and the backward of L = sum w . rgb there."""
+    import numpy as np
+
+    import oracle
+
+    oracle.render(scene, cam, mode="culled", pixels=pixels)
+    P = pixels.shape[0]
+    oracle.render_bwd(scene, cam, w_rgb, np.zeros(P), np.zeros(P), mode="culled", pixels=pixels)
+
+
+def _sample_pixels(n, seed=0):
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.integers(0, W_PIX, n), rng.integers(0, H_PIX, n)], axis=1).astype(np.int32)
+
+
+def cpu_baseline(scene, cam, seconds):
+    """Time the oracle (as it stands) on a pixel sample sized so one step
+    takes about `seconds` of wall time on the host cores."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cores = oracle.num_threads()
+    n = 64
+    pix = _sample_pixels(n)
+    t0 = time.perf_counter()
+    oracle_sample_step(scene, cam, pix, np.ones((n, 3)) / n)
+    t_small = time.perf_counter() - t0
+    # the per-call preprocess + sort of all N Gaussians is a fixed cost
+    n2 = 4 * n
+    pix2 = _sample_pixels(n2)
+    t0 = time.perf_counter()
+    oracle_sample_step(scene, cam, pix2, np.ones((n2, 3)) / n2)
+    t_big = time.perf_counter() - t0
+    per_px = max((t_big - t_small) / (n2 - n), 1e-6)
+    fixed = max(t_small - per_px * n, 0.0)
+    n3 = int(min(max((seconds - fixed) / per_px, 64), 200_000))
+    pix3 = _sample_pixels(n3, seed=1)
+    t0 = time.perf_counter()
+    oracle_sample_step(scene, cam, pix3, np.ones((n3, 3)) / n3)
+    t = time.perf_counter() - t0
+    return {"value": n3 / t / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": "%d random pixels of the 1920x1280 frame; FP64 oracle forward (culled) + backward on "
+                      "those pixels, including its per-call preprocess and depth sort of all %d Gaussians "
+                      "(%.1f s)" % (n3, N_GAUSS, t)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2311_18561_gb300 import synth
+
+    oracle.build()
+    scene = synth.make_urban_scene(N_GAUSS, seed=0)
+    cam = workload_camera(FRAME)
+    # size each step's sample so that warmup + steps stay within a few minutes
+    per_step_budget = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    cb = cpu_baseline(scene, cam, per_step_budget)
+    n = int(cb["sample"].split()[0])
+    pix = _sample_pixels(n, seed=2)
+    w = np.ones((n, 3)) / n
+    for _ in range(args.warmup):
+        oracle_sample_step(scene, cam, pix, w)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample_step(scene, cam, pix, w)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = n / dt / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": W_PIX, "height": H_PIX,
+                      "sample_pixels_per_step": n},
+           "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": "%d random pixels per step, FP64 oracle forward + backward" % n},
+           "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    select_workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,9 +140,9 @@ typedef struct {
     int32_t sync_sizes;     /* 1 (default): pvg_render_fwd reads the pair count
                              * back to the host once per call and grows the
                              * workspace; 0: never synchronises, uses the
-                             * capacities below and fails with
-                             * PVG_ERR_OVERFLOW (reported by the next call or
-                             * pvg_frame_status) if they are exceeded */
+                             * capacities below; pairs beyond the capacity are
+                             * dropped and pvg_frame_stats reports the
+                             * overflow (the images are then incomplete) */
     int32_t reserved0;
     int64_t pair_capacity;  /* pairs per frame when sync_sizes = 0 */
     float dilation;         /* EWA low-pass h in px^2 (default 0.3) */
@@ -194,8 +194,48 @@ pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_
                             const pvg_scene_grad_t *grads, void *stream);
 
 /* ------------------------------------------------------------------ */
-/* introspection (tests)                                               */
+/* loss                                                                */
 /* ------------------------------------------------------------------ */
+
+/* L1 photometric term of the objective (Sec. 3.4, L = (1 - lambda_r) L1 +
+ * ...): *loss = scale * sum_i |pred[i] - target[i]| and, if dl is
+ * non-NULL, dl[i] = scale * sign(pred[i] - target[i]) (0 where equal).
+ * All pointers are device memory of n floats (loss: one float, overwritten).
+ * scale = 1/n gives the mean.  The sum is accumulated with float atomics
+ * (order not fixed).  PVG_ERR_INVALID for NULL pointers or n < 0. */
+pvg_status_t pvg_l1_loss(const float *pred, const float *target, int64_t n, float scale, float *dl,
+                         float *loss, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* measurement and introspection                                       */
+/* ------------------------------------------------------------------ */
+
+/* Kernels this library has launched since it was loaded (all contexts). */
+uint64_t pvg_kernel_launches(void);
+
+/* Stages timed by pvg_profile_* (CUDA events on the call's stream). */
+enum {
+    PVG_STAGE_PROJECT = 0,        /* time evaluation, projection, tile counts */
+    PVG_STAGE_DEPTH_SORT = 1,     /* visible compaction + depth radix sort */
+    PVG_STAGE_FINALIZE = 2,       /* records (incl. SH colour) in depth order */
+    PVG_STAGE_PAIRS = 3,          /* pair count scan + emission */
+    PVG_STAGE_TILE_SORT = 4,      /* tile-id radix sort + tile ranges */
+    PVG_STAGE_COMPOSITE = 5,      /* per-tile alpha compositing */
+    PVG_STAGE_COMPOSITE_BWD = 6,  /* compositing adjoint (image-space grads) */
+    PVG_STAGE_PREPROCESS_BWD = 7, /* chain rule to the PVG parameters */
+    PVG_NUM_STAGES = 8
+};
+/* Record CUDA events around every stage of later calls on `ctx` (on: 1). */
+pvg_status_t pvg_profile_enable(pvg_ctx_t *ctx, int on);
+/* Waits for the recorded events, writes the summed milliseconds and the
+ * number of timed calls per stage into ms[8] / calls[8] (host arrays), and
+ * forgets them. */
+pvg_status_t pvg_profile_read(pvg_ctx_t *ctx, double *ms, int64_t *calls);
+
+/* Sum over all pixels of the last forward into `frame` of the number of
+ * list entries each pixel evaluated (up to and including the one that
+ * stopped it): the compositing work E.  Synchronises the frame's stream. */
+pvg_status_t pvg_frame_eval_count(pvg_frame_t *frame, int64_t *evals);
 
 /* Copy device-side intermediate results of the last forward into
  * caller-owned DEVICE buffers (any may be NULL), for parity testing:

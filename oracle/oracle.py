@@ -44,7 +44,8 @@ def load():
         lib.pvgo_sh_basis.argtypes = [C.c_int, C.c_int64, P, P, P]
         lib.pvgo_preprocess.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 9
         lib.pvgo_render.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + [P] * 6
-        lib.pvgo_render_bwd.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 3 + [P] * 10
+        lib.pvgo_render_bwd.argtypes = ([C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + [P] * 3
+                                        + [P] * 10)
         lib.pvgo_num_threads.argtypes = []
         for f in (lib.pvgo_time_eval, lib.pvgo_sh_basis, lib.pvgo_preprocess, lib.pvgo_render,
                   lib.pvgo_render_bwd, lib.pvgo_num_threads):
@@ -155,10 +156,12 @@ def render(scene, cam, opts=None, mode="brute", pixels=None):
 GRAD_NAMES = ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh")
 
 
-def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=False):
+def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=False, mode="brute",
+               pixels=None):
     """Gradients of sum(dL_rgb*rgb) + sum(dL_depth*depth) + sum(dL_alpha*alpha)
-    (full image, brute force; dL_rgb [H,W,3], others [H,W]) w.r.t. every
-    parameter, as a dict keyed like the scene."""
+    w.r.t. every parameter, as a dict keyed like the scene.  Full image
+    (dL_rgb [H,W,3], others [H,W]) or, with ``pixels`` [P,2], only those
+    pixels (dL_rgb [P,3], others [P]).  mode 'brute' or 'culled'."""
     n, deg, arrs = _scene_args(scene)
     k = (deg + 1) ** 2
     g = dict(mu=np.zeros((n, 3)), vel=np.zeros((n, 3)), tau=np.zeros(n), beta=np.zeros(n),
@@ -167,7 +170,11 @@ def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=Fal
     g2d = np.zeros((n, 10))
     ca, oa = cam_array(cam), opt_array(opts)
     gr, gd, ga = _d(dL_rgb), _d(dL_depth), _d(dL_alpha)
-    rc = load().pvgo_render_bwd(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), _p(gr), _p(gd), _p(ga),
+    pix = None if pixels is None else np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+    npix = 0 if pix is None else pix.shape[0]
+    m = {"brute": 0, "culled": 1}[mode]
+    rc = load().pvgo_render_bwd(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, npix, _p(pix),
+                                _p(gr), _p(gd), _p(ga),
                                 *[_p(g[name]) for name in GRAD_NAMES], _p(g2d))
     if rc != 0:
         raise ValueError("oracle backward rejected its inputs")

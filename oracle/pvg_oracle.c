@@ -492,6 +492,23 @@ int pvgo_num_threads(void)
 /* per-Gaussian image-space gradient accumulator */
 enum { G2_U = 0, G2_V, G2_A, G2_B, G2_C, G2_O, G2_R, G2_G, G2_BL, G2_Z, G2_LEN };
 
+/* growable list of (Gaussian index, 10 image-space gradient terms) */
+typedef struct { int64_t len, cap; int64_t *idx; double *val; } contrib_list_t;
+
+static double *contrib_push(contrib_list_t *L, int64_t idx)
+{
+    if (L->len == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 1024;
+        L->idx = (int64_t *)realloc(L->idx, sizeof(int64_t) * (size_t)L->cap);
+        L->val = (double *)realloc(L->val, sizeof(double) * G2_LEN * (size_t)L->cap);
+    }
+    L->idx[L->len] = idx;
+    double *A = &L->val[L->len * G2_LEN];
+    for (int c = 0; c < G2_LEN; c++) A[c] = 0.0;
+    L->len++;
+    return A;
+}
+
 /* chain rule from the image-space gradients of Gaussian i to its
  * parameters (adjoint of steps 1-4) */
 static void backward_one(const scene_t *S, int64_t i, const gauss_t *g, const double *cam, const double *opt,
@@ -641,13 +658,16 @@ static void backward_one(const scene_t *S, int64_t i, const gauss_t *g, const do
 }
 
 /* exported: gradients of L = sum(dL_rgb . rgb) + sum(dL_depth depth) +
- * sum(dL_alpha alpha) over the full image (brute force), w.r.t. every
- * parameter.  Gradient arrays are overwritten.  If g2d is non-NULL it
+ * sum(dL_alpha alpha) w.r.t. every parameter, over the full image
+ * (pix = NULL, row-major pixels) or over the P listed (px, py) pixels
+ * (dL arrays then indexed by list position); mode 0 brute force, 1 culled
+ * (same result).  Gradient arrays are overwritten.  If g2d is non-NULL it
  * receives the per-Gaussian image-space gradients [n, 10]:
  * (u, v, conic a, b, c, o~, r, g, b, z). */
 int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, const double *tau,
                     const double *beta, const double *period, const double *scale, const double *quat,
-                    const double *opac, const double *sh, const double *cam, const double *opt,
+                    const double *opac, const double *sh, const double *cam, const double *opt, int mode,
+                    int64_t npix, const int32_t *pix,
                     const double *dL_rgb, const double *dL_depth, const double *dL_alpha, double *dmu,
                     double *dvel, double *dtau, double *dbeta, double *dperiod, double *dscale, double *dquat,
                     double *dopac, double *dsh, double *g2d)
@@ -661,13 +681,30 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
     int64_t *order = NULL;
     const int64_t m = depth_order(G, n, &order);
     double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * G2_LEN, sizeof(double));
-    blend_t *bl = (blend_t *)malloc(sizeof(blend_t) * (size_t)(m > 0 ? m : 1));
-    for (int py = 0; py < H; py++)
-        for (int px = 0; px < W; px++) {
-            const int64_t k = (int64_t)py * W + px;
+    const int64_t P = pix ? npix : (int64_t)W * H;
+    /* pixels are split into fixed contiguous chunks, one per thread; each
+     * thread lists its per-(pixel, Gaussian) contributions and the lists are
+     * added in chunk order, so the sums do not depend on scheduling */
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    contrib_list_t *lists = (contrib_list_t *)calloc((size_t)nthreads, sizeof(contrib_list_t));
+#pragma omp parallel num_threads(nthreads)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        const int64_t k0 = P * tid / nthreads, k1 = P * (tid + 1) / nthreads;
+        blend_t *bl = (blend_t *)malloc(sizeof(blend_t) * (size_t)(m > 0 ? m : 1));
+        contrib_list_t *L = &lists[tid];
+        for (int64_t k = k0; k < k1; k++) {
+            const int px = pix ? pix[2 * k] : (int)(k % W);
+            const int py = pix ? pix[2 * k + 1] : (int)(k / W);
             double out[6];
             int32_t nb;
-            composite_pixel(G, order, m, 0, px, py, cam, opt, out, &nb, NULL, bl);
+            composite_pixel(G, order, m, mode == 1, px, py, cam, opt, out, &nb, NULL, bl);
             const double Tfin = out[5];
             const double gC[3] = {dL_rgb[3 * k], dL_rgb[3 * k + 1], dL_rgb[3 * k + 2]};
             const double gD = dL_depth[k], gO = dL_alpha[k];
@@ -677,30 +714,41 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
             for (int j = nb - 1; j >= 0; j--) {
                 const blend_t *e = &bl[j];
                 const gauss_t *g = &G[e->idx];
-                double *A = &acc[e->idx * G2_LEN];
+                double *A = contrib_push(L, e->idx);
                 const double w = e->alpha * e->T;
                 /* d/dalpha_j of each channel */
                 double ga = 0.0;
                 for (int c = 0; c < 3; c++) ga += gC[c] * (g->rgb[c] * e->T - sC[c] / (1.0 - e->alpha));
                 ga += gD * (g->z * e->T - sD / (1.0 - e->alpha));
                 ga += gO * (e->T - sO / (1.0 - e->alpha));
-                for (int c = 0; c < 3; c++) A[G2_R + c] += gC[c] * w;
-                A[G2_Z] += gD * w;
+                for (int c = 0; c < 3; c++) A[G2_R + c] = gC[c] * w;
+                A[G2_Z] = gD * w;
                 if (!e->capped) {
-                    A[G2_O] += ga * e->G;
+                    A[G2_O] = ga * e->G;
                     const double gpow = ga * e->alpha; /* alpha = o~ exp(power) */
                     const double dx = e->dx, dy = e->dy;
-                    A[G2_A] += gpow * (-0.5 * dx * dx);
-                    A[G2_B] += gpow * (-dx * dy);
-                    A[G2_C] += gpow * (-0.5 * dy * dy);
-                    A[G2_U] += gpow * (g->conic[0] * dx + g->conic[1] * dy);
-                    A[G2_V] += gpow * (g->conic[1] * dx + g->conic[2] * dy);
+                    A[G2_A] = gpow * (-0.5 * dx * dx);
+                    A[G2_B] = gpow * (-dx * dy);
+                    A[G2_C] = gpow * (-0.5 * dy * dy);
+                    A[G2_U] = gpow * (g->conic[0] * dx + g->conic[1] * dy);
+                    A[G2_V] = gpow * (g->conic[1] * dx + g->conic[2] * dy);
                 }
                 for (int c = 0; c < 3; c++) sC[c] += g->rgb[c] * w;
                 sD += g->z * w;
                 sO += w;
             }
         }
+        free(bl);
+    }
+    for (int t = 0; t < nthreads; t++) {
+        for (int64_t q = 0; q < lists[t].len; q++) {
+            double *A = &acc[lists[t].idx[q] * G2_LEN];
+            for (int c = 0; c < G2_LEN; c++) A[c] += lists[t].val[q * G2_LEN + c];
+        }
+        free(lists[t].idx);
+        free(lists[t].val);
+    }
+    free(lists);
     memset(dmu, 0, sizeof(double) * 3 * (size_t)n);
     memset(dvel, 0, sizeof(double) * 3 * (size_t)n);
     memset(dtau, 0, sizeof(double) * (size_t)n);
@@ -710,6 +758,7 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
     memset(dquat, 0, sizeof(double) * 4 * (size_t)n);
     memset(dopac, 0, sizeof(double) * (size_t)n);
     memset(dsh, 0, sizeof(double) * 3 * (size_t)K * (size_t)n);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         if (g2d)
             for (int c = 0; c < G2_LEN; c++) g2d[i * G2_LEN + c] = acc[i * G2_LEN + c];
@@ -717,7 +766,6 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
         backward_one(&S, i, &G[i], cam, opt, &acc[i * G2_LEN], dmu, dvel, dtau, dbeta, dperiod, dscale, dquat,
                      dopac, dsh);
     }
-    free(bl);
     free(acc);
     free(order);
     free(G);

@@ -73,7 +73,15 @@ _SIGS = {
     "pvg_render_bwd": (C.c_int, [_P, C.POINTER(Scene), C.POINTER(Camera), C.c_int32, _P, C.POINTER(ImageGrad),
                                  C.POINTER(SceneGrad), _P]),
     "pvg_frame_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pvg_l1_loss": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
+    "pvg_kernel_launches": (C.c_uint64, []),
+    "pvg_profile_enable": (C.c_int, [_P, C.c_int]),
+    "pvg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "pvg_frame_eval_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
 }
+
+STAGES = ("project", "depth_sort", "finalize", "pairs", "tile_sort", "composite", "composite_bwd",
+          "preprocess_bwd")
 
 
 def lib_path() -> str:

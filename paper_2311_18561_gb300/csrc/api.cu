@@ -13,6 +13,7 @@
 //   c  k_composite          images + per-pixel T and last position
 // Backward: k_composite_bwd (image-space gradients per record) and
 // k_preprocess_bwd (parameter gradients).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,11 @@
 #include "pvg_internal.cuh"
 
 using namespace pvg;
+
+namespace pvg {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace pvg
 
 namespace {
 
@@ -77,6 +83,51 @@ pvg_status_t cuda_status(cudaError_t e, const char *what) {
 
 #define PVG_CUDA(expr) PVG_TRY(cuda_status((expr), #expr))
 
+// CUDA-event timing of the stages of each call, on the call's stream.
+struct StageTimer {
+    bool on = false;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> pending;
+    cudaEvent_t open[PVG_NUM_STAGES] = {};
+    cudaEvent_t get() {
+        cudaEvent_t e = nullptr;
+        if (!pool.empty()) {
+            e = pool.back();
+            pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+        }
+        return e;
+    }
+    void begin(int st, cudaStream_t s) {
+        if (!on) return;
+        open[st] = get();
+        if (open[st]) cudaEventRecord(open[st], s);
+    }
+    void end(int st, cudaStream_t s) {
+        if (!on || !open[st]) return;
+        cudaEvent_t b = get();
+        if (!b) return;
+        cudaEventRecord(b, s);
+        pending.push_back({st, open[st], b});
+        open[st] = nullptr;
+    }
+    void destroy() {
+        for (auto &r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+        pending.clear();
+        pool.clear();
+    }
+};
+
 }  // namespace
 
 struct pvg_frame {
@@ -88,6 +139,7 @@ struct pvg_frame {
     DevBuf pair_vals;           // [K]
     DevBuf ranges;              // [tiles]
     DevBuf pix_T, pix_last;     // [pixels]
+    DevBuf pix_neval;           // [pixels]
     DevBuf g2d;                 // [NV * 10]
     std::vector<ViewDesc> views;
     uint32_t n_items = 0, total_tiles = 0, total_pix = 0, pair_capacity = 0;
@@ -110,6 +162,7 @@ struct pvg_ctx {
     DevBuf temp;
     uint32_t *h_pinned = nullptr;
     pvg_frame *own_frame = nullptr;
+    StageTimer timer;
 };
 
 // ------------------------------------------------------------------ misc
@@ -172,7 +225,7 @@ extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
     for (DevBuf *b : {&f->counters, &f->sgid, &f->szkey, &f->rec, &f->rect, &f->vis_cnt, &f->pair_vals,
-                      &f->ranges, &f->pix_T, &f->pix_last, &f->g2d})
+                      &f->ranges, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
     delete f;
@@ -213,6 +266,7 @@ extern "C" void pvg_destroy(pvg_ctx_t *x) {
         release(*b);
     if (x->h_pinned) cudaFreeHost(x->h_pinned);
     pvg_frame_destroy(x->own_frame);
+    x->timer.destroy();
     delete x;
 }
 
@@ -327,6 +381,7 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     PVG_TRY(ensure(f->ranges, sizeof(uint2) * tiles));
     PVG_TRY(ensure(f->pix_T, sizeof(float) * pix));
     PVG_TRY(ensure(f->pix_last, sizeof(uint32_t) * pix));
+    PVG_TRY(ensure(f->pix_neval, sizeof(uint32_t) * pix));
     uint32_t pair_cap;
     if (x->cfg.sync_sizes) {
         pair_cap = (uint32_t)(f->pair_vals.bytes / sizeof(uint32_t));
@@ -372,10 +427,15 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.ranges = ptr<uint2>(f->ranges);
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
+    p.pix_neval = ptr<uint32_t>(f->pix_neval);
+    StageTimer &tm = x->timer;
 
     if (NV > 0) {
         // (a) project + count, (b) depth sort of the visible items
+        tm.begin(PVG_STAGE_PROJECT, s);
         launch_project_count(p, s);
+        tm.end(PVG_STAGE_PROJECT, s);
+        tm.begin(PVG_STAGE_DEPTH_SORT, s);
         compact_visible(p, p.szkey, p.sgid, x->temp.p, s);
         bool in_alt = false;
         radix_sort_pairs(p.szkey, p.sgid, ptr<uint32_t>(x->alt_keys), ptr<uint32_t>(x->alt_vals), &p.counters[0], NV,
@@ -384,8 +444,12 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
             PVG_CUDA(cudaMemcpyAsync(p.szkey, x->alt_keys.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
             PVG_CUDA(cudaMemcpyAsync(p.sgid, x->alt_vals.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
         }
+        tm.end(PVG_STAGE_DEPTH_SORT, s);
         // (a) records in depth order, (b) pair count
+        tm.begin(PVG_STAGE_FINALIZE, s);
         launch_finalize(p, s);
+        tm.end(PVG_STAGE_FINALIZE, s);
+        tm.begin(PVG_STAGE_PAIRS, s);
         p.pair_capacity = x->cfg.sync_sizes ? 0xffffffffu : pair_cap;
         scan_count_pairs(p, x->temp.p, s);
         if (x->cfg.sync_sizes) {
@@ -414,17 +478,22 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
         p.pair_keys = E_keys;
         p.pair_vals = E_vals;
         scan_emit_pairs(p, x->temp.p, s);
+        tm.end(PVG_STAGE_PAIRS, s);
+        tm.begin(PVG_STAGE_TILE_SORT, s);
         bool t_alt = false;
         radix_sort_pairs(E_keys, E_vals, F_keys, F_vals, &p.counters[1], pair_cap, 0, tbits, x->temp.p, s, &t_alt);
         p.pair_keys = t_alt ? F_keys : E_keys;
         p.pair_vals = ptr<uint32_t>(f->pair_vals);
         launch_ranges(p, s);
+        tm.end(PVG_STAGE_TILE_SORT, s);
     } else {
         PVG_CUDA(cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * tiles, s));
     }
     f->pair_capacity = pair_cap;
     p.pair_vals = ptr<uint32_t>(f->pair_vals);
+    tm.begin(PVG_STAGE_COMPOSITE, s);
     launch_composite(p, s);
+    tm.end(PVG_STAGE_COMPOSITE, s);
     PVG_CUDA(cudaGetLastError());
     f->valid = true;
     return PVG_OK;
@@ -490,9 +559,15 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.g2d = ptr<float>(f->g2d);
+    StageTimer &tm = x->timer;
+    tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
+    note_launch();
     k_zero_g2d<<<152 * 4, 256, 0, s>>>(p.g2d, &p.counters[0]);
     launch_composite_bwd(p, s);
+    tm.end(PVG_STAGE_COMPOSITE_BWD, s);
+    tm.begin(PVG_STAGE_PREPROCESS_BWD, s);
     launch_preprocess_bwd(p, n_views > 1, s);
+    tm.end(PVG_STAGE_PREPROCESS_BWD, s);
     PVG_CUDA(cudaGetLastError());
     return PVG_OK;
 }
@@ -538,8 +613,65 @@ extern "C" pvg_status_t pvg_frame_export(pvg_frame_t *f, uint32_t *sorted_gid, u
         PVG_CUDA(cudaMemcpyAsync(pair_vals, f->pair_vals.p, 4 * K, cudaMemcpyDeviceToDevice, s));
     if (ranges && f->total_tiles)
         PVG_CUDA(cudaMemcpyAsync(ranges, f->ranges.p, 8 * (size_t)f->total_tiles, cudaMemcpyDeviceToDevice, s));
-    if (rect && M) k_export_rect<<<152, 256, 0, s>>>(ptr<uint2>(f->rect), ptr<uint32_t>(f->counters), rect);
+    if (rect && M) {
+        note_launch();
+        k_export_rect<<<152, 256, 0, s>>>(ptr<uint2>(f->rect), ptr<uint32_t>(f->counters), rect);
+    }
     PVG_CUDA(cudaGetLastError());
     PVG_CUDA(cudaStreamSynchronize(s));
     return PVG_OK;
+}
+
+// ------------------------------------------------------------------ measurement
+
+extern "C" uint64_t pvg_kernel_launches(void) { return pvg::g_launches.load(); }
+
+extern "C" pvg_status_t pvg_profile_enable(pvg_ctx_t *x, int on) {
+    if (!x) return PVG_ERR_INVALID;
+    x->timer.on = on != 0;
+    return PVG_OK;
+}
+
+extern "C" pvg_status_t pvg_profile_read(pvg_ctx_t *x, double *ms, int64_t *calls) {
+    if (!x || !ms || !calls) return PVG_ERR_INVALID;
+    for (int k = 0; k < PVG_NUM_STAGES; k++) {
+        ms[k] = 0.0;
+        calls[k] = 0;
+    }
+    for (auto &r : x->timer.pending) {
+        PVG_CUDA(cudaEventSynchronize(r.b));
+        float e = 0.f;
+        PVG_CUDA(cudaEventElapsedTime(&e, r.a, r.b));
+        ms[r.stage] += e;
+        calls[r.stage] += 1;
+        x->timer.pool.push_back(r.a);
+        x->timer.pool.push_back(r.b);
+    }
+    x->timer.pending.clear();
+    return PVG_OK;
+}
+
+__global__ static void k_sum_u32(const uint32_t *v, uint32_t n, unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += v[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+extern "C" pvg_status_t pvg_frame_eval_count(pvg_frame_t *f, int64_t *evals) {
+    if (!f || !evals || !f->valid) return PVG_ERR_INVALID;
+    DevBuf tmp;
+    PVG_TRY(ensure(tmp, sizeof(unsigned long long)));
+    unsigned long long h = 0;
+    cudaStream_t s = f->stream;
+    pvg_status_t st = cuda_status(cudaMemsetAsync(tmp.p, 0, sizeof(h), s), "memset");
+    if (st == PVG_OK) {
+        note_launch();
+        k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, ptr<unsigned long long>(tmp));
+        st = cuda_status(cudaMemcpyAsync(&h, tmp.p, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+    }
+    if (st == PVG_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
+    release(tmp);
+    *evals = (int64_t)h;
+    return st;
 }

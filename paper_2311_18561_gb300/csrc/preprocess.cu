@@ -453,14 +453,17 @@ int grid_for(uint32_t n) {
 }  // namespace
 
 void launch_project_count(const Params &p, cudaStream_t s) {
+    note_launch();
     k_project_count<<<grid_for(p.n_items), 256, 0, s>>>(p);
 }
 
 void launch_finalize(const Params &p, cudaStream_t s) {
+    note_launch();
     k_finalize<<<grid_for(p.n_items), 256, 0, s>>>(p);
 }
 
 void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s) {
+    note_launch();
     k_preprocess_bwd<<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic);
 }
 

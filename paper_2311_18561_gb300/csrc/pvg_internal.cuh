@@ -73,7 +73,8 @@ struct Params {
     uint32_t *pair_vals;     // [K]
     uint2 *ranges;           // [total_tiles]
     float *pix_T;            // [sum HW]
-    uint32_t *pix_last;      // [sum HW]
+    uint32_t *pix_last;      // [sum HW] list position after the last blend
+    uint32_t *pix_neval;     // [sum HW] list entries evaluated (stop included)
     // backward
     float *g2d;              // [M*10]
 };
@@ -117,6 +118,8 @@ __device__ __forceinline__ float falloff_exp2(float ap, float bp, float cp, floa
 
 // host-side launchers (one translation unit each)
 namespace pvg {
+// counts every kernel launch of the library (reported by pvg_kernel_launches)
+void note_launch();
 cudaError_t set_sh_constants();
 void launch_project_count(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);

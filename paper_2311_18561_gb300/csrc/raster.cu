@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(TW *TH) k_composite(Params P) {
     const uint2 r = P.ranges[tile];
 
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, O = 0.f;
-    uint32_t last = 0;
+    uint32_t last = 0, neval = r.y - r.x;
     bool done = !inside;
     for (uint32_t base = r.x; base < r.y; base += BLOCK) {
         if (__syncthreads_count(!done) == 0) break;
@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(TW *TH) k_composite(Params P) {
                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
                 if (Tn < kTStop) {
                     done = true;
+                    neval = base + k + 1 - r.x;
                     break;
                 }
                 const float w = __fmul_rn(alpha, T);
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(TW *TH) k_composite(Params P) {
         if (P.pix_T) {
             P.pix_T[V.pix_base + pix] = T;
             P.pix_last[V.pix_base + pix] = last;
+            P.pix_neval[V.pix_base + pix] = neval;
         }
     }
 }
@@ -222,12 +224,14 @@ __global__ void __launch_bounds__(TW *TH) k_composite_bwd(Params P) {
 template <int TW, int TH>
 void launch_fwd_t(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0) return;
+    note_launch();
     k_composite<TW, TH><<<p.total_tiles, TW * TH, 0, s>>>(p);
 }
 
 template <int TW, int TH>
 void launch_bwd_t(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0) return;
+    note_launch();
     k_composite_bwd<TW, TH><<<p.total_tiles, TW * TH, 0, s>>>(p);
 }
 

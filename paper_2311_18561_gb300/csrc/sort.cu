@@ -346,8 +346,11 @@ void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, vo
     TempLayout t = temp_layout(temp);
     CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, p.n_items};
     const int G = scan_blocks(p.n_items);
+    note_launch();
     k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    note_launch();
     k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[0], 0xffffffffu, nullptr);
+    note_launch();
     k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
 }
 
@@ -364,8 +367,11 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32
         const uint32_t *vi = alt ? vals_alt : vals;
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
+        note_launch();
         k_radix_upsweep<<<G, kSortThreads, 0, s>>>(ki, d_count, capacity, b, mask, t.hist);
+        note_launch();
         k_radix_scan<<<1, 1024, 0, s>>>(t.hist, kRadix * G);
+        note_launch();
         k_radix_downsweep<<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist);
         alt = !alt;
         b += nb;
@@ -380,7 +386,9 @@ void scan_count_pairs(const Params &p, void *temp, cudaStream_t s) {
     EmitF f{&p.counters[0], p.vis_cnt, p.rect, p.sgid, p.views, p.n_views, p.pair_keys, p.pair_vals,
             p.pair_capacity};
     const int G = scan_blocks(p.n_items);
+    note_launch();
     k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    note_launch();
     k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[1], p.pair_capacity, &p.counters[2]);
 }
 
@@ -389,11 +397,13 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     EmitF f{&p.counters[0], p.vis_cnt, p.rect, p.sgid, p.views, p.n_views, p.pair_keys, p.pair_vals,
             p.pair_capacity};
     const int G = scan_blocks(p.n_items);
+    note_launch();
     k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
 }
 
 void launch_ranges(const Params &p, cudaStream_t s) {
     cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * (size_t)p.total_tiles, s);
+    note_launch();
     k_ranges<<<152 * 8, 256, 0, s>>>(p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
 }
 

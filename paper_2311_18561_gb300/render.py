@@ -229,3 +229,42 @@ def render_differentiable(params, cam, renderer=None):
     """params: dict of tensors (may require grad).  Returns rgb, depth, alpha."""
     r = renderer or default_renderer()
     return PVGRender.apply(cam, r, *[params[k] for k in PARAM_NAMES])
+
+
+def l1_loss(pred, target, dl=None, loss=None, scale=None, stream=None):
+    """loss = scale * sum|pred - target| (default scale = 1/numel) and
+    dl = scale * sign(pred - target), computed by ``pvg_l1_loss``."""
+    if pred.shape != target.shape or not pred.is_contiguous() or not target.is_contiguous():
+        raise ValueError("pred and target must be contiguous tensors of one shape")
+    n = pred.numel()
+    if dl is None:
+        dl = torch.empty_like(pred)
+    if loss is None:
+        loss = torch.empty(1, device=pred.device, dtype=torch.float32)
+    s = 1.0 / max(n, 1) if scale is None else float(scale)
+    st = abi.lib().pvg_l1_loss(pred.data_ptr(), target.data_ptr(), n, s, dl.data_ptr(), loss.data_ptr(),
+                              _stream_ptr(stream))
+    abi.check(st, "pvg_l1_loss")
+    return loss, dl
+
+
+def kernel_launches() -> int:
+    return int(abi.lib().pvg_kernel_launches())
+
+
+def profile_enable(renderer, on=True):
+    abi.check(abi.lib().pvg_profile_enable(renderer.handle, 1 if on else 0), "pvg_profile_enable")
+
+
+def profile_read(renderer):
+    """{stage: (total ms, calls)} since the last read (synchronises)."""
+    ms = (C.c_double * 8)()
+    calls = (C.c_int64 * 8)()
+    abi.check(abi.lib().pvg_profile_read(renderer.handle, ms, calls), "pvg_profile_read")
+    return {name: (float(ms[k]), int(calls[k])) for k, name in enumerate(abi.STAGES)}
+
+
+def eval_count(frame) -> int:
+    e = C.c_int64()
+    abi.check(abi.lib().pvg_frame_eval_count(frame.handle, C.byref(e)), "pvg_frame_eval_count")
+    return int(e.value)

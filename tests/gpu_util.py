@@ -18,7 +18,7 @@ def to_numpy_images(out):
                 alpha=out["alpha"].cpu().numpy().astype(np.float64))
 
 
-def compare_to_oracle(got, ref, pixels=None, max_flag_frac=0.01):
+def compare_to_oracle(got, ref, pixels=None, max_flag_frac=0.05):
     """got: dict of numpy arrays [H,W,(3)] or [P,(3)] if pixels given."""
     flag = ref["flag"] != 0
     e_rgb = np.abs(got["rgb"] - ref["rgb"]).max(axis=-1)

@@ -198,3 +198,27 @@ def test_backward_matches_finite_differences(degree):
             assert gflat[idx] == pytest.approx(fd[1], rel=2e-4, abs=2e-5), (name, idx)
             checked += 1
     assert checked >= 60
+
+
+def test_backward_on_a_pixel_list_equals_masked_full_image():
+    """The pixel-list (culled) backward is the full-image backward with the
+    upstream gradient zero outside the list."""
+    rng = np.random.default_rng(11)
+    sc = synth.make_fd_scene(seed=5, n=80, sh_degree=2)
+    cam = synth.fd_camera(24, 20, t=0.3)
+    H, W = cam["height"], cam["width"]
+    pix = np.stack([rng.integers(0, W, 60), rng.integers(0, H, 60)], axis=1)
+    pix = np.unique(pix, axis=0)
+    w_rgb = rng.normal(size=(len(pix), 3))
+    w_d = rng.normal(size=len(pix))
+    w_a = rng.normal(size=len(pix))
+    part = oracle.render_bwd(sc, cam, w_rgb, w_d, w_a, mode="culled", pixels=pix)
+    full_rgb = np.zeros((H, W, 3))
+    full_d = np.zeros((H, W))
+    full_a = np.zeros((H, W))
+    full_rgb[pix[:, 1], pix[:, 0]] = w_rgb
+    full_d[pix[:, 1], pix[:, 0]] = w_d
+    full_a[pix[:, 1], pix[:, 0]] = w_a
+    full = oracle.render_bwd(sc, cam, full_rgb, full_d, full_a)
+    for k in full:
+        np.testing.assert_allclose(part[k], full[k], rtol=1e-10, atol=1e-12)
