@@ -194,6 +194,22 @@ pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_
                             const pvg_scene_grad_t *grads, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* sorting                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Stable LSD radix sort of n (key, value) pairs by bits [begin_bit,
+ * end_bit) of the key, in place, on `stream` -- the sort the renderer uses
+ * for "sorting the Gaussians according to their depth in camera space"
+ * (Sec. 3.1): float32 depth bits of the visible Gaussians, then tile ids
+ * of the (tile, Gaussian) pairs.  keys / vals: caller-owned device arrays
+ * of n uint32 each.  Pairs with equal sort bits keep their input order.
+ * Scratch (ping-pong buffers of n pairs, digit histograms) belongs to
+ * `ctx` and grows on demand.  PVG_ERR_INVALID if n < 0, n >= 2^32, a
+ * pointer is NULL while n > 0, or not 0 <= begin_bit < end_bit <= 32. */
+pvg_status_t pvg_sort_pairs(pvg_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int32_t begin_bit,
+                            int32_t end_bit, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* loss                                                                */
 /* ------------------------------------------------------------------ */
 

@@ -160,6 +160,7 @@ struct pvg_ctx {
     DevBuf alt_keys, alt_vals;   // [NV] depth sort ping-pong
     DevBuf pair_keys, pair_keys2, pair_vals2;  // [K]
     DevBuf temp;
+    DevBuf sort_n;               // u32: element count of pvg_sort_pairs
     uint32_t *h_pinned = nullptr;
     pvg_frame *own_frame = nullptr;
     StageTimer timer;
@@ -262,7 +263,7 @@ extern "C" void pvg_destroy(pvg_ctx_t *x) {
     if (!x) return;
     cudaDeviceSynchronize();
     for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->alt_keys, &x->alt_vals, &x->pair_keys,
-                      &x->pair_keys2, &x->pair_vals2, &x->temp})
+                      &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n})
         release(*b);
     if (x->h_pinned) cudaFreeHost(x->h_pinned);
     pvg_frame_destroy(x->own_frame);
@@ -674,4 +675,31 @@ extern "C" pvg_status_t pvg_frame_eval_count(pvg_frame_t *f, int64_t *evals) {
     release(tmp);
     *evals = (int64_t)h;
     return st;
+}
+
+// ------------------------------------------------------------------ sorting
+
+__global__ static void k_store_u32(uint32_t *dst, uint32_t v) { *dst = v; }
+
+extern "C" pvg_status_t pvg_sort_pairs(pvg_ctx_t *x, uint32_t *keys, uint32_t *vals, int64_t n, int32_t begin_bit,
+                                       int32_t end_bit, void *stream_) {
+    if (!x || n < 0 || n >= (int64_t)0xffffffffLL || begin_bit < 0 || end_bit > 32 || begin_bit >= end_bit)
+        return PVG_ERR_INVALID;
+    if (n == 0) return PVG_OK;
+    if (!keys || !vals) return PVG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream_;
+    PVG_TRY(ensure(x->alt_keys, sizeof(uint32_t) * (size_t)n));
+    PVG_TRY(ensure(x->alt_vals, sizeof(uint32_t) * (size_t)n));
+    PVG_TRY(ensure(x->sort_n, sizeof(uint32_t)));
+    note_launch();
+    k_store_u32<<<1, 1, 0, s>>>(ptr<uint32_t>(x->sort_n), (uint32_t)n);
+    bool in_alt = false;
+    radix_sort_pairs(keys, vals, ptr<uint32_t>(x->alt_keys), ptr<uint32_t>(x->alt_vals), ptr<uint32_t>(x->sort_n),
+                     (uint32_t)n, begin_bit, end_bit, x->temp.p, s, &in_alt);
+    if (in_alt) {
+        PVG_CUDA(cudaMemcpyAsync(keys, x->alt_keys.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        PVG_CUDA(cudaMemcpyAsync(vals, x->alt_vals.p, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    PVG_CUDA(cudaGetLastError());
+    return PVG_OK;
 }

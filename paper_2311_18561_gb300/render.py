@@ -268,3 +268,14 @@ def eval_count(frame) -> int:
     e = C.c_int64()
     abi.check(abi.lib().pvg_frame_eval_count(frame.handle, C.byref(e)), "pvg_frame_eval_count")
     return int(e.value)
+
+
+def sort_pairs(renderer, keys, vals, begin_bit=0, end_bit=32, stream=None):
+    """Stable in-place radix sort of int32/uint32 CUDA tensors ``keys`` /
+    ``vals`` by key bits [begin_bit, end_bit) (``pvg_sort_pairs``)."""
+    if keys.shape != vals.shape or keys.dim() != 1 or not keys.is_contiguous() or not vals.is_contiguous():
+        raise ValueError("keys and vals must be contiguous 1-D tensors of one length")
+    st = abi.lib().pvg_sort_pairs(renderer.handle, keys.data_ptr(), vals.data_ptr(), keys.numel(), int(begin_bit),
+                                  int(end_bit), _stream_ptr(stream))
+    abi.check(st, "pvg_sort_pairs")
+    return keys, vals
