@@ -209,6 +209,26 @@ pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_
 pvg_status_t pvg_sort_pairs(pvg_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int64_t n, int32_t begin_bit,
                             int32_t end_bit, void *stream);
 
+/* The sort of pvg_sort_pairs for callers that cannot allocate device
+ * memory (code running during CUDA-graph capture, real-time or callback
+ * threads where cudaMalloc may block on a device-wide synchronisation,
+ * hosts that forbid allocations outside their own pool).  The paper has no
+ * counterpart; this is an interface convenience.  It needs no context and
+ * calls no cudaMalloc / cudaFree or allocating routine: its scratch is a
+ * set of fixed device arrays inside this library (about 8.6 MiB, held on
+ * every GPU that loads the library until the process exits).
+ *   - n must be <= 1,048,576 (2^20); larger n returns PVG_ERR_INVALID and
+ *     enqueues nothing.  Other arguments as for pvg_sort_pairs.
+ *   - The first call on a device looks up that device's array addresses
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - All calls share the arrays and leave the last call's contents in
+ *     them: calls that overlap on the GPU (different streams or devices'
+ *     threads racing on one device) race and corrupt each other's results;
+ *     serialise them. */
+pvg_status_t pvg_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, int32_t begin_bit,
+                                    int32_t end_bit, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* loss                                                                */
 /* ------------------------------------------------------------------ */

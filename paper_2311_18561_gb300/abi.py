@@ -74,6 +74,7 @@ _SIGS = {
                                  C.POINTER(SceneGrad), _P]),
     "pvg_frame_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "pvg_sort_pairs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
+    "pvg_sort_pairs_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
     "pvg_l1_loss": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
     "pvg_kernel_launches": (C.c_uint64, []),
     "pvg_profile_enable": (C.c_int, [_P, C.c_int]),
