@@ -37,11 +37,11 @@ FRAME = 25
 # name: (Gaussians, width, height, focal or None (hfov 50 deg), description)
 WORKLOADS = {
     "urban": (1_500_000, 1920, 1280, None,
-              "urban scene, 1.5M Gaussians, SH-3, 1920x1280, street-path frame 25 (t=25/49), 16x16 tiles: "
+              "urban scene, 1.5M Gaussians, SH-3, 1920x1280, street-path frame 25 (t=25/49): "
               "forward render + L1 loss + backward"),
     "training": (1_000_000, 1242, 375, 720.0,
                  "training config: urban-distribution scene, 1M Gaussians, SH-3, 1242x375 (f=720), "
-                 "street-path frame 25, 16x16 tiles: forward render + L1 loss + backward"),
+                 "street-path frame 25: forward render + L1 loss + backward"),
 }
 N_GAUSS, W_PIX, H_PIX, FOCAL, WORKLOAD = WORKLOADS["urban"]
 
@@ -74,6 +74,7 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="urban")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default="", help="tile_w,tile_h,pixels_per_thread (default: autotune)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall-clock budget of the oracle's bounded sample")
     return ap.parse_args()
@@ -187,7 +188,14 @@ def run_ours(args):
     st = R.scene_to_device(scene, dev)
     target_host = torch.from_numpy(synth.random_image(H_PIX, W_PIX, seed=1)).pin_memory()
     target = target_host.to(dev)
-    r = R.Renderer()
+    if args.tile:
+        tw, th, px = (int(v) for v in args.tile.split(","))
+        best, table = (tw, th, px), None
+    else:
+        from paper_2311_18561_gb300 import tune
+
+        best, table = tune.tune(st, [cam], backward=True, use_cache=False)
+    r = R.Renderer(tile=best[:2], pixels_per_thread=best[2])
     fr = R.Frame()
     outs = r.alloc_images([cam])
     grads = {k: torch.empty_like(st[k]) for k in R.PARAM_NAMES}
@@ -244,7 +252,7 @@ def run_ours(args):
 
     M, K, ov = fr.stats()
     r.forward(st, [cam], outs=outs, frame=fr)
-    E = R.eval_count(fr)
+    E = R.eval_count(r, fr)
     ms_step = step_ms / args.steps
     t = torch.tensor([ms_step, fwd_ms], device=dev)
     if world > 1:
@@ -298,10 +306,13 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded urban-shaped PVG scene, random-init parameters)",
         "config": {"workload": WORKLOAD, "gaussians": N_GAUSS, "width": W_PIX, "height": H_PIX,
-                   "name": args.workload, "sh_degree": 3, "tile": "16x16",
+                   "name": args.workload, "sh_degree": 3,
+                   "tile": "%dx%d, %d px/thread (%s)" % (best[0], best[1], best[2],
+                                                         "given" if table is None else "autotuned"),
                    "l2": "flushed before every step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "fwd_bwd_step_ms": ms_step,
+        "autotune_ms": None if table is None else {"%dx%dx%d" % k: round(v, 4) for k, v in table.items()},
         "render_fwd": {"ms": fwd_ms, "mpix_s": world * mpix / (fwd_ms * 1e-3)},
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "visible": M, "pairs": K, "evals": E, "overflow": ov,

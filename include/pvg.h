@@ -136,14 +136,18 @@ typedef struct pvg_ctx pvg_ctx_t;
 typedef struct pvg_frame pvg_frame_t;
 
 typedef struct {
-    int32_t tile_w, tile_h; /* 16x16 by default; supported: 8x8, 16x8, 16x16, 32x8, 32x16 */
+    int32_t tile_w, tile_h; /* tile shape, 16x16 by default */
     int32_t sync_sizes;     /* 1 (default): pvg_render_fwd reads the pair count
                              * back to the host once per call and grows the
                              * workspace; 0: never synchronises, uses the
                              * capacities below; pairs beyond the capacity are
                              * dropped and pvg_frame_stats reports the
                              * overflow (the images are then incomplete) */
-    int32_t reserved0;
+    int32_t pixels_per_thread; /* compositing pixels per thread (1, 2 or 4; 0 = 1).
+                             * Supported (tile_w, tile_h, pixels_per_thread):
+                             * (16,16,1|2|4) (8,8,1|2) (16,8,1|2) (32,8,1)
+                             * (32,16,1|2|4) (32,32,4) (16,32,4).  Images do not
+                             * depend on the choice (bit-identical). */
     int64_t pair_capacity;  /* pairs per frame when sync_sizes = 0 */
     float dilation;         /* EWA low-pass h in px^2 (default 0.3) */
     float fov_clamp;        /* J clamp factor (default 1.3) */
@@ -268,17 +272,20 @@ pvg_status_t pvg_profile_enable(pvg_ctx_t *ctx, int on);
  * forgets them. */
 pvg_status_t pvg_profile_read(pvg_ctx_t *ctx, double *ms, int64_t *calls);
 
-/* Sum over all pixels of the last forward into `frame` of the number of
- * list entries each pixel evaluated (up to and including the one that
- * stopped it): the compositing work E.  Synchronises the frame's stream. */
-pvg_status_t pvg_frame_eval_count(pvg_frame_t *frame, int64_t *evals);
+/* The compositing work E of the last forward into `frame`: summed over all
+ * pixels, the number of entries of the pixel's tile list whose footprint
+ * box contains the pixel, up to and including the entry that stopped it.
+ * Re-runs the compositor in a counting mode (writes no image) with `ctx`'s
+ * scratch; synchronises the frame's stream. */
+pvg_status_t pvg_frame_eval_count(pvg_ctx_t *ctx, pvg_frame_t *frame, int64_t *evals);
 
 /* Copy device-side intermediate results of the last forward into
  * caller-owned DEVICE buffers (any may be NULL), for parity testing:
  *   sorted_gid [n_visible]   (view * N + index) in (view-major via tiles, depth, index) order
  *   depth_key  [n_visible]   float32 bits of the camera depth, same order
  *   rect       [n_visible*4] tile rectangle (tx0, ty0, tx1, ty1), half-open, int32
- *   records    [n_visible*12] u, v, conic a, b, c, o~, z, 0, r, g, b, 0 (float32)
+ *   records    [n_visible*12] u, v, conic a, b, c, o~, z, hx, r, g, b, hy (float32;
+ *                            hx, hy = footprint half extents in pixels)
  *   pair_vals  [n_pairs]     position in the depth order, sorted by (tile, depth, index)
  *   ranges     [total_tiles*2] [start, end) per tile, tiles of view 0 first
  * Synchronises the frame's stream. */

@@ -52,7 +52,7 @@ class SceneGrad(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("sync_sizes", C.c_int32),
-                ("reserved0", C.c_int32), ("pair_capacity", C.c_int64), ("dilation", C.c_float),
+                ("pixels_per_thread", C.c_int32), ("pair_capacity", C.c_int64), ("dilation", C.c_float),
                 ("fov_clamp", C.c_float), ("reserved", C.c_float * 6)]
 
 
@@ -79,7 +79,7 @@ _SIGS = {
     "pvg_kernel_launches": (C.c_uint64, []),
     "pvg_profile_enable": (C.c_int, [_P, C.c_int]),
     "pvg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
-    "pvg_frame_eval_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "pvg_frame_eval_count": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
 }
 
 STAGES = ("project", "depth_sort", "finalize", "pairs", "tile_sort", "composite", "composite_bwd",
@@ -113,10 +113,12 @@ def check(status, where):
         raise PVGError(status, where)
 
 
-def config(tile=(16, 16), sync_sizes=True, pair_capacity=1 << 24, dilation=0.3, fov_clamp=1.3) -> Config:
+def config(tile=(16, 16), sync_sizes=True, pair_capacity=1 << 24, dilation=0.3, fov_clamp=1.3,
+           pixels_per_thread=1) -> Config:
     c = Config()
     lib().pvg_config_default(C.byref(c))
     c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
+    c.pixels_per_thread = int(pixels_per_thread)
     c.sync_sizes = 1 if sync_sizes else 0
     c.pair_capacity = int(pair_capacity)
     c.dilation = float(dilation)

@@ -134,6 +134,7 @@ struct pvg_frame {
     int device = -1;
     DevBuf counters;            // u32 [4]: M, K, overflow
     DevBuf sgid, szkey;         // [NV]
+    DevBuf inv;                 // [NV] depth position per item
     DevBuf rec;                 // [NV * 3] float4
     DevBuf rect, vis_cnt;       // [NV]
     DevBuf pair_vals;           // [K]
@@ -143,7 +144,7 @@ struct pvg_frame {
     DevBuf g2d;                 // [NV * 10]
     std::vector<ViewDesc> views;
     uint32_t n_items = 0, total_tiles = 0, total_pix = 0, pair_capacity = 0;
-    int tile_w = 0, tile_h = 0;
+    int tile_w = 0, tile_h = 0, px = 1;
     int64_t n = -1;
     int sh_degree = -1;
     float dilation = 0.f;
@@ -159,6 +160,8 @@ struct pvg_ctx {
     DevBuf item_cnt, item_zkey;  // [NV]
     DevBuf alt_keys, alt_vals;   // [NV] depth sort ping-pong
     DevBuf pair_keys, pair_keys2, pair_vals2;  // [K]
+    DevBuf vis_off;              // [NV]
+    DevBuf chunk_start;          // [K / 2048 + 1]
     DevBuf temp;
     DevBuf sort_n;               // u32: element count of pvg_sort_pairs
     uint32_t *h_pinned = nullptr;
@@ -191,6 +194,7 @@ extern "C" void pvg_config_default(pvg_config_t *cfg) {
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->tile_w = 16;
     cfg->tile_h = 16;
+    cfg->pixels_per_thread = 1;
     cfg->sync_sizes = 1;
     cfg->pair_capacity = 1 << 24;
     cfg->dilation = 0.3f;
@@ -198,7 +202,8 @@ extern "C" void pvg_config_default(pvg_config_t *cfg) {
 }
 
 static pvg_status_t check_config(const pvg_config_t *c) {
-    if (!composite_supported(c->tile_w, c->tile_h)) return PVG_ERR_INVALID;
+    const int px = c->pixels_per_thread ? c->pixels_per_thread : 1;
+    if (!composite_supported(c->tile_w, c->tile_h, px)) return PVG_ERR_INVALID;
     if (!(c->dilation >= 0.f) || !(c->fov_clamp > 0.f)) return PVG_ERR_INVALID;
     if (!c->sync_sizes && (c->pair_capacity <= 0 || c->pair_capacity > 0xfffffff0LL)) return PVG_ERR_INVALID;
     return PVG_OK;
@@ -225,7 +230,7 @@ extern "C" pvg_status_t pvg_frame_create(pvg_frame_t **frame) {
 extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
-    for (DevBuf *b : {&f->counters, &f->sgid, &f->szkey, &f->rec, &f->rect, &f->vis_cnt, &f->pair_vals,
+    for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->rect, &f->vis_cnt, &f->pair_vals,
                       &f->ranges, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
@@ -263,7 +268,7 @@ extern "C" void pvg_destroy(pvg_ctx_t *x) {
     if (!x) return;
     cudaDeviceSynchronize();
     for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->alt_keys, &x->alt_vals, &x->pair_keys,
-                      &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n})
+                      &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n, &x->vis_off, &x->chunk_start})
         release(*b);
     if (x->h_pinned) cudaFreeHost(x->h_pinned);
     pvg_frame_destroy(x->own_frame);
@@ -374,7 +379,9 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     PVG_TRY(ensure(x->item_zkey, sizeof(uint32_t) * NV));
     PVG_TRY(ensure(x->alt_keys, sizeof(uint32_t) * NV));
     PVG_TRY(ensure(x->alt_vals, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(x->vis_off, sizeof(uint32_t) * NV));
     PVG_TRY(ensure(f->sgid, sizeof(uint32_t) * NV));
+    PVG_TRY(ensure(f->inv, sizeof(uint32_t) * NV));
     PVG_TRY(ensure(f->szkey, sizeof(uint32_t) * NV));
     PVG_TRY(ensure(f->rec, sizeof(float4) * 3 * (size_t)NV));
     PVG_TRY(ensure(f->rect, sizeof(uint2) * NV));
@@ -392,6 +399,7 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
         PVG_TRY(ensure(x->pair_keys, sizeof(uint32_t) * (size_t)pair_cap));
         PVG_TRY(ensure(x->pair_keys2, sizeof(uint32_t) * (size_t)pair_cap));
         PVG_TRY(ensure(x->pair_vals2, sizeof(uint32_t) * (size_t)pair_cap));
+        PVG_TRY(ensure(x->chunk_start, sizeof(uint32_t) * emit_chunks(pair_cap)));
     }
     f->views = views;
     f->n_items = NV;
@@ -399,6 +407,7 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     f->total_pix = pix;
     f->tile_w = x->cfg.tile_w;
     f->tile_h = x->cfg.tile_h;
+    f->px = x->cfg.pixels_per_thread ? x->cfg.pixels_per_thread : 1;
     f->n = scene->n;
     f->sh_degree = scene->sh_degree;
     f->dilation = x->cfg.dilation;
@@ -412,8 +421,10 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     std::memset(&p, 0, sizeof(p));
     p.views = ptr<ViewDesc>(x->views);
     p.n_views = n_views;
+    p.sh_degree = scene->sh_degree;
     p.tile_w = x->cfg.tile_w;
     p.tile_h = x->cfg.tile_h;
+    p.px = f->px;
     p.dilation = x->cfg.dilation;
     p.n_items = NV;
     p.total_tiles = tiles;
@@ -421,6 +432,7 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.item_cnt = ptr<uint32_t>(x->item_cnt);
     p.item_zkey = ptr<uint32_t>(x->item_zkey);
     p.sgid = ptr<uint32_t>(f->sgid);
+    p.inv = ptr<uint32_t>(f->inv);
     p.szkey = ptr<uint32_t>(f->szkey);
     p.rec = ptr<float4>(f->rec);
     p.rect = ptr<uint2>(f->rect);
@@ -429,6 +441,7 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.pix_neval = ptr<uint32_t>(f->pix_neval);
+    p.vis_off = ptr<uint32_t>(x->vis_off);
     StageTimer &tm = x->timer;
 
     if (NV > 0) {
@@ -448,6 +461,8 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
         tm.end(PVG_STAGE_DEPTH_SORT, s);
         // (a) records in depth order, (b) pair count
         tm.begin(PVG_STAGE_FINALIZE, s);
+        PVG_CUDA(cudaMemsetAsync(p.inv, 0xff, sizeof(uint32_t) * NV, s));
+        launch_scatter_inv(p, s);
         launch_finalize(p, s);
         tm.end(PVG_STAGE_FINALIZE, s);
         tm.begin(PVG_STAGE_PAIRS, s);
@@ -461,9 +476,11 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
             PVG_TRY(ensure(x->pair_keys, sizeof(uint32_t) * (size_t)K));
             PVG_TRY(ensure(x->pair_keys2, sizeof(uint32_t) * (size_t)K));
             PVG_TRY(ensure(x->pair_vals2, sizeof(uint32_t) * (size_t)K));
+            PVG_TRY(ensure(x->chunk_start, sizeof(uint32_t) * emit_chunks(K)));
             pair_cap = K;
         }
         p.pair_capacity = pair_cap;
+        p.chunk_start = ptr<uint32_t>(x->chunk_start);
         // emission target so that an odd/even number of tile passes ends in f->pair_vals
         const int tbits = bits_for(tiles);
         const int tpasses = (tbits + 7) / 8;
@@ -532,8 +549,11 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     struct { float *p; size_t n; } zero[] = {
         {grads->mu, 3 * N}, {grads->vel, 3 * N}, {grads->tau, N}, {grads->beta, N}, {grads->period, N},
         {grads->scale, 3 * N}, {grads->quat, 4 * N}, {grads->opacity, N}, {grads->sh, 3 * K * N}};
-    for (auto &z : zero)
-        if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
+    // one view: k_preprocess_bwd writes every entry (zeros for invisible
+    // Gaussians); several views accumulate with atomics into zeroed arrays
+    if (n_views > 1 || f->n_items == 0)
+        for (auto &z : zero)
+            if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
     if (f->n_items == 0) return PVG_OK;
     PVG_TRY(ensure(x->views, sizeof(ViewDesc) * n_views));
     PVG_TRY(ensure(f->g2d, sizeof(float) * 10 * (size_t)f->n_items));
@@ -543,14 +563,17 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     std::memset(&p, 0, sizeof(p));
     p.views = ptr<ViewDesc>(x->views);
     p.n_views = n_views;
+    p.sh_degree = scene->sh_degree;
     p.tile_w = f->tile_w;
     p.tile_h = f->tile_h;
+    p.px = f->px;
     p.dilation = f->dilation;
     p.n_items = f->n_items;
     p.total_tiles = f->total_tiles;
     p.pair_capacity = f->pair_capacity;
     p.counters = ptr<uint32_t>(f->counters);
     p.sgid = ptr<uint32_t>(f->sgid);
+    p.inv = ptr<uint32_t>(f->inv);
     p.szkey = ptr<uint32_t>(f->szkey);
     p.rec = ptr<float4>(f->rec);
     p.rect = ptr<uint2>(f->rect);
@@ -659,22 +682,35 @@ __global__ static void k_sum_u32(const uint32_t *v, uint32_t n, unsigned long lo
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
-extern "C" pvg_status_t pvg_frame_eval_count(pvg_frame_t *f, int64_t *evals) {
-    if (!f || !evals || !f->valid) return PVG_ERR_INVALID;
-    DevBuf tmp;
-    PVG_TRY(ensure(tmp, sizeof(unsigned long long)));
-    unsigned long long h = 0;
+extern "C" pvg_status_t pvg_frame_eval_count(pvg_ctx_t *x, pvg_frame_t *f, int64_t *evals) {
+    if (!x || !f || !evals || !f->valid) return PVG_ERR_INVALID;
     cudaStream_t s = f->stream;
-    pvg_status_t st = cuda_status(cudaMemsetAsync(tmp.p, 0, sizeof(h), s), "memset");
-    if (st == PVG_OK) {
-        note_launch();
-        k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, ptr<unsigned long long>(tmp));
-        st = cuda_status(cudaMemcpyAsync(&h, tmp.p, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
-    }
-    if (st == PVG_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
-    release(tmp);
+    const int nv = (int)f->views.size();
+    PVG_TRY(ensure(x->views, sizeof(ViewDesc) * nv));
+    PVG_TRY(ensure(x->sort_n, sizeof(unsigned long long)));
+    PVG_CUDA(cudaMemcpyAsync(x->views.p, f->views.data(), sizeof(ViewDesc) * nv, cudaMemcpyHostToDevice, s));
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.views = ptr<ViewDesc>(x->views);
+    p.n_views = nv;
+    p.tile_w = f->tile_w;
+    p.tile_h = f->tile_h;
+    p.px = f->px;
+    p.total_tiles = f->total_tiles;
+    p.rec = ptr<float4>(f->rec);
+    p.pair_vals = ptr<uint32_t>(f->pair_vals);
+    p.ranges = ptr<uint2>(f->ranges);
+    p.pix_neval = ptr<uint32_t>(f->pix_neval);
+    PVG_CUDA(cudaMemsetAsync(f->pix_neval.p, 0, sizeof(uint32_t) * f->total_pix, s));
+    launch_composite_stats(p, s);
+    unsigned long long h = 0;
+    PVG_CUDA(cudaMemsetAsync(x->sort_n.p, 0, sizeof(h), s));
+    note_launch();
+    k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, ptr<unsigned long long>(x->sort_n));
+    PVG_CUDA(cudaMemcpyAsync(&h, x->sort_n.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PVG_CUDA(cudaStreamSynchronize(s));
     *evals = (int64_t)h;
-    return st;
+    return PVG_OK;
 }
 
 // ------------------------------------------------------------------ sorting

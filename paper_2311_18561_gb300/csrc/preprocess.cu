@@ -5,13 +5,13 @@
 //                    EWA projection (Sec. 3.1, Eq. 2) and the tile
 //                    footprint; writes the tile count and depth bits of
 //                    every item.
-//   k_finalize       (stage a, pass 2) for the m-th visible item in depth
+//   k_finalize       (stage a, pass 2) for every visible item, in item
 //                    order: the same projection plus the SH colour; writes
 //                    the 48-byte compositing record, the tile rectangle and
-//                    the tile count in depth order.
-//   k_preprocess_bwd (stage d2) adjoint of both passes: from the
-//                    image-space gradients of record m to dL/d{mu, v, tau,
-//                    beta, l, s, q, o, sh}.
+//                    the tile count at the item's depth position m.
+//   k_preprocess_bwd (stage d2) adjoint of both passes, in item order: from
+//                    the image-space gradients of record m to dL/d{mu, v,
+//                    tau, beta, l, s, q, o, sh}.
 //
 // All three recompute the projection with the same inline function and
 // the library is built with --fmad=false, so pass 1 and pass 2 agree bit
@@ -64,13 +64,49 @@ struct Fwd {
     float A, B, C, det;
     float ca, cb, cc;
     float u, v;
-    // footprint
+    // footprint: guarded half extents in pixels and the tile rectangle
+    float hx, hy;
     uint32_t tx0, ty0, tx1, ty1, count;
 };
 
 __device__ __forceinline__ float3 ld3(const float *p, uint32_t i) {
     return make_float3(p[3 * (size_t)i], p[3 * (size_t)i + 1], p[3 * (size_t)i + 2]);
 }
+
+// n floats at src (item-strided, so 16-byte aligned when the base is and
+// n is a multiple of 4) into registers / back, as float4 when possible
+template <int NF>
+__device__ __forceinline__ void load_floats(const float *src, float (&dst)[NF], bool vec) {
+    if constexpr (NF % 4 == 0) {
+        if (vec) {
+            const float4 *p = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+            for (int q = 0; q < NF / 4; q++) {
+                const float4 v = p[q];
+                dst[4 * q] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NF; q++) dst[q] = src[q];
+}
+
+template <int NF>
+__device__ __forceinline__ void store_floats(float *dst, const float (&src)[NF], bool vec) {
+    if constexpr (NF % 4 == 0) {
+        if (vec) {
+            float4 *p = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+            for (int q = 0; q < NF / 4; q++) p[q] = make_float4(src[4 * q], src[4 * q + 1], src[4 * q + 2], src[4 * q + 3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NF; q++) dst[q] = src[q];
+}
+
+__device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Kahan's difference of products a*b - c*d, accurate to a few ulp.
 __device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
@@ -170,6 +206,8 @@ __device__ __forceinline__ bool project(const ViewDesc &V, uint32_t i, float dil
         const float rx = sqrtf(Q * F.A) * 1.001f + 1.0f;
         const float ry = sqrtf(Q * F.C) * 1.001f + 1.0f;
         if (!(isfinite(F.u) && isfinite(F.v)) || rx != rx || ry != ry) return false;
+        F.hx = rx;
+        F.hy = ry;
         const float x0 = fmaxf(ceilf(F.u - rx - 0.5f), 0.0f);
         const float x1 = fminf(floorf(F.u + rx - 0.5f), (float)(V.W - 1));
         const float y0 = fmaxf(ceilf(F.v - ry - 0.5f), 0.0f);
@@ -184,52 +222,58 @@ __device__ __forceinline__ bool project(const ViewDesc &V, uint32_t i, float dil
     return true;
 }
 
-// SH basis Y[k] at unit direction d (k = l^2 + l + m), and optionally the
-// gradient of each polynomial.
-template <bool kGrad>
-__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float *Y, float (*dY)[3]) {
+// SH basis Y[k] at unit direction (x, y, z), k = l^2 + l + m, for degree
+// D, and optionally the gradient of each polynomial.  D is a template
+// argument so that every index is a constant and the arrays stay in
+// registers.
+template <int D, bool kGrad>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float (&Y)[16], float (&dY)[16][3]) {
     Y[0] = c_sh[0];
     if (kGrad) { dY[0][0] = dY[0][1] = dY[0][2] = 0.f; }
-    if (deg < 1) return;
-    const float c1 = c_sh[1];
-    Y[1] = -c1 * y; Y[2] = c1 * z; Y[3] = -c1 * x;
-    if (kGrad) {
-        dY[1][0] = 0.f; dY[1][1] = -c1; dY[1][2] = 0.f;
-        dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = c1;
-        dY[3][0] = -c1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    if constexpr (D >= 1) {
+        const float c1 = c_sh[1];
+        Y[1] = -c1 * y; Y[2] = c1 * z; Y[3] = -c1 * x;
+        if (kGrad) {
+            dY[1][0] = 0.f; dY[1][1] = -c1; dY[1][2] = 0.f;
+            dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = c1;
+            dY[3][0] = -c1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+        }
     }
-    if (deg < 2) return;
-    const float c2 = c_sh[2], c3 = c_sh[3], c4 = c_sh[4];
-    const float xx = x * x, yy = y * y, zz = z * z;
-    Y[4] = c2 * x * y;
-    Y[5] = -c2 * y * z;
-    Y[6] = c3 * (2.f * zz - xx - yy);
-    Y[7] = -c2 * x * z;
-    Y[8] = c4 * (xx - yy);
-    if (kGrad) {
-        dY[4][0] = c2 * y; dY[4][1] = c2 * x; dY[4][2] = 0.f;
-        dY[5][0] = 0.f; dY[5][1] = -c2 * z; dY[5][2] = -c2 * y;
-        dY[6][0] = -2.f * c3 * x; dY[6][1] = -2.f * c3 * y; dY[6][2] = 4.f * c3 * z;
-        dY[7][0] = -c2 * z; dY[7][1] = 0.f; dY[7][2] = -c2 * x;
-        dY[8][0] = 2.f * c4 * x; dY[8][1] = -2.f * c4 * y; dY[8][2] = 0.f;
+    if constexpr (D >= 2) {
+        const float c2 = c_sh[2], c3 = c_sh[3], c4 = c_sh[4];
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = c2 * x * y;
+        Y[5] = -c2 * y * z;
+        Y[6] = c3 * (2.f * zz - xx - yy);
+        Y[7] = -c2 * x * z;
+        Y[8] = c4 * (xx - yy);
+        if (kGrad) {
+            dY[4][0] = c2 * y; dY[4][1] = c2 * x; dY[4][2] = 0.f;
+            dY[5][0] = 0.f; dY[5][1] = -c2 * z; dY[5][2] = -c2 * y;
+            dY[6][0] = -2.f * c3 * x; dY[6][1] = -2.f * c3 * y; dY[6][2] = 4.f * c3 * z;
+            dY[7][0] = -c2 * z; dY[7][1] = 0.f; dY[7][2] = -c2 * x;
+            dY[8][0] = 2.f * c4 * x; dY[8][1] = -2.f * c4 * y; dY[8][2] = 0.f;
+        }
     }
-    if (deg < 3) return;
-    const float c5 = c_sh[5], c6 = c_sh[6], c7 = c_sh[7], c8 = c_sh[8], c9 = c_sh[9];
-    Y[9] = -c5 * y * (3.f * xx - yy);
-    Y[10] = c6 * x * y * z;
-    Y[11] = -c7 * y * (4.f * zz - xx - yy);
-    Y[12] = c8 * z * (2.f * zz - 3.f * xx - 3.f * yy);
-    Y[13] = -c7 * x * (4.f * zz - xx - yy);
-    Y[14] = c9 * z * (xx - yy);
-    Y[15] = -c5 * x * (xx - 3.f * yy);
-    if (kGrad) {
-        dY[9][0] = -6.f * c5 * x * y; dY[9][1] = -3.f * c5 * (xx - yy); dY[9][2] = 0.f;
-        dY[10][0] = c6 * y * z; dY[10][1] = c6 * x * z; dY[10][2] = c6 * x * y;
-        dY[11][0] = 2.f * c7 * x * y; dY[11][1] = -c7 * (4.f * zz - xx - 3.f * yy); dY[11][2] = -8.f * c7 * y * z;
-        dY[12][0] = -6.f * c8 * x * z; dY[12][1] = -6.f * c8 * y * z; dY[12][2] = c8 * (6.f * zz - 3.f * xx - 3.f * yy);
-        dY[13][0] = -c7 * (4.f * zz - 3.f * xx - yy); dY[13][1] = 2.f * c7 * x * y; dY[13][2] = -8.f * c7 * x * z;
-        dY[14][0] = 2.f * c9 * x * z; dY[14][1] = -2.f * c9 * y * z; dY[14][2] = c9 * (xx - yy);
-        dY[15][0] = -3.f * c5 * (xx - yy); dY[15][1] = 6.f * c5 * x * y; dY[15][2] = 0.f;
+    if constexpr (D >= 3) {
+        const float c5 = c_sh[5], c6 = c_sh[6], c7 = c_sh[7], c8 = c_sh[8], c9 = c_sh[9];
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[9] = -c5 * y * (3.f * xx - yy);
+        Y[10] = c6 * x * y * z;
+        Y[11] = -c7 * y * (4.f * zz - xx - yy);
+        Y[12] = c8 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+        Y[13] = -c7 * x * (4.f * zz - xx - yy);
+        Y[14] = c9 * z * (xx - yy);
+        Y[15] = -c5 * x * (xx - 3.f * yy);
+        if (kGrad) {
+            dY[9][0] = -6.f * c5 * x * y; dY[9][1] = -3.f * c5 * (xx - yy); dY[9][2] = 0.f;
+            dY[10][0] = c6 * y * z; dY[10][1] = c6 * x * z; dY[10][2] = c6 * x * y;
+            dY[11][0] = 2.f * c7 * x * y; dY[11][1] = -c7 * (4.f * zz - xx - 3.f * yy); dY[11][2] = -8.f * c7 * y * z;
+            dY[12][0] = -6.f * c8 * x * z; dY[12][1] = -6.f * c8 * y * z; dY[12][2] = c8 * (6.f * zz - 3.f * xx - 3.f * yy);
+            dY[13][0] = -c7 * (4.f * zz - 3.f * xx - yy); dY[13][1] = 2.f * c7 * x * y; dY[13][2] = -8.f * c7 * x * z;
+            dY[14][0] = 2.f * c9 * x * z; dY[14][1] = -2.f * c9 * y * z; dY[14][2] = c9 * (xx - yy);
+            dY[15][0] = -3.f * c5 * (xx - yy); dY[15][1] = 6.f * c5 * x * y; dY[15][2] = 0.f;
+        }
     }
 }
 
@@ -245,10 +289,22 @@ __global__ void __launch_bounds__(256) k_project_count(Params P) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_finalize(Params P) {
+// inverse of the depth order: inv[sgid[m]] = m (inv is 0xffffffff elsewhere)
+__global__ void __launch_bounds__(256) k_scatter_inv(Params P) {
     const uint32_t M = P.counters[0];
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-        const uint32_t g = P.sgid[m];
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x)
+        P.inv[P.sgid[m]] = m;
+}
+
+// Records in depth order, computed in item order (coalesced parameter
+// reads; the 48-byte record goes to its depth position m = inv[g]).
+template <int D>
+__global__ void __launch_bounds__(256) k_finalize(Params P) {
+    constexpr int K = (D + 1) * (D + 1);
+    const uint32_t n = P.n_items;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const uint32_t m = P.inv[g];
+        if (m == 0xffffffffu) continue;
         const int view = view_of_item(P.views, P.n_views, g);
         const ViewDesc &V = P.views[view];
         const uint32_t i = g - V.item_base;
@@ -259,15 +315,15 @@ __global__ void __launch_bounds__(256) k_finalize(Params P) {
             P.rect[m] = make_uint2(0u, 0u);
             continue;
         }
-        // colour
-        const int deg = V.sh_degree, K = (deg + 1) * (deg + 1);
         float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
         const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         dx *= inv; dy *= inv; dz *= inv;
-        float Y[16];
-        sh_eval<false>(deg, dx, dy, dz, Y, nullptr);
-        const float *sh = V.sh + (size_t)i * K * 3;
+        float Y[16], dY[16][3];
+        sh_eval<D, false>(dx, dy, dz, Y, dY);
+        float sh[3 * K];
+        load_floats<3 * K>(V.sh + (size_t)i * K * 3, sh, aligned16(V.sh));
         float rgb[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
         for (int k = 0; k < K; k++) {
             rgb[0] += sh[3 * k] * Y[k];
             rgb[1] += sh[3 * k + 1] * Y[k];
@@ -275,8 +331,8 @@ __global__ void __launch_bounds__(256) k_finalize(Params P) {
         }
         const float z = __uint_as_float(P.szkey[m]);
         P.rec[3 * (size_t)m + 0] = make_float4(F.u, F.v, F.ca, F.cb);
-        P.rec[3 * (size_t)m + 1] = make_float4(F.cc, F.ot, z, 0.0f);
-        P.rec[3 * (size_t)m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), 0.0f);
+        P.rec[3 * (size_t)m + 1] = make_float4(F.cc, F.ot, z, F.hx);
+        P.rec[3 * (size_t)m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), F.hy);
         P.rect[m] = make_uint2(F.tx0 | (F.ty0 << 16), F.tx1 | (F.ty1 << 16));
         P.vis_cnt[m] = F.count;
     }
@@ -287,15 +343,48 @@ __device__ __forceinline__ void put(float *dst, size_t k, float v, bool atomic) 
     else dst[k] = v;
 }
 
+// Writes zero gradients for item g of view V (single-view calls, where
+// this kernel writes every gradient entry instead of a separate memset).
+template <int K>
+__device__ __forceinline__ void zero_grads(const ViewDesc &V, uint32_t i) {
+    if (V.g_mu) for (int k = 0; k < 3; k++) V.g_mu[3 * (size_t)i + k] = 0.f;
+    if (V.g_vel) for (int k = 0; k < 3; k++) V.g_vel[3 * (size_t)i + k] = 0.f;
+    if (V.g_scale) for (int k = 0; k < 3; k++) V.g_scale[3 * (size_t)i + k] = 0.f;
+    if (V.g_quat) {
+        const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+        store_floats<4>(V.g_quat + 4 * (size_t)i, z4, aligned16(V.g_quat));
+    }
+    if (V.g_tau) V.g_tau[i] = 0.f;
+    if (V.g_beta) V.g_beta[i] = 0.f;
+    if (V.g_period) V.g_period[i] = 0.f;
+    if (V.g_opac) V.g_opac[i] = 0.f;
+    if (V.g_sh) {
+        float z[3 * K];
+#pragma unroll
+        for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
+        store_floats<3 * K>(V.g_sh + (size_t)i * 3 * K, z, aligned16(V.g_sh));
+    }
+}
+
+// Adjoint of the projection and colour, in item order: item g reads the
+// image-space gradients of its depth position m = inv[g].  With `atomic`
+// (several views share the gradients) the gradients were zeroed before and
+// are accumulated; otherwise every entry of item g is written, zeros for
+// invisible items.
+template <int D>
 __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
-    const uint32_t M = P.counters[0];
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-        const uint32_t g = P.sgid[m];
+    constexpr int K = (D + 1) * (D + 1);
+    const uint32_t n = P.n_items;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
         const int view = view_of_item(P.views, P.n_views, g);
         const ViewDesc &V = P.views[view];
         const uint32_t i = g - V.item_base;
+        const uint32_t m = P.inv[g];
         Fwd F;
-        if (!project(V, i, P.dilation, P.tile_w, P.tile_h, F)) continue;
+        if (m == 0xffffffffu || !project(V, i, P.dilation, P.tile_w, P.tile_h, F)) {
+            if (!atomic) zero_grads<K>(V, i);
+            continue;
+        }
         const float *G2 = P.g2d + 10 * (size_t)m;
         const float gu = G2[0], gv = G2[1], ga = G2[2], gb = G2[3], gc = G2[4];
         const float got = G2[5], gz = G2[9];
@@ -304,24 +393,39 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
 
         // ---- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5)
         {
-            const int deg = V.sh_degree, K = (deg + 1) * (deg + 1);
             float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
             const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
             const float inv = 1.0f / dist;
             dx *= inv; dy *= inv; dz *= inv;
             float Y[16], dY[16][3];
-            sh_eval<true>(deg, dx, dy, dz, Y, dY);
-            const float *sh = V.sh + (size_t)i * K * 3;
+            sh_eval<D, true>(dx, dy, dz, Y, dY);
+            float sh[3 * K];
+            load_floats<3 * K>(V.sh + (size_t)i * K * 3, sh, aligned16(V.sh));
             float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
             for (int k = 0; k < K; k++)
+#pragma unroll
                 for (int c = 0; c < 3; c++) raw[c] += sh[3 * k + c] * Y[k];
             float gcol[3];
+#pragma unroll
             for (int c = 0; c < 3; c++) gcol[c] = raw[c] > 0.0f ? G2[6 + c] : 0.0f;
             float gd[3] = {0.f, 0.f, 0.f};
             if (V.g_sh) {
-                for (int k = 0; k < K; k++)
-                    for (int c = 0; c < 3; c++) put(V.g_sh, ((size_t)i * K + k) * 3 + c, gcol[c] * Y[k], atomic);
+                if (atomic) {
+#pragma unroll
+                    for (int k = 0; k < K; k++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) atomicAdd(V.g_sh + ((size_t)i * K + k) * 3 + c, gcol[c] * Y[k]);
+                } else {
+                    float gsh[3 * K];
+#pragma unroll
+                    for (int k = 0; k < K; k++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) gsh[3 * k + c] = gcol[c] * Y[k];
+                    store_floats<3 * K>(V.g_sh + (size_t)i * K * 3, gsh, aligned16(V.g_sh));
+                }
             }
+#pragma unroll
             for (int k = 0; k < K; k++) {
                 const float w = gcol[0] * sh[3 * k] + gcol[1] * sh[3 * k + 1] + gcol[2] * sh[3 * k + 2];
                 gd[0] += w * dY[k][0];
@@ -412,10 +516,13 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
                                      y * GR[5] + x * GR[6] + y * GR[7]);
             const float dot = F.qn[0] * gw + F.qn[1] * gx + F.qn[2] * gy + F.qn[3] * gzq;
             if (V.g_quat) {
-                put(V.g_quat, 4 * (size_t)i + 0, (gw - F.qn[0] * dot) * F.qinv, atomic);
-                put(V.g_quat, 4 * (size_t)i + 1, (gx - F.qn[1] * dot) * F.qinv, atomic);
-                put(V.g_quat, 4 * (size_t)i + 2, (gy - F.qn[2] * dot) * F.qinv, atomic);
-                put(V.g_quat, 4 * (size_t)i + 3, (gzq - F.qn[3] * dot) * F.qinv, atomic);
+                const float gq[4] = {(gw - F.qn[0] * dot) * F.qinv, (gx - F.qn[1] * dot) * F.qinv,
+                                     (gy - F.qn[2] * dot) * F.qinv, (gzq - F.qn[3] * dot) * F.qinv};
+                if (atomic) {
+                    for (int k = 0; k < 4; k++) atomicAdd(V.g_quat + 4 * (size_t)i + k, gq[k]);
+                } else {
+                    store_floats<4>(V.g_quat + 4 * (size_t)i, gq, aligned16(V.g_quat));
+                }
             }
             if (V.g_scale)
                 for (int k = 0; k < 3; k++) put(V.g_scale, 3 * (size_t)i + k, gsc[k], atomic);
@@ -457,14 +564,29 @@ void launch_project_count(const Params &p, cudaStream_t s) {
     k_project_count<<<grid_for(p.n_items), 256, 0, s>>>(p);
 }
 
+void launch_scatter_inv(const Params &p, cudaStream_t s) {
+    note_launch();
+    k_scatter_inv<<<grid_for(p.n_items), 256, 0, s>>>(p);
+}
+
 void launch_finalize(const Params &p, cudaStream_t s) {
     note_launch();
-    k_finalize<<<grid_for(p.n_items), 256, 0, s>>>(p);
+    switch (p.sh_degree) {
+        case 0: k_finalize<0><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+        case 1: k_finalize<1><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+        case 2: k_finalize<2><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+        default: k_finalize<3><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+    }
 }
 
 void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s) {
     note_launch();
-    k_preprocess_bwd<<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic);
+    switch (p.sh_degree) {
+        case 0: k_preprocess_bwd<0><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        case 1: k_preprocess_bwd<1><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        case 2: k_preprocess_bwd<2><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        default: k_preprocess_bwd<3><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+    }
 }
 
 }  // namespace pvg

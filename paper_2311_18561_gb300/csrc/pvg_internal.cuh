@@ -6,7 +6,8 @@
 //   visible   depth-sorted visible items, position m                 [M]
 //     sgid[m]   gid of the m-th visible item in (depth, gid) order
 //     rec[m]    3 x float4 record read by the compositor:
-//               (u, v, conic a, conic b) (conic c, o~, z, 0) (r, g, b, 0)
+//               (u, v, conic a, conic b) (conic c, o~, z, hx) (r, g, b, hy)
+//               hx, hy: guarded half extents of the footprint box in pixels
 //     rect[m]   tile rectangle, packed (tx0 | ty0 << 16, tx1 | ty1 << 16)
 //   pairs     (tile, m) pairs sorted by (tile, depth, gid)             [K]
 //   ranges    [start, end) into the pairs per global tile             [tiles]
@@ -52,7 +53,9 @@ struct ViewDesc {
 struct Params {
     const ViewDesc *views;
     int32_t n_views;
+    int32_t sh_degree;       // of the call's scene (kernels are specialised on it)
     int32_t tile_w, tile_h;
+    int32_t px;              // pixels per compositing thread
     float dilation;
     uint32_t n_items;        // NV
     uint32_t total_tiles;
@@ -64,17 +67,20 @@ struct Params {
     uint32_t *item_zkey;     // [NV] depth bits (valid where item_cnt > 0)
     // visible
     uint32_t *sgid;          // [M]
+    uint32_t *inv;           // [NV] depth position of each item, 0xffffffff if not visible
     uint32_t *szkey;         // [M]
     float4 *rec;             // [M*3]
     uint2 *rect;             // [M]
     uint32_t *vis_cnt;       // [M] tiles per visible item
+    uint32_t *vis_off;       // [M] first pair position of the item
+    uint32_t *chunk_start;   // [K / 2048 + 1] first item of each pair chunk
     // pairs
     uint32_t *pair_keys;     // [K] tile ids (sorted in place via ping-pong)
     uint32_t *pair_vals;     // [K]
     uint2 *ranges;           // [total_tiles]
     float *pix_T;            // [sum HW]
     uint32_t *pix_last;      // [sum HW] list position after the last blend
-    uint32_t *pix_neval;     // [sum HW] list entries evaluated (stop included)
+    uint32_t *pix_neval;     // [sum HW] in-footprint list entries up to the stop (stats pass)
     // backward
     float *g2d;              // [M*10]
 };
@@ -122,6 +128,7 @@ namespace pvg {
 void note_launch();
 cudaError_t set_sh_constants();
 void launch_project_count(const Params &p, cudaStream_t s);
+void launch_scatter_inv(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);
 void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s);
 // sort / scan
@@ -132,9 +139,11 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32
                       cudaStream_t s, bool *result_in_alt);
 void scan_count_pairs(const Params &p, void *temp, cudaStream_t s);
 void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
+size_t emit_chunks(uint32_t capacity);
 void launch_ranges(const Params &p, cudaStream_t s);
 // raster
-bool composite_supported(int tw, int th);
+bool composite_supported(int tw, int th, int px);
 void launch_composite(const Params &p, cudaStream_t s);
+void launch_composite_stats(const Params &p, cudaStream_t s);
 void launch_composite_bwd(const Params &p, cudaStream_t s);
 }  // namespace pvg

@@ -36,6 +36,9 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 constexpr int kRadix = 256;
 constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
 
+constexpr uint32_t kEmitChunk = 2048;  // pair outputs per expansion chunk
+constexpr int kEmitThreads = 256;
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -101,31 +104,23 @@ struct CompactF {
     }
 };
 
+// Count scan of the per-visible-item tile counts.  apply() stores the
+// item's first output position and, for every chunk of kEmitChunk outputs
+// that starts inside the item's outputs, the item index, so the expansion
+// kernel can find each chunk's items without a global search.
 struct EmitF {
     const uint32_t *d_m;
     const uint32_t *vis_cnt;
-    const uint2 *rect;
-    const uint32_t *sgid;
-    const ViewDesc *views;
-    int nv;
-    uint32_t *keys, *vals;
+    uint32_t *vis_off;
+    uint32_t *chunk_start;
     uint32_t capacity;
     __device__ uint32_t n() const { return *d_m; }
     __device__ uint32_t value(uint32_t m) const { return vis_cnt[m]; }
     __device__ void apply(uint32_t m, uint32_t off, uint32_t v) const {
+        vis_off[m] = off;
         if (v == 0) return;
-        const uint2 r = rect[m];
-        const uint32_t tx0 = r.x & 0xffffu, ty0 = r.x >> 16, tx1 = r.y & 0xffffu, ty1 = r.y >> 16;
-        const int view = view_of_item(views, nv, sgid[m]);
-        const uint32_t tb = views[view].tile_base;
-        const uint32_t tw = (uint32_t)views[view].tiles_x;
-        uint32_t j = off;
-        for (uint32_t ty = ty0; ty < ty1; ty++)
-            for (uint32_t tx = tx0; tx < tx1; tx++, j++)
-                if (j < capacity) {
-                    keys[j] = tb + ty * tw + tx;
-                    vals[j] = m;
-                }
+        const uint32_t end = min(off + v, capacity);
+        for (uint32_t c = (off + kEmitChunk - 1) / kEmitChunk; c * kEmitChunk < end; c++) chunk_start[c] = m;
     }
 };
 
@@ -214,22 +209,66 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * gridDim.x + blockIdx.x] = sh[d];
 }
 
-// exclusive scan of the digit-major histogram (kRadix * G entries)
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int entries) {
+// Row scan of the digit-major histogram hist[d * G + b], one block per
+// digit d: exclusive prefix over the G blocks in place, row total to
+// totals[d].  The downsweep adds the exclusive prefix of the totals over
+// the digits.  G <= 1024.
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, uint32_t *totals, int G) {
     __shared__ uint32_t smem[33];
-    const int per = (entries + 1023) / 1024;
-    const int s = threadIdx.x * per;
-    uint32_t acc = 0;
-    for (int k = 0; k < per; k++)
-        if (s + k < entries) acc += hist[s + k];
-    uint32_t total;
-    uint32_t run = block_excl_scan(acc, smem, &total);
-    for (int k = 0; k < per; k++)
-        if (s + k < entries) {
-            const uint32_t c = hist[s + k];
-            hist[s + k] = run;
-            run += c;
+    uint32_t *row = hist + (size_t)blockIdx.x * G;
+    const uint32_t v = (int)threadIdx.x < G ? row[threadIdx.x] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, smem, &tot);
+    if ((int)threadIdx.x < G) row[threadIdx.x] = ex;
+    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+// Expansion of the sorted visible items into (tile id, depth position)
+// pairs: one thread per output pair, chunks of kEmitChunk outputs; the
+// item of output j is the last m with vis_off[m] <= j, searched among the
+// chunk's items staged in shared memory.
+__global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *__restrict__ vis_off,
+                                                              const uint32_t *__restrict__ chunk_start,
+                                                              const uint2 *__restrict__ rect,
+                                                              const uint32_t *__restrict__ sgid,
+                                                              const ViewDesc *views, int nv, const uint32_t *d_m,
+                                                              const uint32_t *d_k, uint32_t capacity,
+                                                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    __shared__ uint32_t s_off[kEmitChunk + 1];
+    const uint32_t M = *d_m;
+    const uint32_t K = min(*d_k, capacity);
+    const uint32_t nchunks = (K + kEmitChunk - 1) / kEmitChunk;
+    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const uint32_t j0 = c * kEmitChunk;
+        const uint32_t m_lo = chunk_start[c];
+        const uint32_t m_hi = (c + 1 < nchunks) ? chunk_start[c + 1] : M - 1;
+        const uint32_t span = m_hi - m_lo + 1;
+        const bool staged = span <= kEmitChunk + 1;
+        __syncthreads();
+        if (staged)
+            for (uint32_t q = threadIdx.x; q < span; q += kEmitThreads) s_off[q] = vis_off[m_lo + q];
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < kEmitChunk; q += kEmitThreads) {
+            const uint32_t j = j0 + q;
+            if (j >= K) break;
+            // last m in [m_lo, m_hi] with vis_off[m] <= j
+            uint32_t lo = 0, hi = span - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                const uint32_t o = staged ? s_off[mid] : vis_off[m_lo + mid];
+                if (o <= j) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t m = m_lo + lo;
+            const uint32_t r = j - (staged ? s_off[lo] : vis_off[m]);
+            const uint2 rc = rect[m];
+            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu;
+            const uint32_t w = tx1 - tx0;
+            const uint32_t ty = ty0 + r / w, tx = tx0 + r % w;
+            const int view = nv == 1 ? 0 : view_of_item(views, nv, sgid[m]);
+            keys[j] = views[view].tile_base + ty * (uint32_t)views[view].tiles_x + tx;
+            vals[j] = m;
         }
+    }
 }
 
 static_assert(kSortThreads == kRadix, "one thread per digit in the downsweep");
@@ -248,10 +287,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
                                                                   uint32_t *__restrict__ keys_out,
                                                                   uint32_t *__restrict__ vals_out,
                                                                   const uint32_t *d_n, uint32_t cap, int shift,
-                                                                  uint32_t mask, const uint32_t *hist) {
+                                                                  uint32_t mask, const uint32_t *hist,
+                                                                  const uint32_t *totals) {
     __shared__ SortSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int d = tid; d < kRadix; d += kSortThreads) S.base[d] = hist[d * gridDim.x + blockIdx.x];
+    {
+        // digit bases: exclusive prefix of the per-digit totals (one thread per digit)
+        uint32_t tot;
+        const uint32_t dbase = block_excl_scan(totals[tid], S.scan, &tot);
+        S.base[tid] = dbase + hist[tid * gridDim.x + blockIdx.x];
+    }
     uint32_t b0, b1;
     segment_of(min(*d_n, cap), gridDim.x, kSortTile, &b0, &b1);
     const uint32_t lt = lanemask_lt();
@@ -329,12 +374,14 @@ __global__ void k_ranges(const uint32_t *keys, const uint32_t *d_k, uint32_t cap
 struct TempLayout {
     uint32_t *hist;      // kRadix * kMaxSortBlocks
     uint32_t *partials;  // kMaxScanBlocks
+    uint32_t *totals;    // kRadix (shares the partials' space: never live together)
 };
 
 TempLayout temp_layout(void *temp) {
     TempLayout t;
     t.hist = (uint32_t *)temp;
     t.partials = t.hist + kRadix * kMaxSortBlocks;
+    t.totals = t.partials;
     return t;
 }
 
@@ -370,9 +417,9 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32
         note_launch();
         k_radix_upsweep<<<G, kSortThreads, 0, s>>>(ki, d_count, capacity, b, mask, t.hist);
         note_launch();
-        k_radix_scan<<<1, 1024, 0, s>>>(t.hist, kRadix * G);
+        k_radix_scan<<<kRadix, 1024, 0, s>>>(t.hist, t.totals, G);
         note_launch();
-        k_radix_downsweep<<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist);
+        k_radix_downsweep<<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist, t.totals);
         alt = !alt;
         b += nb;
     }
@@ -383,8 +430,7 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32
 // counters[2]; then emission of the (tile, m) pairs in depth order.
 void scan_count_pairs(const Params &p, void *temp, cudaStream_t s) {
     TempLayout t = temp_layout(temp);
-    EmitF f{&p.counters[0], p.vis_cnt, p.rect, p.sgid, p.views, p.n_views, p.pair_keys, p.pair_vals,
-            p.pair_capacity};
+    EmitF f{&p.counters[0], p.vis_cnt, p.vis_off, p.chunk_start, p.pair_capacity};
     const int G = scan_blocks(p.n_items);
     note_launch();
     k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
@@ -392,13 +438,21 @@ void scan_count_pairs(const Params &p, void *temp, cudaStream_t s) {
     k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[1], p.pair_capacity, &p.counters[2]);
 }
 
+size_t emit_chunks(uint32_t capacity) { return (capacity + kEmitChunk - 1) / kEmitChunk + 1; }
+
 void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     TempLayout t = temp_layout(temp);
-    EmitF f{&p.counters[0], p.vis_cnt, p.rect, p.sgid, p.views, p.n_views, p.pair_keys, p.pair_vals,
-            p.pair_capacity};
+    EmitF f{&p.counters[0], p.vis_cnt, p.vis_off, p.chunk_start, p.pair_capacity};
     const int G = scan_blocks(p.n_items);
     note_launch();
     k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    uint32_t grid = (uint32_t)((p.pair_capacity + kEmitChunk - 1) / kEmitChunk);
+    if (grid < 1) grid = 1;
+    if (grid > 152 * 8) grid = 152 * 8;
+    note_launch();
+    k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.chunk_start, p.rect, p.sgid, p.views, p.n_views,
+                                                 &p.counters[0], &p.counters[1], p.pair_capacity, p.pair_keys,
+                                                 p.pair_vals);
 }
 
 void launch_ranges(const Params &p, cudaStream_t s) {

@@ -66,9 +66,10 @@ def _stream_ptr(stream=None):
 class Renderer:
     """Owns one ``pvg_ctx_t`` (workspace) on the current CUDA device."""
 
-    def __init__(self, tile=(16, 16), sync_sizes=True, pair_capacity=1 << 24, dilation=0.3, fov_clamp=1.3):
+    def __init__(self, tile=(16, 16), sync_sizes=True, pair_capacity=1 << 24, dilation=0.3, fov_clamp=1.3,
+                 pixels_per_thread=1):
         self._lib = abi.lib()
-        self.cfg = abi.config(tile, sync_sizes, pair_capacity, dilation, fov_clamp)
+        self.cfg = abi.config(tile, sync_sizes, pair_capacity, dilation, fov_clamp, pixels_per_thread)
         h = C.c_void_p()
         abi.check(self._lib.pvg_create(C.byref(h), C.byref(self.cfg)), "pvg_create")
         self.handle = h
@@ -85,8 +86,10 @@ class Renderer:
         except Exception:
             pass
 
-    def set_tile(self, tile):
+    def set_tile(self, tile, pixels_per_thread=None):
         self.cfg.tile_w, self.cfg.tile_h = int(tile[0]), int(tile[1])
+        if pixels_per_thread is not None:
+            self.cfg.pixels_per_thread = int(pixels_per_thread)
         abi.check(self._lib.pvg_set_config(self.handle, C.byref(self.cfg)), "pvg_set_config")
 
     def alloc_images(self, cams, device="cuda"):
@@ -264,9 +267,9 @@ def profile_read(renderer):
     return {name: (float(ms[k]), int(calls[k])) for k, name in enumerate(abi.STAGES)}
 
 
-def eval_count(frame) -> int:
+def eval_count(renderer, frame) -> int:
     e = C.c_int64()
-    abi.check(abi.lib().pvg_frame_eval_count(frame.handle, C.byref(e)), "pvg_frame_eval_count")
+    abi.check(abi.lib().pvg_frame_eval_count(renderer.handle, frame.handle, C.byref(e)), "pvg_frame_eval_count")
     return int(e.value)
 
 

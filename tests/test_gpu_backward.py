@@ -78,6 +78,25 @@ def test_autograd_l1_training_step():
     _compare_grads({k: params[k].grad for k in NAMES}, ref)
 
 
+@pytest.mark.parametrize("cfg", [(16, 16, 2), (16, 16, 4), (32, 32, 4)])
+def test_backward_multi_pixel_configs(cfg):
+    scene = synth.make_fd_scene(seed=7, n=500, sh_degree=3)
+    cam = synth.fd_camera(64, 48, t=0.35)
+    H, W = cam["height"], cam["width"]
+    w_rgb, w_d, w_a = _weights(H, W, 5)
+    r = R.Renderer(tile=cfg[:2], pixels_per_thread=cfg[2])
+    fr = R.Frame()
+    st = R.scene_to_device(scene)
+    r.forward(st, [cam], frame=fr)
+    dl = dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"),
+              depth=torch.tensor(w_d, dtype=torch.float32, device="cuda"),
+              alpha=torch.tensor(w_a, dtype=torch.float32, device="cuda"))
+    grads = r.backward(st, [cam], fr, [dl])
+    torch.cuda.synchronize()
+    ref = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), w_d, w_a)
+    _compare_grads(grads, ref)
+
+
 def test_multi_view_backward_sums_views():
     scene = synth.make_fd_scene(seed=4, n=400, sh_degree=1)
     cams = [synth.fd_camera(48, 40, t=0.2), synth.fd_camera(64, 48, t=0.7)]

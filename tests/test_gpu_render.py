@@ -16,7 +16,9 @@ from .gpu_util import compare_to_oracle, gpu_render, to_numpy_images
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
-TILES = [(16, 16), (8, 8), (16, 8), (32, 8), (32, 16)]
+# every supported (tile width, tile height, pixels per thread)
+CONFIGS = [(16, 16, 1), (16, 16, 2), (16, 16, 4), (8, 8, 1), (8, 8, 2), (16, 8, 1), (16, 8, 2), (32, 8, 1),
+           (32, 16, 1), (32, 16, 2), (32, 16, 4), (32, 32, 4), (16, 32, 4)]
 
 
 @pytest.fixture(scope="module")
@@ -61,25 +63,36 @@ def test_sh_degrees_1_2(renderer, deg):
 
 
 def test_tile_shape_invariance_bit_exact():
-    """The per-pixel work does not depend on the tile shape: images are
-    bit-identical for every supported tile."""
+    """The per-pixel work does not depend on the tile shape or on how many
+    pixels a thread handles: images are bit-identical for every supported
+    configuration."""
     scene = synth.make_plain_scene(seed=4, n=3000)
     cam = synth.plain_camera(width=203, height=141, t=0.42)
     st = R.scene_to_device(scene)
     ref = None
-    for tile in TILES:
-        r = R.Renderer(tile=tile)
+    for (tw, th, px) in CONFIGS:
+        r = R.Renderer(tile=(tw, th), pixels_per_thread=px)
         out = gpu_render(r, st, [cam])[0]
         cur = [out[k].cpu().numpy() for k in ("rgb", "depth", "alpha")]
         if ref is None:
             ref = cur
         else:
             for a, b in zip(ref, cur):
-                np.testing.assert_array_equal(a, b, err_msg=str(tile))
+                np.testing.assert_array_equal(a, b, err_msg=str((tw, th, px)))
         r.close()
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+@pytest.mark.parametrize("cfg", [(16, 16, 4), (32, 32, 4), (8, 8, 2)])
+def test_multi_pixel_configs_match_oracle(cfg):
+    scene = synth.make_fd_scene(seed=12, n=900, sh_degree=3)
+    cam = synth.fd_camera(77, 53, t=0.55)
+    r = R.Renderer(tile=cfg[:2], pixels_per_thread=cfg[2])
+    out = gpu_render(r, R.scene_to_device(scene), [cam])[0]
+    compare_to_oracle(to_numpy_images(out), oracle.render(scene, cam))
+    r.close()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16), (32, 32)])
 def test_depth_order_tile_lists_and_ranges_bit_exact(tile):
     scene = synth.make_plain_scene(seed=5, n=2000)
     # duplicate some positions so that exact depth ties occur
@@ -88,7 +101,7 @@ def test_depth_order_tile_lists_and_ranges_bit_exact(tile):
     scene["tau"][1000:1100] = scene["tau"][:100]
     scene["period"][1000:1100] = scene["period"][:100]
     cam = synth.plain_camera(width=150, height=110, t=0.5)
-    r = R.Renderer(tile=tile)
+    r = R.Renderer(tile=tile, pixels_per_thread=4 if tile == (32, 32) else 1)
     fr = R.Frame()
     gpu_render(r, R.scene_to_device(scene), [cam], frame=fr)
     tx, ty = R.tiles_of(cam, tile)
