@@ -72,9 +72,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="urban")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched", "serving"), default="urban")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="tile_w,tile_h,pixels_per_thread (default: autotune)")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving leg (req/s)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="duration of the serving leg")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall-clock budget of the oracle's bounded sample")
     return ap.parse_args()
@@ -323,6 +326,10 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if not args.no_serve:
+        del st, grads, flush
+        torch.cuda.empty_cache()
+        out["serving"] = serving_leg(dev, args.serve_rate, args.serve_seconds, config=best)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, cam, args.cpu_seconds)
     if world > 1:
@@ -330,6 +337,209 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- serving
+
+SERVE_SCENES = None
+
+
+def serve_scenes(dev):
+    """The four resident scenes of the serving config (0.5M, 1M, 2M, 4M
+    Gaussians, urban distribution, SH-3)."""
+    global SERVE_SCENES
+    if SERVE_SCENES is None:
+        from paper_2311_18561_gb300 import render as R
+        from paper_2311_18561_gb300 import synth
+
+        SERVE_SCENES = [R.scene_to_device(synth.make_urban_scene(n, seed=10 + k), dev)
+                        for k, n in enumerate(synth.SERVE_SCENE_SIZES)]
+    return SERVE_SCENES
+
+
+def _percentiles(lat_ms):
+    import numpy as np
+
+    a = np.asarray(lat_ms, dtype=np.float64)
+    return float(np.percentile(a, 50)), float(np.percentile(a, 99))
+
+
+def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_streams=2, seed=0):
+    """Poisson arrivals at `rate` req/s for `seconds` (random scene, pose on
+    the street path +-2 m, t ~ U[0,1], resolution from {640x480, 1242x375,
+    1920x1280}) served by the continuous-batching server, then the same
+    schedule served one request per launch, synchronously."""
+    import collections
+
+    import torch
+
+    from paper_2311_18561_gb300 import render as R
+    from paper_2311_18561_gb300 import serve as S
+    from paper_2311_18561_gb300 import synth
+
+    scenes = serve_scenes(dev)
+    reqs = synth.serve_requests(rate, seconds, n_scenes=len(scenes), seed=seed)
+    pool = collections.defaultdict(list)
+
+    def buf(cam):
+        key = (cam["width"], cam["height"])
+        return pool[key].pop() if pool[key] else torch.empty(3, cam["height"], cam["width"], device=dev)
+
+    srv = S.Server(max_batch_views=max_batch_views, n_streams=n_streams, memory_budget=24 << 30,
+                   tile=config[:2], pixels_per_thread=config[2])
+    ids = [srv.add_scene(sc) for sc in scenes]
+    # warm-up: grow every worker's workspace on the largest requests
+    warm = []
+    for k in range(2 * n_streams * max_batch_views):
+        cam = synth.street_camera(0.5, 1920, 1280)
+        warm.append(srv.submit(ids[len(ids) - 1 - (k % len(ids))], cam, dict(rgb=buf(cam))))
+    for rid in warm:
+        srv.wait(rid, 120.0)
+        srv.release(rid)
+    torch.cuda.synchronize()
+    stats, outstanding, i = [], collections.deque(), 0
+    t0 = time.perf_counter()
+    while i < len(reqs) or outstanding:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i][0] <= now:
+            _, sid, cam = reqs[i]
+            b = buf(cam)
+            outstanding.append((srv.submit(ids[sid], cam, dict(rgb=b)), cam, b))
+            i += 1
+        while outstanding:
+            rid, cam, b = outstanding[0]
+            done, st = srv.poll(rid)
+            if not done:
+                break
+            stats.append((st, cam))
+            pool[(cam["width"], cam["height"])].append(b)
+            srv.release(rid)
+            outstanding.popleft()
+        time.sleep(0.0002)
+    counters = srv.counters()
+    srv.close()
+    lat = [st["done_ms"] - st["submit_ms"] for st, _ in stats]
+    span_ms = max(st["done_ms"] for st, _ in stats) - min(st["submit_ms"] for st, _ in stats)
+    pix = sum(c["width"] * c["height"] for _, c in stats)
+    p50, p99 = _percentiles(lat)
+    served = {"p50_ms": p50, "p99_ms": p99, "mpix_s": pix / (span_ms * 1e-3) / 1e6, "requests": len(stats),
+              "launches": counters["batches"], "mean_views_per_launch": counters["views"] / max(1, counters["batches"]),
+              "errors": sum(1 for st, _ in stats if st["status"] != 0)}
+    # one request per launch, synchronous, same schedule
+    r = R.Renderer(tile=config[:2], pixels_per_thread=config[2])
+    for k in range(3):
+        r.forward(scenes[-1], [synth.street_camera(0.5, 1920, 1280)])
+    torch.cuda.synchronize()
+    lat1, outs1 = [], {}
+    t0 = time.perf_counter()
+    for arr, sid, cam in reqs:
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        key = (cam["width"], cam["height"])
+        if key not in outs1:
+            outs1[key] = r.alloc_images([cam])
+        r.forward(scenes[sid], [cam], outs=outs1[key])
+        torch.cuda.synchronize()
+        lat1.append((time.perf_counter() - t0 - arr) * 1e3)
+    span1 = time.perf_counter() - t0 - reqs[0][0]
+    r.close()
+    q50, q99 = _percentiles(lat1)
+    one = {"p50_ms": q50, "p99_ms": q99, "mpix_s": pix / span1 / 1e6}
+    return {"rate_req_s": rate, "seconds": seconds, "scenes": list(synth.SERVE_SCENE_SIZES),
+            "max_batch_views": max_batch_views, "streams": n_streams, "served": served,
+            "one_request_per_launch": one}
+
+
+def run_serving(args):
+    """Serving sweep over request rates (report only)."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rates = [200.0, 500.0, 1000.0, 2000.0]
+    res = [serving_leg(dev, rt, args.serve_seconds) for rt in rates]
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "workload": "serving sweep", "legs": res}), flush=True)
+
+
+def run_batched(args):
+    """64 views (22 x 1920x1280, 21 x 1242x375, 21 x 960x640, own t each) of
+    a 3M-Gaussian urban scene: forward + L1 + backward replayed as one CUDA
+    graph, against the same calls uncaptured and against one launch
+    sequence per view."""
+    import torch
+
+    from paper_2311_18561_gb300 import batch as B
+    from paper_2311_18561_gb300 import render as R
+    from paper_2311_18561_gb300 import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene = R.scene_to_device(synth.make_urban_scene(3_000_000, seed=0), dev)
+    cams = synth.batched_views(seed=0, n_views=64)
+    g = B.BatchGraph(scene, cams, autotune=not args.tile,
+                     config=tuple(int(v) for v in args.tile.split(",")) if args.tile else None,
+                     tune_configs=((16, 16, 1), (16, 16, 2), (16, 16, 4), (32, 16, 4), (16, 32, 4), (32, 32, 4)))
+    mpix = g.pixels / 1e6
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+    ms_graph = timed(g.replay, args.steps)
+    over = g.overflowed()
+    tw, th, px = g.config
+    # uncaptured, one call for all views (size read-back per call)
+    r = R.Renderer(tile=(tw, th), pixels_per_thread=px)
+    fr = R.Frame()
+    outs = r.alloc_images(cams)
+    grads = {k: torch.empty_like(scene[k]) for k in R.PARAM_NAMES}
+
+    def direct():
+        r.forward(scene, cams, outs=outs, frame=fr)
+        dls = []
+        for v, o in enumerate(outs):
+            dls.append(dict(rgb=R.l1_loss(o["rgb"], g.targets[v])[1]))
+        r.backward(scene, cams, fr, dls, grads=grads)
+
+    direct()
+    ms_direct = timed(direct, max(3, args.steps // 4))
+    fr.close()
+    del outs
+    # one launch sequence per view
+    r1 = R.Renderer(tile=(tw, th), pixels_per_thread=px)
+    f1 = R.Frame()
+    o1 = {}
+
+    def per_view():
+        for v, cam in enumerate(cams):
+            key = (cam["width"], cam["height"])
+            if key not in o1:
+                o1[key] = r1.alloc_images([cam])
+            o = r1.forward(scene, [cam], outs=o1[key], frame=f1)[0]
+            dl = R.l1_loss(o["rgb"], g.targets[v])[1]
+            r1.backward(scene, [cam], f1, [dict(rgb=dl)], grads=grads)
+
+    per_view()
+    ms_per_view = timed(per_view, max(2, args.steps // 8))
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "workload": "batched: 64 views (22x1920x1280, 21x1242x375, 21x960x640), "
+            "3M Gaussians SH-3, fwd + L1 + bwd", "mpix_per_batch": mpix, "config": list(g.config),
+            "pair_capacity": g.pair_capacity, "overflow": over,
+            "graph": {"ms": ms_graph, "mpix_s": mpix / (ms_graph * 1e-3)},
+            "uncaptured_one_call": {"ms": ms_direct, "mpix_s": mpix / (ms_direct * 1e-3)},
+            "one_launch_per_view": {"ms": ms_per_view, "mpix_s": mpix / (ms_per_view * 1e-3)}}), flush=True)
 
 
 # --------------------------------------------------------------------------- oracle
@@ -424,6 +634,10 @@ def run_reference(args):
 
 def main():
     args = parse_args()
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     select_workload(args.workload)
     if args.impl == "reference":
         run_reference(args)

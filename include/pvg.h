@@ -189,6 +189,21 @@ pvg_status_t pvg_frame_stats(pvg_frame_t *frame, int64_t *n_visible, int64_t *n_
 pvg_status_t pvg_render_fwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_camera_t *cams,
                             int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame, void *stream);
 
+/* Like pvg_render_fwd, but view v renders scenes[v] (host array of
+ * n_views scene descriptors; several views may name the same arrays).  All
+ * scenes must have the same SH degree.  Used to batch requests for
+ * different scenes into one launch sequence; a frame rendered this way
+ * with more than one distinct scene cannot be passed to pvg_render_bwd.
+ *
+ * CUDA-graph capture (both render entry points and pvg_render_bwd): a call
+ * may be captured when the context was created with sync_sizes = 0 and the
+ * same call (same sizes, same frame) has run once uncaptured, so that no
+ * buffer has to grow; otherwise PVG_ERR_INVALID.  The view descriptors are
+ * copied from pinned staging owned by the frame: a replayed graph renders
+ * the cameras given at capture time. */
+pvg_status_t pvg_render_fwd_multi(pvg_ctx_t *ctx, const pvg_scene_t *scenes, const pvg_camera_t *cams,
+                                  int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame, void *stream);
+
 /* Adjoint of the forward pass saved in `frame` (which must have been
  * rendered from the same scene values and cameras): zeroes `grads` and
  * writes dL/dparam for L = sum over views of <dL[v], image[v]>.
@@ -196,6 +211,64 @@ pvg_status_t pvg_render_fwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_
 pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_camera_t *cams,
                             int32_t n_views, pvg_frame_t *frame, const pvg_image_grad_t *dL,
                             const pvg_scene_grad_t *grads, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* serving                                                             */
+/* ------------------------------------------------------------------ */
+
+/* A render server: several scenes resident in HBM, requests (scene, camera
+ * at time t, destination images) queued on the host and rendered by
+ * `n_streams` worker threads, each with its own CUDA stream and workspace.
+ * A free worker takes requests from the head of the queue into one batch
+ * (up to max_batch_views views, of any scenes with one SH degree and any
+ * sizes) as long as their estimated working memory fits in what is left of
+ * memory_budget, and renders the batch with one pvg_render_fwd_multi launch
+ * sequence; requests that arrive meanwhile join the next batch of the next
+ * free worker, so batches overlap on the device (continuous batching).
+ * Every request renders bit-identically alone and in a batch.  The server
+ * uses the device that is current at creation. */
+typedef struct pvg_server pvg_server_t;
+
+typedef struct {
+    int32_t max_batch_views; /* views per launch sequence (default 16) */
+    int32_t n_streams;       /* worker streams, 1..16 (default 2) */
+    int64_t memory_budget;   /* bytes of estimated in-flight working memory (default 8 GiB) */
+    int32_t max_pending;     /* queued requests before submit returns PVG_ERR_BUSY (default 4096) */
+    int32_t tile_w, tile_h, pixels_per_thread; /* compositing configuration (16, 16, 1) */
+    int32_t reserved[4];
+} pvg_serve_config_t;
+
+/* Per-request timing in milliseconds since the server was created; start
+ * and done are -1 until reached. */
+typedef struct {
+    double submit_ms, start_ms, done_ms;
+    int32_t batch_views;  /* views in the launch that rendered it */
+    int32_t status;       /* pvg_status_t of that launch */
+} pvg_req_stats_t;
+
+void pvg_serve_config_default(pvg_serve_config_t *cfg);
+pvg_status_t pvg_serve_create(pvg_server_t **server, const pvg_serve_config_t *cfg);
+/* Registers a resident scene (device arrays stay caller-owned and must
+ * outlive the server); returns its id. */
+pvg_status_t pvg_serve_add_scene(pvg_server_t *server, const pvg_scene_t *scene, int32_t *scene_id);
+/* Queues a request; never blocks.  dst: device images ([3,H,W] rgb
+ * required, depth / alpha may be NULL), written when the request is done.
+ * PVG_ERR_BUSY if max_pending requests are already queued,
+ * PVG_ERR_NOT_FOUND for an unknown scene id. */
+pvg_status_t pvg_serve_submit(pvg_server_t *server, int32_t scene_id, const pvg_camera_t *cam,
+                              const pvg_image_t *dst, uint64_t *req_id);
+/* Non-blocking status: *done = 1 once the images are written. */
+pvg_status_t pvg_serve_poll(pvg_server_t *server, uint64_t req_id, int32_t *done, pvg_req_stats_t *stats);
+/* Blocks until the request is done or timeout_ms elapsed (PVG_ERR_TIMEOUT);
+ * returns the status of the launch that rendered it. */
+pvg_status_t pvg_serve_wait(pvg_server_t *server, uint64_t req_id, double timeout_ms, pvg_req_stats_t *stats);
+/* Forgets a finished request (PVG_ERR_BUSY if it is not done yet). */
+pvg_status_t pvg_serve_release(pvg_server_t *server, uint64_t req_id);
+/* Queue length, launches and views so far, estimated in-flight bytes. */
+pvg_status_t pvg_serve_counters(pvg_server_t *server, int64_t *queued, int64_t *batches, int64_t *views,
+                                int64_t *in_flight_bytes);
+/* Finishes every queued request, stops the workers and frees the server. */
+pvg_status_t pvg_serve_destroy(pvg_server_t *server);
 
 /* ------------------------------------------------------------------ */
 /* sorting                                                             */

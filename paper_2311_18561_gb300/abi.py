@@ -56,6 +56,17 @@ class Config(C.Structure):
                 ("fov_clamp", C.c_float), ("reserved", C.c_float * 6)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("max_batch_views", C.c_int32), ("n_streams", C.c_int32), ("memory_budget", C.c_int64),
+                ("max_pending", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("pixels_per_thread", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class ReqStats(C.Structure):
+    _fields_ = [("submit_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double),
+                ("batch_views", C.c_int32), ("status", C.c_int32)]
+
+
 # every symbol include/pvg.h declares, with (restype, argtypes)
 _P = C.c_void_p
 _SIGS = {
@@ -70,9 +81,21 @@ _SIGS = {
     "pvg_frame_destroy": (None, [_P]),
     "pvg_frame_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "pvg_render_fwd": (C.c_int, [_P, C.POINTER(Scene), C.POINTER(Camera), C.c_int32, C.POINTER(Image), _P, _P]),
+    "pvg_render_fwd_multi": (C.c_int, [_P, C.POINTER(Scene), C.POINTER(Camera), C.c_int32, C.POINTER(Image), _P,
+                                       _P]),
     "pvg_render_bwd": (C.c_int, [_P, C.POINTER(Scene), C.POINTER(Camera), C.c_int32, _P, C.POINTER(ImageGrad),
                                  C.POINTER(SceneGrad), _P]),
     "pvg_frame_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pvg_serve_config_default": (None, [C.POINTER(ServeConfig)]),
+    "pvg_serve_create": (C.c_int, [C.POINTER(_P), C.POINTER(ServeConfig)]),
+    "pvg_serve_add_scene": (C.c_int, [_P, C.POINTER(Scene), C.POINTER(C.c_int32)]),
+    "pvg_serve_submit": (C.c_int, [_P, C.c_int32, C.POINTER(Camera), C.POINTER(Image), C.POINTER(C.c_uint64)]),
+    "pvg_serve_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(ReqStats)]),
+    "pvg_serve_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(ReqStats)]),
+    "pvg_serve_release": (C.c_int, [_P, C.c_uint64]),
+    "pvg_serve_counters": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]),
+    "pvg_serve_destroy": (C.c_int, [_P]),
     "pvg_sort_pairs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
     "pvg_sort_pairs_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
     "pvg_l1_loss": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),

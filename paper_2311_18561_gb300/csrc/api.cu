@@ -66,6 +66,12 @@ pvg_status_t ensure(DevBuf &b, size_t bytes) {
     return PVG_OK;
 }
 
+// ensure() that refuses to allocate while the stream is being captured
+pvg_status_t ensure_c(DevBuf &b, size_t bytes, bool capturing) {
+    if (capturing) return b.bytes >= (bytes ? bytes : 16) ? PVG_OK : PVG_ERR_INVALID;
+    return ensure(b, bytes);
+}
+
 template <class T>
 T *ptr(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
 
@@ -130,8 +136,13 @@ struct StageTimer {
 
 }  // namespace
 
+struct ViewStage;
+void free_stage_ptr(ViewStage *st);
+ViewStage *new_stage();
+
 struct pvg_frame {
     int device = -1;
+    ViewStage *stage_fwd = nullptr, *stage_bwd = nullptr;
     DevBuf counters;            // u32 [4]: M, K, overflow
     DevBuf sgid, szkey;         // [NV]
     DevBuf inv;                 // [NV] depth position per item
@@ -143,6 +154,7 @@ struct pvg_frame {
     DevBuf pix_neval;           // [pixels]
     DevBuf g2d;                 // [NV * 10]
     std::vector<ViewDesc> views;
+    bool one_scene = true;      // every view renders the same scene
     uint32_t n_items = 0, total_tiles = 0, total_pix = 0, pair_capacity = 0;
     int tile_w = 0, tile_h = 0, px = 1;
     int64_t n = -1;
@@ -213,6 +225,8 @@ extern "C" pvg_status_t pvg_frame_create(pvg_frame_t **frame) {
     if (!frame) return PVG_ERR_INVALID;
     pvg_frame *f = new pvg_frame();
     PVG_CUDA(cudaGetDevice(&f->device));
+    f->stage_fwd = new_stage();
+    f->stage_bwd = new_stage();
     if (cudaMallocHost(&f->h_counters, 4 * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         delete f;
@@ -234,6 +248,8 @@ extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
                       &f->ranges, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
+    free_stage_ptr(f->stage_fwd);
+    free_stage_ptr(f->stage_bwd);
     delete f;
 }
 
@@ -299,16 +315,20 @@ static pvg_status_t validate_scene(const pvg_scene_t *sc) {
     return PVG_OK;
 }
 
-static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *sc, const pvg_camera_t *cams, int nv,
-                                std::vector<ViewDesc> &out, uint32_t *n_items, uint32_t *total_tiles,
-                                uint32_t *total_pix) {
-    if (!cams || nv < 1 || nv > kMaxViewsPerCall) return PVG_ERR_INVALID;
+// Per-view descriptors.  Scene of view v = scenes[v * scene_stride]
+// (stride 0: one scene for every view).  Items of view v are
+// [item_base, item_base + n_v), item_base = sum of the earlier views' n.
+static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *scenes, int scene_stride,
+                                const pvg_camera_t *cams, int nv, std::vector<ViewDesc> &out, uint32_t *n_items,
+                                uint32_t *total_tiles, uint32_t *total_pix) {
+    if (!cams || !scenes || nv < 1 || nv > kMaxViewsPerCall) return PVG_ERR_INVALID;
     const int TW = x->cfg.tile_w, TH = x->cfg.tile_h;
-    const uint64_t nitems = (uint64_t)sc->n * (uint64_t)nv;
-    if (nitems >= (1ull << 31)) return PVG_ERR_INVALID;
     out.assign(nv, ViewDesc());
-    uint64_t tiles = 0, pix = 0;
+    uint64_t tiles = 0, pix = 0, items = 0;
     for (int v = 0; v < nv; v++) {
+        const pvg_scene_t *sc = &scenes[(size_t)v * scene_stride];
+        PVG_TRY(validate_scene(sc));
+        if (sc->sh_degree != scenes[0].sh_degree) return PVG_ERR_INVALID;
         const pvg_camera_t &c = cams[v];
         if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return PVG_ERR_INVALID;
         if (!(c.fx > 0.f) || !(c.fy > 0.f) || !std::isfinite(c.fx) || !std::isfinite(c.fy) ||
@@ -332,19 +352,87 @@ static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *sc, const p
         d.tiles_y = (c.height + TH - 1) / TH;
         d.tile_base = (uint32_t)tiles;
         d.pix_base = (uint32_t)pix;
-        d.item_base = (uint32_t)((uint64_t)v * (uint64_t)sc->n);
+        d.item_base = (uint32_t)items;
         d.n = (uint32_t)sc->n;
         d.sh_degree = sc->sh_degree;
         d.mu = sc->mu; d.vel = sc->vel; d.tau = sc->tau; d.beta = sc->beta; d.period = sc->period;
         d.scale = sc->scale; d.quat = sc->quat; d.opac = sc->opacity; d.sh = sc->sh;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
         pix += (uint64_t)c.width * c.height;
+        items += (uint64_t)sc->n;
+        if (items >= (1ull << 31)) return PVG_ERR_INVALID;
     }
     if (tiles >= (1ull << 31) || pix >= (1ull << 32)) return PVG_ERR_INVALID;
-    *n_items = (uint32_t)nitems;
+    *n_items = (uint32_t)items;
     *total_tiles = (uint32_t)tiles;
     *total_pix = (uint32_t)pix;
     return PVG_OK;
+}
+
+// Copies the view descriptors to the device through pinned staging owned
+// by `stage` (so that the copy can be captured in a CUDA graph).  Outside
+// capture, waits for the previous copy from the same staging first.
+struct ViewStage {
+    ViewDesc *host = nullptr;  // pinned
+    size_t cap = 0;
+    DevBuf dev;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+static pvg_status_t stage_views(ViewStage &st, const std::vector<ViewDesc> &views, cudaStream_t s,
+                                bool capturing) {
+    const size_t n = views.size();
+    if (st.pending && !capturing) {
+        PVG_CUDA(cudaEventSynchronize(st.done));
+        st.pending = false;
+    }
+    if (st.cap < n) {
+        if (capturing) return PVG_ERR_INVALID;  // no allocation while capturing
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.cap = 0;
+        if (cudaMallocHost(&st.host, sizeof(ViewDesc) * n) != cudaSuccess) {
+            cudaGetLastError();
+            return PVG_ERR_OOM;
+        }
+        st.cap = n;
+    }
+    PVG_TRY(ensure(st.dev, sizeof(ViewDesc) * n));
+    if (!st.done) PVG_CUDA(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming));
+    std::memcpy(st.host, views.data(), sizeof(ViewDesc) * n);
+    PVG_CUDA(cudaMemcpyAsync(st.dev.p, st.host, sizeof(ViewDesc) * n, cudaMemcpyHostToDevice, s));
+    if (!capturing) {
+        PVG_CUDA(cudaEventRecord(st.done, s));
+        st.pending = true;
+    }
+    return PVG_OK;
+}
+
+ViewStage *new_stage() { return new ViewStage(); }
+
+static void free_stage(ViewStage &st);
+void free_stage_ptr(ViewStage *st) {
+    if (!st) return;
+    free_stage(*st);
+    delete st;
+}
+
+static void free_stage(ViewStage &st) {
+    if (st.pending) cudaEventSynchronize(st.done);
+    if (st.host) cudaFreeHost(st.host);
+    if (st.done) cudaEventDestroy(st.done);
+    release(st.dev);
+    st = ViewStage();
+}
+
+static bool is_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
 }
 
 static int bits_for(uint32_t n) {
@@ -356,52 +444,54 @@ static int bits_for(uint32_t n) {
 
 // ------------------------------------------------------------------ forward
 
-extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cams,
-                                       int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame,
-                                       void *stream_) {
-    if (!x || !out) return PVG_ERR_INVALID;
-    PVG_TRY(validate_scene(scene));
+static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int scene_stride,
+                                    const pvg_camera_t *cams, int32_t n_views, const pvg_image_t *out,
+                                    pvg_frame_t *frame, void *stream_) {
+    if (!x || !out || !scenes) return PVG_ERR_INVALID;
     for (int v = 0; v < n_views; v++)
         if (!out[v].rgb) return PVG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream_;
+    const bool capturing = is_capturing(s);
+    if (capturing && x->cfg.sync_sizes) return PVG_ERR_INVALID;  // a graph cannot hold the size read-back
     pvg_frame *f = frame ? frame : x->own_frame;
     std::vector<ViewDesc> views;
     uint32_t NV, tiles, pix;
-    PVG_TRY(build_views(x, scene, cams, n_views, views, &NV, &tiles, &pix));
+    PVG_TRY(build_views(x, scenes, scene_stride, cams, n_views, views, &NV, &tiles, &pix));
+    const pvg_scene_t *scene = &scenes[0];
     for (int v = 0; v < n_views; v++) {
         views[v].out_rgb = out[v].rgb;
         views[v].out_depth = out[v].depth;
         views[v].out_alpha = out[v].alpha;
     }
     // workspace
-    PVG_TRY(ensure(x->views, sizeof(ViewDesc) * n_views));
-    PVG_TRY(ensure(x->item_cnt, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(x->item_zkey, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(x->alt_keys, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(x->alt_vals, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(x->vis_off, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(f->sgid, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(f->inv, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(f->szkey, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(f->rec, sizeof(float4) * 3 * (size_t)NV));
-    PVG_TRY(ensure(f->rect, sizeof(uint2) * NV));
-    PVG_TRY(ensure(f->vis_cnt, sizeof(uint32_t) * NV));
-    PVG_TRY(ensure(f->ranges, sizeof(uint2) * tiles));
-    PVG_TRY(ensure(f->pix_T, sizeof(float) * pix));
-    PVG_TRY(ensure(f->pix_last, sizeof(uint32_t) * pix));
-    PVG_TRY(ensure(f->pix_neval, sizeof(uint32_t) * pix));
+    PVG_TRY(ensure_c(x->item_cnt, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(x->item_zkey, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(x->alt_keys, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(x->alt_vals, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(x->vis_off, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(f->sgid, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(f->inv, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(f->szkey, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(f->rec, sizeof(float4) * 3 * (size_t)NV, capturing));
+    PVG_TRY(ensure_c(f->rect, sizeof(uint2) * NV, capturing));
+    PVG_TRY(ensure_c(f->vis_cnt, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(f->ranges, sizeof(uint2) * tiles, capturing));
+    PVG_TRY(ensure_c(f->pix_T, sizeof(float) * pix, capturing));
+    PVG_TRY(ensure_c(f->pix_last, sizeof(uint32_t) * pix, capturing));
+    PVG_TRY(ensure_c(f->pix_neval, sizeof(uint32_t) * pix, capturing));
     uint32_t pair_cap;
     if (x->cfg.sync_sizes) {
         pair_cap = (uint32_t)(f->pair_vals.bytes / sizeof(uint32_t));
     } else {
         pair_cap = (uint32_t)x->cfg.pair_capacity;
-        PVG_TRY(ensure(f->pair_vals, sizeof(uint32_t) * (size_t)pair_cap));
-        PVG_TRY(ensure(x->pair_keys, sizeof(uint32_t) * (size_t)pair_cap));
-        PVG_TRY(ensure(x->pair_keys2, sizeof(uint32_t) * (size_t)pair_cap));
-        PVG_TRY(ensure(x->pair_vals2, sizeof(uint32_t) * (size_t)pair_cap));
-        PVG_TRY(ensure(x->chunk_start, sizeof(uint32_t) * emit_chunks(pair_cap)));
+        PVG_TRY(ensure_c(f->pair_vals, sizeof(uint32_t) * (size_t)pair_cap, capturing));
+        PVG_TRY(ensure_c(x->pair_keys, sizeof(uint32_t) * (size_t)pair_cap, capturing));
+        PVG_TRY(ensure_c(x->pair_keys2, sizeof(uint32_t) * (size_t)pair_cap, capturing));
+        PVG_TRY(ensure_c(x->pair_vals2, sizeof(uint32_t) * (size_t)pair_cap, capturing));
+        PVG_TRY(ensure_c(x->chunk_start, sizeof(uint32_t) * emit_chunks(pair_cap), capturing));
     }
     f->views = views;
+    f->one_scene = scene_stride == 0 || n_views == 1;
     f->n_items = NV;
     f->total_tiles = tiles;
     f->total_pix = pix;
@@ -414,12 +504,12 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     f->stream = s;
     f->valid = false;
 
-    PVG_CUDA(cudaMemcpyAsync(x->views.p, views.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice, s));
+    PVG_TRY(stage_views(*f->stage_fwd, views, s, capturing));
     PVG_CUDA(cudaMemsetAsync(f->counters.p, 0, 4 * sizeof(uint32_t), s));
 
     Params p;
     std::memset(&p, 0, sizeof(p));
-    p.views = ptr<ViewDesc>(x->views);
+    p.views = ptr<ViewDesc>(f->stage_fwd->dev);
     p.n_views = n_views;
     p.sh_degree = scene->sh_degree;
     p.tile_w = x->cfg.tile_w;
@@ -443,6 +533,8 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.pix_neval = ptr<uint32_t>(f->pix_neval);
     p.vis_off = ptr<uint32_t>(x->vis_off);
     StageTimer &tm = x->timer;
+    const bool timer_on = tm.on;
+    if (capturing) tm.on = false;
 
     if (NV > 0) {
         // (a) project + count, (b) depth sort of the visible items
@@ -472,11 +564,11 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
             PVG_CUDA(cudaMemcpyAsync(x->h_pinned, &p.counters[1], sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             PVG_CUDA(cudaStreamSynchronize(s));
             const uint32_t K = x->h_pinned[0];
-            PVG_TRY(ensure(f->pair_vals, sizeof(uint32_t) * (size_t)K));
-            PVG_TRY(ensure(x->pair_keys, sizeof(uint32_t) * (size_t)K));
-            PVG_TRY(ensure(x->pair_keys2, sizeof(uint32_t) * (size_t)K));
-            PVG_TRY(ensure(x->pair_vals2, sizeof(uint32_t) * (size_t)K));
-            PVG_TRY(ensure(x->chunk_start, sizeof(uint32_t) * emit_chunks(K)));
+            PVG_TRY(ensure_c(f->pair_vals, sizeof(uint32_t) * (size_t)K, capturing));
+            PVG_TRY(ensure_c(x->pair_keys, sizeof(uint32_t) * (size_t)K, capturing));
+            PVG_TRY(ensure_c(x->pair_keys2, sizeof(uint32_t) * (size_t)K, capturing));
+            PVG_TRY(ensure_c(x->pair_vals2, sizeof(uint32_t) * (size_t)K, capturing));
+            PVG_TRY(ensure_c(x->chunk_start, sizeof(uint32_t) * emit_chunks(K), capturing));
             pair_cap = K;
         }
         p.pair_capacity = pair_cap;
@@ -512,9 +604,22 @@ extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     tm.begin(PVG_STAGE_COMPOSITE, s);
     launch_composite(p, s);
     tm.end(PVG_STAGE_COMPOSITE, s);
+    tm.on = timer_on;
     PVG_CUDA(cudaGetLastError());
     f->valid = true;
     return PVG_OK;
+}
+
+extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cams,
+                                       int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame,
+                                       void *stream) {
+    return render_fwd_impl(x, scene, 0, cams, n_views, out, frame, stream);
+}
+
+extern "C" pvg_status_t pvg_render_fwd_multi(pvg_ctx_t *x, const pvg_scene_t *scenes, const pvg_camera_t *cams,
+                                             int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame,
+                                             void *stream) {
+    return render_fwd_impl(x, scenes, 1, cams, n_views, out, frame, stream);
 }
 
 // ------------------------------------------------------------------ backward
@@ -531,9 +636,11 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     if (!x || !dL || !grads) return PVG_ERR_INVALID;
     PVG_TRY(validate_scene(scene));
     pvg_frame *f = frame ? frame : x->own_frame;
-    if (!f->valid || f->n != scene->n || f->sh_degree != scene->sh_degree || (int)f->views.size() != n_views)
+    if (!f->valid || !f->one_scene || f->n != scene->n || f->sh_degree != scene->sh_degree ||
+        (int)f->views.size() != n_views)
         return PVG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream_;
+    const bool capturing = is_capturing(s);
     std::vector<ViewDesc> views = f->views;
     for (int v = 0; v < n_views; v++) {
         if (!cams || cams[v].width != views[v].W || cams[v].height != views[v].H) return PVG_ERR_INVALID;
@@ -555,13 +662,13 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
         for (auto &z : zero)
             if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
     if (f->n_items == 0) return PVG_OK;
-    PVG_TRY(ensure(x->views, sizeof(ViewDesc) * n_views));
+    if (capturing && f->g2d.bytes < sizeof(float) * 10 * (size_t)f->n_items) return PVG_ERR_INVALID;
     PVG_TRY(ensure(f->g2d, sizeof(float) * 10 * (size_t)f->n_items));
-    PVG_CUDA(cudaMemcpyAsync(x->views.p, views.data(), sizeof(ViewDesc) * n_views, cudaMemcpyHostToDevice, s));
+    PVG_TRY(stage_views(*f->stage_bwd, views, s, capturing));
 
     Params p;
     std::memset(&p, 0, sizeof(p));
-    p.views = ptr<ViewDesc>(x->views);
+    p.views = ptr<ViewDesc>(f->stage_bwd->dev);
     p.n_views = n_views;
     p.sh_degree = scene->sh_degree;
     p.tile_w = f->tile_w;
@@ -584,6 +691,8 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.g2d = ptr<float>(f->g2d);
     StageTimer &tm = x->timer;
+    const bool timer_on = tm.on;
+    if (capturing) tm.on = false;
     tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
     note_launch();
     k_zero_g2d<<<152 * 4, 256, 0, s>>>(p.g2d, &p.counters[0]);
@@ -592,6 +701,7 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     tm.begin(PVG_STAGE_PREPROCESS_BWD, s);
     launch_preprocess_bwd(p, n_views > 1, s);
     tm.end(PVG_STAGE_PREPROCESS_BWD, s);
+    tm.on = timer_on;
     PVG_CUDA(cudaGetLastError());
     return PVG_OK;
 }

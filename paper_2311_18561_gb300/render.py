@@ -282,3 +282,24 @@ def sort_pairs(renderer, keys, vals, begin_bit=0, end_bit=32, stream=None):
                                   int(end_bit), _stream_ptr(stream))
     abi.check(st, "pvg_sort_pairs")
     return keys, vals
+
+
+def render_multi(renderer, scenes, cams, outs=None, frame=None, stream=None):
+    """View v renders scenes[v] (``pvg_render_fwd_multi``); scenes may repeat."""
+    if len(scenes) != len(cams):
+        raise ValueError("one scene per camera")
+    if outs is None:
+        outs = renderer.alloc_images(cams)
+    sc = (abi.Scene * len(cams))()
+    for k, s in enumerate(scenes):
+        sc[k] = abi_scene(s)
+    ca = abi.cameras(cams)
+    imgs = (abi.Image * len(cams))()
+    for k, o in enumerate(outs):
+        imgs[k].rgb = o["rgb"].data_ptr()
+        imgs[k].depth = o["depth"].data_ptr() if o.get("depth") is not None else None
+        imgs[k].alpha = o["alpha"].data_ptr() if o.get("alpha") is not None else None
+    st = abi.lib().pvg_render_fwd_multi(renderer.handle, sc, ca, len(cams), imgs,
+                                        frame.handle if frame is not None else None, _stream_ptr(stream))
+    abi.check(st, "pvg_render_fwd_multi")
+    return outs
