@@ -61,9 +61,14 @@ def workload_camera(frame):
 
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# FP32 FMA-pipe lane-instructions per list-entry evaluation in the
-# compositor: 2 FADD (dx, dy), 4 FMUL + 2 FFMA (falloff exponent, o~ G)
+# Algorithmic FP32 FMA-pipe lane-instructions of the compositor:
+# every in-footprint evaluation: 2 FADD (dx, dy), 4 FMUL + 2 FFMA (falloff
+# exponent, o~ G) = 8; every blended evaluation in addition, forward:
+# 1 - alpha, T (1 - alpha), alpha T, 4 FFMA (r g b z), O += w = 8;
+# backward: 1 - alpha, T / (1 - alpha), alpha T_i, dL/dalpha (13), 4 FFMA
+# (r g b z terms), o~ term, 5 moments (8), 5 suffix sums = 35.
 OPS_PER_EVAL = 8
+OPS_PER_BLEND = {"composite": 8, "composite_bwd": 35}
 
 
 def parse_args():
@@ -255,7 +260,7 @@ def run_ours(args):
 
     M, K, ov = fr.stats()
     r.forward(st, [cam], outs=outs, frame=fr)
-    E = R.eval_count(r, fr)
+    E, B = R.eval_count(r, fr)
     ms_step = step_ms / args.steps
     t = torch.tensor([ms_step, fwd_ms], device=dev)
     if world > 1:
@@ -283,15 +288,20 @@ def run_ours(args):
     dominant = max(stage_ms, key=stage_ms.get)
     pk = peaks()
     roof = None
-    if dominant in ("composite", "composite_bwd"):
-        alu_peak = SM_COUNT * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x clock, lane-instr/s
-        ach = E * OPS_PER_EVAL / (stage_ms[dominant] * 1e-3)
-        roof = {"kernel": "k_composite" if dominant == "composite" else "k_composite_bwd",
-                "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak / 1e12,
-                "unit": "T FP32-lane-instr/s", "frac": ach / alu_peak,
-                "traffic": ncu_traffic("k_composite" if dominant == "composite" else "k_composite_bwd"),
-                "work": "E=%d list-entry evaluations x %d FP32 instructions" % (E, OPS_PER_EVAL),
+    alu_peak = SM_COUNT * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x clock, lane-instr/s
+
+    def alu_roof(stage):
+        ops = E * OPS_PER_EVAL + B * OPS_PER_BLEND[stage]
+        ach = ops / (stage_ms[stage] * 1e-3)
+        kern = "k_composite" if stage == "composite" else "k_composite_bwd"
+        return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak / 1e12,
+                "unit": "T FP32-lane-instr/s", "frac": ach / alu_peak, "traffic": ncu_traffic(kern),
+                "work": "E=%d in-footprint evaluations x %d + %d blended x %d FP32 instructions"
+                        % (E, OPS_PER_EVAL, B, OPS_PER_BLEND[stage]),
                 "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (derived)" % pk["sm_max_mhz"]}
+
+    if dominant in ("composite", "composite_bwd"):
+        roof = alu_roof(dominant)
     else:
         # HBM-bound stages: algorithmic bytes per launch
         algo = {"project": N_GAUSS * 68 + N_GAUSS * 8, "finalize": M * (68 + 192 + 48 + 8 + 4),
@@ -318,7 +328,8 @@ def run_ours(args):
         "autotune_ms": None if table is None else {"%dx%dx%d" % k: round(v, 4) for k, v in table.items()},
         "render_fwd": {"ms": fwd_ms, "mpix_s": world * mpix / (fwd_ms * 1e-3)},
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "visible": M, "pairs": K, "evals": E, "overflow": ov,
+        "visible": M, "pairs": K, "evals": E, "blended_evals": B, "overflow": ov,
+        "roofline_composite_fwd": alu_roof("composite"),
         "wall_s_timed_region": wall,
         "roofline": roof,
         "e2e": {"value": world * mpix / e2e_s, "unit": "Mpix/s", "h2d_bytes_per_step": target_host.numel() * 4,

@@ -345,12 +345,13 @@ pvg_status_t pvg_profile_enable(pvg_ctx_t *ctx, int on);
  * forgets them. */
 pvg_status_t pvg_profile_read(pvg_ctx_t *ctx, double *ms, int64_t *calls);
 
-/* The compositing work E of the last forward into `frame`: summed over all
- * pixels, the number of entries of the pixel's tile list whose footprint
- * box contains the pixel, up to and including the entry that stopped it.
- * Re-runs the compositor in a counting mode (writes no image) with `ctx`'s
- * scratch; synchronises the frame's stream. */
-pvg_status_t pvg_frame_eval_count(pvg_ctx_t *ctx, pvg_frame_t *frame, int64_t *evals);
+/* The compositing work of the last forward into `frame`, summed over all
+ * pixels: *evals = entries of the pixel's tile list whose footprint box
+ * contains the pixel, up to and including the entry that stopped it (E);
+ * *blends (may be NULL) = those among them with alpha >= 1/255 (blended or
+ * stopping the pixel).  Re-runs the compositor in a counting mode (writes
+ * no image) with `ctx`'s scratch; synchronises the frame's stream. */
+pvg_status_t pvg_frame_eval_count(pvg_ctx_t *ctx, pvg_frame_t *frame, int64_t *evals, int64_t *blends);
 
 /* Copy device-side intermediate results of the last forward into
  * caller-owned DEVICE buffers (any may be NULL), for parity testing:

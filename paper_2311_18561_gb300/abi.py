@@ -102,7 +102,7 @@ _SIGS = {
     "pvg_kernel_launches": (C.c_uint64, []),
     "pvg_profile_enable": (C.c_int, [_P, C.c_int]),
     "pvg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
-    "pvg_frame_eval_count": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
+    "pvg_frame_eval_count": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
 STAGES = ("project", "depth_sort", "finalize", "pairs", "tile_sort", "composite", "composite_bwd",

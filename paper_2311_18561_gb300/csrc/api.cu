@@ -150,6 +150,7 @@ struct pvg_frame {
     DevBuf rect, vis_cnt;       // [NV]
     DevBuf pair_vals;           // [K]
     DevBuf ranges;              // [tiles]
+    DevBuf tile_order;          // [tiles] compositor launch order
     DevBuf pix_T, pix_last;     // [pixels]
     DevBuf pix_neval;           // [pixels]
     DevBuf g2d;                 // [NV * 10]
@@ -245,7 +246,7 @@ extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
     for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->rect, &f->vis_cnt, &f->pair_vals,
-                      &f->ranges, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d})
+                      &f->ranges, &f->tile_order, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
     free_stage_ptr(f->stage_fwd);
@@ -476,9 +477,10 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     PVG_TRY(ensure_c(f->rect, sizeof(uint2) * NV, capturing));
     PVG_TRY(ensure_c(f->vis_cnt, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(f->ranges, sizeof(uint2) * tiles, capturing));
+    PVG_TRY(ensure_c(f->tile_order, sizeof(uint32_t) * tiles, capturing));
     PVG_TRY(ensure_c(f->pix_T, sizeof(float) * pix, capturing));
     PVG_TRY(ensure_c(f->pix_last, sizeof(uint32_t) * pix, capturing));
-    PVG_TRY(ensure_c(f->pix_neval, sizeof(uint32_t) * pix, capturing));
+    PVG_TRY(ensure_c(f->pix_neval, sizeof(uint32_t) * 2 * (size_t)pix, capturing));
     uint32_t pair_cap;
     if (x->cfg.sync_sizes) {
         pair_cap = (uint32_t)(f->pair_vals.bytes / sizeof(uint32_t));
@@ -528,6 +530,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     p.rect = ptr<uint2>(f->rect);
     p.vis_cnt = ptr<uint32_t>(f->vis_cnt);
     p.ranges = ptr<uint2>(f->ranges);
+    p.tile_order = ptr<uint32_t>(f->tile_order);
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.pix_neval = ptr<uint32_t>(f->pix_neval);
@@ -595,12 +598,15 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
         p.pair_keys = t_alt ? F_keys : E_keys;
         p.pair_vals = ptr<uint32_t>(f->pair_vals);
         launch_ranges(p, s);
+        launch_tile_order(p, s);
         tm.end(PVG_STAGE_TILE_SORT, s);
     } else {
         PVG_CUDA(cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * tiles, s));
+        launch_tile_order(p, s);
     }
     f->pair_capacity = pair_cap;
     p.pair_vals = ptr<uint32_t>(f->pair_vals);
+    if (!frame) p.pix_T = nullptr;  // inference only: no state for a backward pass
     tm.begin(PVG_STAGE_COMPOSITE, s);
     launch_composite(p, s);
     tm.end(PVG_STAGE_COMPOSITE, s);
@@ -687,6 +693,7 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.vis_cnt = ptr<uint32_t>(f->vis_cnt);
     p.pair_vals = ptr<uint32_t>(f->pair_vals);
     p.ranges = ptr<uint2>(f->ranges);
+    p.tile_order = ptr<uint32_t>(f->tile_order);
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.g2d = ptr<float>(f->g2d);
@@ -792,12 +799,12 @@ __global__ static void k_sum_u32(const uint32_t *v, uint32_t n, unsigned long lo
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
-extern "C" pvg_status_t pvg_frame_eval_count(pvg_ctx_t *x, pvg_frame_t *f, int64_t *evals) {
+extern "C" pvg_status_t pvg_frame_eval_count(pvg_ctx_t *x, pvg_frame_t *f, int64_t *evals, int64_t *blends) {
     if (!x || !f || !evals || !f->valid) return PVG_ERR_INVALID;
     cudaStream_t s = f->stream;
     const int nv = (int)f->views.size();
     PVG_TRY(ensure(x->views, sizeof(ViewDesc) * nv));
-    PVG_TRY(ensure(x->sort_n, sizeof(unsigned long long)));
+    PVG_TRY(ensure(x->sort_n, 2 * sizeof(unsigned long long)));
     PVG_CUDA(cudaMemcpyAsync(x->views.p, f->views.data(), sizeof(ViewDesc) * nv, cudaMemcpyHostToDevice, s));
     Params p;
     std::memset(&p, 0, sizeof(p));
@@ -807,19 +814,25 @@ extern "C" pvg_status_t pvg_frame_eval_count(pvg_ctx_t *x, pvg_frame_t *f, int64
     p.tile_h = f->tile_h;
     p.px = f->px;
     p.total_tiles = f->total_tiles;
+    p.total_pix = f->total_pix;
     p.rec = ptr<float4>(f->rec);
     p.pair_vals = ptr<uint32_t>(f->pair_vals);
     p.ranges = ptr<uint2>(f->ranges);
+    p.tile_order = ptr<uint32_t>(f->tile_order);
     p.pix_neval = ptr<uint32_t>(f->pix_neval);
-    PVG_CUDA(cudaMemsetAsync(f->pix_neval.p, 0, sizeof(uint32_t) * f->total_pix, s));
+    PVG_CUDA(cudaMemsetAsync(f->pix_neval.p, 0, sizeof(uint32_t) * 2 * (size_t)f->total_pix, s));
     launch_composite_stats(p, s);
-    unsigned long long h = 0;
-    PVG_CUDA(cudaMemsetAsync(x->sort_n.p, 0, sizeof(h), s));
+    unsigned long long h[2] = {0, 0};
+    unsigned long long *d = ptr<unsigned long long>(x->sort_n);
+    PVG_CUDA(cudaMemsetAsync(d, 0, sizeof(h), s));
     note_launch();
-    k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, ptr<unsigned long long>(x->sort_n));
-    PVG_CUDA(cudaMemcpyAsync(&h, x->sort_n.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, d);
+    note_launch();
+    k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval) + f->total_pix, f->total_pix, d + 1);
+    PVG_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
     PVG_CUDA(cudaStreamSynchronize(s));
-    *evals = (int64_t)h;
+    *evals = (int64_t)h[0];
+    if (blends) *blends = (int64_t)h[1];
     return PVG_OK;
 }
 

@@ -59,6 +59,7 @@ struct Params {
     float dilation;
     uint32_t n_items;        // NV
     uint32_t total_tiles;
+    uint32_t total_pix;
     uint32_t pair_capacity;
     // device counters: [0] visible M, [1] pairs K, [2] overflow flag
     uint32_t *counters;
@@ -78,9 +79,10 @@ struct Params {
     uint32_t *pair_keys;     // [K] tile ids (sorted in place via ping-pong)
     uint32_t *pair_vals;     // [K]
     uint2 *ranges;           // [total_tiles]
+    uint32_t *tile_order;    // [total_tiles] tiles by decreasing list length (compositor launch order)
     float *pix_T;            // [sum HW]
     uint32_t *pix_last;      // [sum HW] list position after the last blend
-    uint32_t *pix_neval;     // [sum HW] in-footprint list entries up to the stop (stats pass)
+    uint32_t *pix_neval;     // [2][sum HW] stats pass: in-footprint entries up to the stop, and blended ones
     // backward
     float *g2d;              // [M*10]
 };
@@ -141,6 +143,7 @@ void scan_count_pairs(const Params &p, void *temp, cudaStream_t s);
 void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
 size_t emit_chunks(uint32_t capacity);
 void launch_ranges(const Params &p, cudaStream_t s);
+void launch_tile_order(const Params &p, cudaStream_t s);
 // raster
 bool composite_supported(int tw, int th, int px);
 void launch_composite(const Params &p, cudaStream_t s);

@@ -42,7 +42,7 @@ template <int TW, int TH, int PX>
 __device__ __forceinline__ TileGeom tile_geom(const Params &P) {
     static_assert(TW % 8 == 0 && (TH / PX) % 4 == 0 && TH % PX == 0, "tile must be whole 8x4-thread warps");
     TileGeom g;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = P.tile_order ? P.tile_order[blockIdx.x] : blockIdx.x;
     const int view = view_of_tile(P.views, P.n_views, tile);
     g.V = &P.views[view];
     const uint32_t lt = tile - g.V->tile_base;
@@ -65,7 +65,8 @@ __device__ __forceinline__ void stage_record(const Params &P, uint32_t m, float4
 
 // kStats: instead of images, write per pixel the number of list entries
 // whose footprint box contains the pixel, up to and including the one
-// that stopped it (the compositing work E).
+// that stopped it (the compositing work E), and the number of those with
+// alpha >= 1/255 (blended, or stopping the pixel).
 template <int TW, int TH, int PX, bool kStats>
 __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
     constexpr int BLOCK = TW * TH / PX;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
     const float fx = (float)G.px + 0.5f;
     float fy[PX];
     float T[PX], C0[PX], C1[PX], C2[PX], D[PX], O[PX];
-    uint32_t last[PX], neval[PX];
+    uint32_t last[PX], neval[PX], nblend[PX];
     uint32_t done = 0;
 #pragma unroll
     for (int p = 0; p < PX; p++) {
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
         C0[p] = C1[p] = C2[p] = D[p] = O[p] = 0.f;
         last[p] = 0;
         neval[p] = 0;
+        nblend[p] = 0;
         if (!(G.px < V.W && G.py0 + p < V.H)) done |= 1u << p;
     }
     for (uint32_t base = r.x; base < r.y; base += BLOCK) {
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
                 const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
                 const float alpha = fminf(kAlphaCap, __fmul_rn(q.y, ex2_approx(e)));
                 if (alpha < kAlphaMin) continue;
+                if constexpr (kStats) nblend[p]++;
                 const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
                 if (Tn < kTStop) {
                     done |= 1u << p;
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
         const size_t pix = (size_t)py * V.W + G.px;
         if (kStats) {
             P.pix_neval[V.pix_base + pix] = neval[p];
+            P.pix_neval[P.total_pix + V.pix_base + pix] = nblend[p];
             continue;
         }
         V.out_rgb[pix] = C0[p] + T[p] * V.bg[0];
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
                 const float alpha = fminf(kAlphaCap, raw);
                 if (alpha < kAlphaMin) continue;
                 contrib = true;
-                const float inv = 1.0f / (1.0f - alpha);
+                const float inv = __frcp_rn(1.0f - alpha);
                 const float Ti = T[p] * inv;
                 const float w = alpha * Ti;
                 const float ga = Ti * (gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z + gD[p] * col.w + gO[p]) -
@@ -285,15 +289,16 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
                 gv[8] += gC2[p] * w;
                 gv[9] += gD[p] * w;
                 if (raw <= kAlphaCap) {
+                    // moments of gpow = dL/dpower (d alpha / d power = alpha);
+                    // the conic is applied once per Gaussian in the flush
                     gv[5] += ga * G;
-                    const float gpow = ga * alpha;                  // d alpha / d power = alpha
-                    const float gpl = gpow * 0.6931471805599453f;   // gpow / log2(e)
-                    gv[2] += -0.5f * gpow * dx * dx;
-                    gv[3] += -gpow * dx * dy;
-                    gv[4] += -0.5f * gpow * dy * dy;
-                    // a dx + b dy = -(2 a' dx + b' dy) / log2(e)
-                    gv[0] += -gpl * (2.f * g.z * dx + g.w * dy);
-                    gv[1] += -gpl * (g.w * dx + 2.f * q.x * dy);
+                    const float gpow = ga * alpha;
+                    const float mx = gpow * dx, my = gpow * dy;
+                    gv[0] += mx;
+                    gv[1] += my;
+                    gv[2] += mx * dx;
+                    gv[3] += mx * dy;
+                    gv[4] += my * dy;
                 }
                 sC0[p] += col.x * w;
                 sC1[p] += col.y * w;
@@ -308,9 +313,25 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
             }
         }
         __syncthreads();
-        for (int q = tid; q < cnt * NG; q += BLOCK) {
-            const float v = s_acc[q];
-            if (v != 0.f) atomicAdd(&P.g2d[10 * (size_t)s_m[q / NG] + (q % NG)], v);
+        // image-space gradients of each staged Gaussian from its moments:
+        //   d/da = -m_xx / 2, d/db = -m_xy, d/dc = -m_yy / 2,
+        //   d/du = (a m_x + b m_y) = -(2 a' m_x + b' m_y) / log2(e),
+        //   d/dv = (b m_x + c m_y) = -(b' m_x + 2 c' m_y) / log2(e)
+        for (int k = tid; k < cnt; k += BLOCK) {
+            const float *a = &s_acc[k * NG];
+            const float ap = s0[k].z, bp = s0[k].w, cp = s1[k].x;
+            float gt[NG];
+            gt[0] = -0.6931471805599453f * (2.f * ap * a[0] + bp * a[1]);
+            gt[1] = -0.6931471805599453f * (bp * a[0] + 2.f * cp * a[1]);
+            gt[2] = -0.5f * a[2];
+            gt[3] = -a[3];
+            gt[4] = -0.5f * a[4];
+#pragma unroll
+            for (int c = 5; c < NG; c++) gt[c] = a[c];
+            float *dst = &P.g2d[10 * (size_t)s_m[k]];
+#pragma unroll
+            for (int c = 0; c < NG; c++)
+                if (gt[c] != 0.f) atomicAdd(dst + c, gt[c]);
         }
         end = start;
     }

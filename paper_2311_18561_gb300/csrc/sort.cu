@@ -455,6 +455,37 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
                                                  p.pair_vals);
 }
 
+// Tile order for the compositor: heaviest lists first (64 log-spaced
+// length buckets, longest bucket first), so the long tiles start at once
+// and the short ones fill in behind them.  Order within a bucket is left
+// to the atomics (each tile's result does not depend on when it runs).
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                     uint32_t *__restrict__ order) {
+    __shared__ uint32_t cnt[64];
+    __shared__ uint32_t smem[33];
+    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    auto bucket = [&](uint32_t t) {
+        const uint32_t len = ranges[t].y - ranges[t].x;
+        const int b = min(63, (int)(log2f((float)len + 1.0f) * 3.0f));
+        return 63 - b;  // longest first
+    };
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&cnt[bucket(t)], 1u);
+    __syncthreads();
+    uint32_t tot;
+    const uint32_t v = threadIdx.x < 64 ? cnt[threadIdx.x] : 0u;
+    const uint32_t ex = block_excl_scan(v, smem, &tot);
+    if (threadIdx.x < 64) cnt[threadIdx.x] = ex;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&cnt[bucket(t)], 1u)] = t;
+}
+
+void launch_tile_order(const Params &p, cudaStream_t s) {
+    if (p.total_tiles == 0) return;
+    note_launch();
+    k_tile_order<<<1, 1024, 0, s>>>(p.ranges, p.total_tiles, p.tile_order);
+}
+
 void launch_ranges(const Params &p, cudaStream_t s) {
     cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * (size_t)p.total_tiles, s);
     note_launch();

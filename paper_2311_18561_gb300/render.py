@@ -267,10 +267,13 @@ def profile_read(renderer):
     return {name: (float(ms[k]), int(calls[k])) for k, name in enumerate(abi.STAGES)}
 
 
-def eval_count(renderer, frame) -> int:
-    e = C.c_int64()
-    abi.check(abi.lib().pvg_frame_eval_count(renderer.handle, frame.handle, C.byref(e)), "pvg_frame_eval_count")
-    return int(e.value)
+def eval_count(renderer, frame):
+    """(E, blended): list entries each pixel evaluated inside their footprint
+    box up to its stop, and how many of them had alpha >= 1/255."""
+    e, b = C.c_int64(), C.c_int64()
+    abi.check(abi.lib().pvg_frame_eval_count(renderer.handle, frame.handle, C.byref(e), C.byref(b)),
+              "pvg_frame_eval_count")
+    return int(e.value), int(b.value)
 
 
 def sort_pairs(renderer, keys, vals, begin_bit=0, end_bit=32, stream=None):
