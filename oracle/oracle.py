@@ -40,7 +40,7 @@ def load():
         build()
         lib = C.CDLL(_LIB)
         P = C.c_void_p
-        lib.pvgo_time_eval.argtypes = [C.c_int64] + [P] * 6 + [C.c_double, P, P]
+        lib.pvgo_time_eval.argtypes = [C.c_int64] + [P] * 6 + [C.c_double, C.c_double, P, P]
         lib.pvgo_sh_basis.argtypes = [C.c_int, C.c_int64, P, P, P]
         lib.pvgo_preprocess.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 9
         lib.pvgo_render.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + [P] * 6
@@ -67,11 +67,12 @@ def num_threads() -> int:
 
 
 def cam_array(cam) -> np.ndarray:
-    """viewmat[12], fx, fy, cx, cy, width, height, t, z_near, bg[3]."""
+    """viewmat[12], fx, fy, cx, cy, width, height, t, z_near, bg[3], dt."""
     vm = np.asarray(cam["viewmat"], np.float64).reshape(12)
     rest = [cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"],
             cam["t"], cam["z_near"]]
-    return np.concatenate([vm, np.asarray(rest, np.float64), np.asarray(cam["bg"], np.float64).reshape(3)])
+    return np.concatenate([vm, np.asarray(rest, np.float64), np.asarray(cam["bg"], np.float64).reshape(3),
+                           np.asarray([float(cam.get("dt", 0.0))])])
 
 
 def opt_array(opts=None) -> np.ndarray:
@@ -89,13 +90,15 @@ def _scene_args(scene):
     return int(scene["mu"].shape[0]), deg, arrs
 
 
-def time_eval(scene, t):
-    """Eq. 6 and Eq. 7: (mu~(t) [N,3], o~(t) [N])."""
+def time_eval(scene, t, dt=0.0):
+    """Eq. 6 and Eq. 7: (mu~(t) [N,3], o~(t) [N]); with dt != 0 the
+    flow-translated state of Sec. 3.4 (queried at t - dt, moved by
+    v_bar dt)."""
     n = int(np.asarray(scene["mu"]).shape[0])
     arrs = [_d(scene[k]) for k in ("mu", "vel", "tau", "beta", "period", "opacity")]
     mut = np.zeros((n, 3))
     ot = np.zeros(n)
-    load().pvgo_time_eval(n, *[_p(a) for a in arrs], float(t), _p(mut), _p(ot))
+    load().pvgo_time_eval(n, *[_p(a) for a in arrs], float(t), float(dt), _p(mut), _p(ot))
     return mut, ot
 
 

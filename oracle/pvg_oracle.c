@@ -53,14 +53,16 @@
 #define TWO_PI (2.0 * M_PI)
 
 /* camera array layout: viewmat[12], fx, fy, cx, cy, width, height, t,
- * z_near, bg0, bg1, bg2 */
-enum { CAM_FX = 12, CAM_FY, CAM_CX, CAM_CY, CAM_W, CAM_H, CAM_T, CAM_ZNEAR, CAM_BG, CAM_LEN = CAM_BG + 3 };
+ * z_near, bg0, bg1, bg2, dt (temporal-smoothing shift, 0 = plain render) */
+enum { CAM_FX = 12, CAM_FY, CAM_CX, CAM_CY, CAM_W, CAM_H, CAM_T, CAM_ZNEAR, CAM_BG, CAM_DT = CAM_BG + 3,
+       CAM_LEN = CAM_DT + 1 };
 /* option array layout */
 enum { OPT_H = 0, OPT_ACAP, OPT_AMIN, OPT_TSTOP, OPT_FOVCLAMP, OPT_LEN };
 
 typedef struct {
     int valid;
     double delta, theta, sin_t, cos_t, egate; /* time terms */
+    double dt, vbar_w;                        /* flow shift and exp(-rho / 2) */
     double mut[3], ot;                        /* mu~(t), o~(t) */
     double p[3];                              /* camera-space mean */
     int clamp_x, clamp_y;                     /* -1, 0, +1 */
@@ -147,14 +149,20 @@ static void sh_basis(int degree, const double d[3], double *Y, double (*dY)[3])
 /* ------------------------------------------------------------------ */
 /* step 1: time evaluation (Eq. 6, Eq. 7)                             */
 /* ------------------------------------------------------------------ */
-static void time_eval(const scene_t *S, int64_t i, double t, gauss_t *g)
+/* With dt != 0 this is the flow-translated state of Sec. 3.4 ("temporal
+ * smoothing by intrinsic motion"): the point is queried at t - dt and
+ * moved by the average velocity v_bar = v exp(-rho / 2), rho = beta / l
+ * (Eq. 10), times dt; its opacity is the one at t - dt. */
+static void time_eval(const scene_t *S, int64_t i, double t, double dt, gauss_t *g)
 {
     const double l = S->period[i], b = S->beta[i];
-    g->delta = t - S->tau[i];
+    g->dt = dt;
+    g->delta = (t - dt) - S->tau[i];
     g->theta = TWO_PI * g->delta / l;
     g->sin_t = sin(g->theta);
     g->cos_t = cos(g->theta);
-    const double amp = l / TWO_PI * g->sin_t;
+    g->vbar_w = exp(-0.5 * b / l);
+    const double amp = l / TWO_PI * g->sin_t + dt * g->vbar_w;
     for (int k = 0; k < 3; k++)
         g->mut[k] = S->mu[3 * i + k] + amp * S->vel[3 * i + k];
     g->egate = exp(-0.5 * g->delta * g->delta / (b * b));
@@ -173,7 +181,7 @@ static void quat_to_rot(const double q[4], double R[3][3])
 static void preprocess_one(const scene_t *S, int64_t i, const double *cam, const double *opt, gauss_t *g)
 {
     memset(g, 0, sizeof(*g));
-    time_eval(S, i, cam[CAM_T], g);
+    time_eval(S, i, cam[CAM_T], cam[CAM_DT], g);
     const double *V = cam; /* row-major 3x4 */
     for (int r = 0; r < 3; r++)
         g->p[r] = V[4 * r + 0] * g->mut[0] + V[4 * r + 1] * g->mut[1] + V[4 * r + 2] * g->mut[2] + V[4 * r + 3];
@@ -327,12 +335,12 @@ static double eval_alpha(const gauss_t *g, double sx, double sy, const double *o
 /* exported: step 1 alone                                              */
 /* ------------------------------------------------------------------ */
 int pvgo_time_eval(int64_t n, const double *mu, const double *vel, const double *tau, const double *beta,
-                   const double *period, const double *opac, double t, double *out_mut, double *out_ot)
+                   const double *period, const double *opac, double t, double dt, double *out_mut, double *out_ot)
 {
     scene_t S = make_scene(n, 0, mu, vel, tau, beta, period, NULL, NULL, opac, NULL);
     for (int64_t i = 0; i < n; i++) {
         gauss_t g;
-        time_eval(&S, i, t, &g);
+        time_eval(&S, i, t, dt, &g);
         for (int k = 0; k < 3; k++) out_mut[3 * i + k] = g.mut[k];
         out_ot[i] = g.ot;
     }
@@ -643,13 +651,17 @@ static void backward_one(const scene_t *S, int64_t i, const gauss_t *g, const do
     /* time evaluation adjoint */
     const double l = S->period[i], be = S->beta[i];
     const double gv_dot = gmut[0] * S->vel[3 * i] + gmut[1] * S->vel[3 * i + 1] + gmut[2] * S->vel[3 * i + 2];
-    const double amp = l / TWO_PI * g->sin_t;
+    const double amp = l / TWO_PI * g->sin_t + g->dt * g->vbar_w;
     for (int k = 0; k < 3; k++) {
         dmu[3 * i + k] += gmut[k];
         dvel[3 * i + k] += gmut[k] * amp;
     }
     double gtau = -g->cos_t * gv_dot;
     dperiod[i] += gv_dot * (g->sin_t / TWO_PI - g->delta / l * g->cos_t);
+    /* flow shift dt v exp(-beta / (2 l)) */
+    const double gsh = gv_dot * g->dt * g->vbar_w;
+    dbeta[i] += gsh * (-0.5 / l);
+    dperiod[i] += gsh * (0.5 * be / (l * l));
     const double go = g2[G2_O];
     dopac[i] += go * g->egate;
     gtau += go * g->ot * g->delta / (be * be);

@@ -22,7 +22,8 @@ A scene is a dict of float32 numpy arrays::
     quat [N,4] (w,x,y,z; not normalised)  opacity [N]  sh [N,(D+1)^2,3]
 
 and a camera is a dict with ``viewmat`` (3x4), ``fx fy cx cy``, ``width``,
-``height``, ``t``, ``z_near`` and ``bg`` (3,).
+``height``, ``t``, ``z_near``, ``bg`` (3,) and ``dt`` (temporal-smoothing
+shift of the rendered state, 0 for a plain render).
 """
 from __future__ import annotations
 
@@ -196,14 +197,14 @@ def look_at(eye, target, up):
 
 
 def make_camera(viewmat, width, height, fx, fy=None, cx=None, cy=None, t=0.5,
-                z_near=0.2, bg=(0.0, 0.0, 0.0)):
+                z_near=0.2, bg=(0.0, 0.0, 0.0), dt=0.0):
     fy = fx if fy is None else fy
     cx = width / 2.0 if cx is None else cx
     cy = height / 2.0 if cy is None else cy
     return dict(viewmat=np.asarray(viewmat, np.float32).reshape(3, 4),
                 fx=float(fx), fy=float(fy), cx=float(cx), cy=float(cy),
                 width=int(width), height=int(height), t=float(t),
-                z_near=float(z_near), bg=np.asarray(bg, np.float32).reshape(3))
+                z_near=float(z_near), bg=np.asarray(bg, np.float32).reshape(3), dt=float(dt))
 
 
 def focal_from_hfov(width, hfov_deg):

@@ -163,12 +163,13 @@ def _loss(sc, cam, w_rgb, w_d, w_a, opts=None):
     return float((out["rgb"] * w_rgb).sum() + (out["depth"] * w_d).sum() + (out["alpha"] * w_a).sum())
 
 
-@pytest.mark.parametrize("degree", [0, 3])
-def test_backward_matches_finite_differences(degree):
+@pytest.mark.parametrize("degree,dt", [(0, 0.0), (3, 0.0), (3, 0.04)])
+def test_backward_matches_finite_differences(degree, dt):
     rng = np.random.default_rng(7 + degree)
     sc = synth.make_fd_scene(seed=degree, n=60, sh_degree=degree)
     sc = {k: v.astype(np.float64) for k, v in sc.items()}
     cam = synth.fd_camera(32, 24, t=0.45)
+    cam["dt"] = dt  # dt != 0: the flow-translated state of Sec. 3.4
     cam["bg"] = np.array([0.2, 0.5, 0.8], np.float32)
     W, H = cam["width"], cam["height"]
     w_rgb = rng.normal(size=(H, W, 3))

@@ -269,3 +269,45 @@ def test_near_plane_and_opacity_culls():
     assert oracle.preprocess(behind, cam)["valid"][0] == 0
     faint = _single([0.0, 0.0, 0.0], [0.05] * 3, [1, 0, 0, 0], opacity=0.5 / 255)
     assert oracle.preprocess(faint, cam)["valid"][0] == 0
+
+
+# --------------------------------------------------------------------------
+# flow translation (Sec. 3.4, temporal smoothing, Eq. 10 and the H^ state)
+# --------------------------------------------------------------------------
+
+def test_flow_translation_at_paper_settings():
+    # beta = 0.3 and l = 0.2 (the paper's initial beta and fixed l) give
+    # rho = 1.5, so the average velocity is v exp(-0.75): the shifted
+    # state moves by v exp(-0.75) dt relative to the state at t - dt.
+    g = json.load(open(GOLDEN))
+    sc = _scene()
+    sc["beta"] = np.full(sc["beta"].shape, g["beta_init"]["value"])
+    sc["period"] = np.full(sc["period"].shape, g["cycle_length_l"]["value"])
+    t, dt = 0.5, 0.03
+    shifted, o_sh = oracle.time_eval(sc, t, dt)
+    base, o_base = oracle.time_eval(sc, t - dt)
+    np.testing.assert_allclose((shifted - base) / dt, sc["vel"].astype(np.float64) * math.exp(-0.75), rtol=1e-9,
+                               atol=1e-12)
+    np.testing.assert_array_equal(o_sh, o_base)  # opacity is the one at t - dt
+
+
+def test_flow_translation_static_limit():
+    # rho -> inf: v_bar -> 0, the shifted state is the state at t - dt
+    sc = _scene()
+    sc["beta"] = np.full(sc["beta"].shape, 1e6)
+    shifted, _ = oracle.time_eval(sc, 0.6, 0.05)
+    base, _ = oracle.time_eval(sc, 0.55)
+    np.testing.assert_allclose(shifted, base, atol=1e-12)
+
+
+def test_flow_translation_linear_limit_reproduces_the_motion():
+    # l -> inf (linear motion mu + v (t - tau)) and rho = beta / l -> 0
+    # (v_bar -> v): translating the state at t - dt by v dt lands exactly on
+    # the state at t -- constant speed makes consecutive states linear.
+    sc = _scene()
+    sc["period"] = np.full(sc["period"].shape, 1e7)
+    sc["beta"] = np.full(sc["beta"].shape, 1e-3)
+    for dt in (-0.04, 0.02, 0.1):
+        shifted, _ = oracle.time_eval(sc, 0.37, dt)
+        exact, _ = oracle.time_eval(sc, 0.37)
+        np.testing.assert_allclose(shifted, exact, atol=1e-9)
