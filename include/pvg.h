@@ -104,7 +104,10 @@ typedef struct {
     float t;            /* render time (Sec. 3.2: normalised timestamps) */
     float z_near;       /* points with camera depth <= z_near are culled */
     float bg[3];        /* constant background colour (C += T_final bg) */
-    float reserved;
+    float dt;           /* temporal smoothing (Sec. 3.4): 0 renders H(t); otherwise
+                         * the flow-translated state: every point queried at
+                         * t - dt and moved by v_bar dt, v_bar = v exp(-beta/(2 l))
+                         * (Eq. 10), with its opacity at t - dt */
 } pvg_camera_t;
 
 /* Output images of one view (device memory, caller-owned):

@@ -35,7 +35,7 @@ class Scene(C.Structure):
 class Camera(C.Structure):
     _fields_ = [("viewmat", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
                 ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("t", C.c_float),
-                ("z_near", C.c_float), ("bg", C.c_float * 3), ("reserved", C.c_float)]
+                ("z_near", C.c_float), ("bg", C.c_float * 3), ("dt", C.c_float)]
 
 
 class Image(C.Structure):
@@ -160,6 +160,7 @@ def camera(cam) -> Camera:
     c.z_near = float(cam.get("z_near", 0.2))
     bg = list(cam.get("bg", (0.0, 0.0, 0.0)))
     c.bg[:] = [float(b) for b in bg]
+    c.dt = float(cam.get("dt", 0.0))
     return c
 
 

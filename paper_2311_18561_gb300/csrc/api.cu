@@ -345,6 +345,8 @@ static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *scenes, int
             d.campos[k] = -(d.R[k] * d.T[0] + d.R[3 + k] * d.T[1] + d.R[6 + k] * d.T[2]);
         d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
         d.t = c.t; d.znear = c.z_near;
+        if (!std::isfinite(c.dt)) return PVG_ERR_INVALID;
+        d.dt = c.dt;
         d.bg[0] = c.bg[0]; d.bg[1] = c.bg[1]; d.bg[2] = c.bg[2];
         d.limx = x->cfg.fov_clamp * 0.5f * (float)c.width / c.fx;
         d.limy = x->cfg.fov_clamp * 0.5f * (float)c.height / c.fy;

@@ -48,6 +48,7 @@ constexpr float kInv2Pi = 0.15915494309189535f;  // 1 / (2 pi)
 struct Fwd {
     // time terms
     float delta, sn, cs, egate, amp;
+    float vbw;          // exp(-beta / (2 l)) when the view has a flow shift
     float3 mut;
     float ot;
     // camera space
@@ -123,9 +124,16 @@ __device__ __forceinline__ bool project(const ViewDesc &V, uint32_t i, float dil
                                         Fwd &F) {
     // Eq. 6 / Eq. 7
     const float tau = V.tau[i], l = V.period[i], beta = V.beta[i];
-    F.delta = V.t - tau;
+    // with dt != 0 the flow-translated state of Sec. 3.4: queried at t - dt,
+    // moved by v_bar dt, v_bar = v exp(-rho / 2), rho = beta / l (Eq. 10)
+    F.delta = (V.t - V.dt) - tau;
     sincospif(2.0f * F.delta / l, &F.sn, &F.cs);
     F.amp = l * F.sn * kInv2Pi;
+    F.vbw = 0.f;
+    if (V.dt != 0.f) {
+        F.vbw = expf(-0.5f * beta / l);
+        F.amp = F.amp + V.dt * F.vbw;
+    }
     const float3 mu = ld3(V.mu, i), vel = ld3(V.vel, i);
     F.mut = make_float3(mu.x + F.amp * vel.x, mu.y + F.amp * vel.y, mu.z + F.amp * vel.z);
     F.egate = expf(-0.5f * (F.delta * F.delta) / (beta * beta));
@@ -543,9 +551,12 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
                 for (int k = 0; k < 3; k++) put(V.g_vel, 3 * (size_t)i + k, gmut[k] * F.amp, atomic);
             const float ib2 = 1.0f / (beta * beta);
             if (V.g_tau) put(V.g_tau, i, -F.cs * gvd + got * F.ot * F.delta * ib2, atomic);
-            if (V.g_period) put(V.g_period, i, gvd * (F.sn * kInv2Pi - F.delta / l * F.cs), atomic);
+            // flow shift dt v exp(-beta / (2 l)): its beta and l terms
+            const float gsh = gvd * V.dt * F.vbw;
+            if (V.g_period)
+                put(V.g_period, i, gvd * (F.sn * kInv2Pi - F.delta / l * F.cs) + gsh * (0.5f * beta / (l * l)), atomic);
             if (V.g_opac) put(V.g_opac, i, got * F.egate, atomic);
-            if (V.g_beta) put(V.g_beta, i, got * F.ot * F.delta * F.delta * ib2 / beta, atomic);
+            if (V.g_beta) put(V.g_beta, i, got * F.ot * F.delta * F.delta * ib2 / beta - gsh * (0.5f / l), atomic);
         }
     }
 }

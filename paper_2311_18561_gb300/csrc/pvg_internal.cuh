@@ -29,6 +29,7 @@ struct ViewDesc {
     float R[9], T[3];  // world->camera
     float fx, fy, cx, cy;
     float t, znear;
+    float dt;          // temporal-smoothing shift (0: plain render)
     float bg[3];
     float campos[3];   // camera centre in world space, -R^T T
     float limx, limy;  // J clamp on x/z and y/z

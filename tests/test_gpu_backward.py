@@ -39,11 +39,13 @@ def _weights(H, W, seed):
     return rng.normal(size=(3, H, W)), rng.normal(size=(H, W)) * 0.1, rng.normal(size=(H, W))
 
 
-@pytest.mark.parametrize("deg", [0, 3])
-def test_backward_matches_oracle_fd_subcase(deg):
-    """The 500-Gaussian, 64x48 sub-case of the training config."""
+@pytest.mark.parametrize("deg,dt", [(0, 0.0), (3, 0.0), (3, 0.04)])
+def test_backward_matches_oracle_fd_subcase(deg, dt):
+    """The 500-Gaussian, 64x48 sub-case of the training config (dt != 0:
+    the flow-translated state of Sec. 3.4)."""
     scene = synth.make_fd_scene(seed=0, n=500, sh_degree=deg)
     cam = synth.fd_camera(64, 48, t=0.45)
+    cam["dt"] = dt
     cam["bg"] = np.array([0.2, 0.5, 0.8], np.float32)
     H, W = cam["height"], cam["width"]
     w_rgb, w_d, w_a = _weights(H, W, 1)

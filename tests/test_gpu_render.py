@@ -225,3 +225,17 @@ def test_no_sync_mode_matches_and_reports_overflow():
     gpu_render(small, st, [cam], frame=fr2)
     m, k, ov = fr2.stats()
     assert ov == 1 and k > 64
+
+
+@pytest.mark.parametrize("dt", [0.03, -0.05])
+def test_flow_translated_state_matches_oracle(renderer, dt):
+    """Temporal smoothing (Sec. 3.4): rendering the flow-translated state."""
+    scene = synth.make_fd_scene(seed=13, n=900, sh_degree=3)
+    cam = synth.fd_camera(80, 60, t=0.4)
+    cam["dt"] = dt
+    out = gpu_render(renderer, R.scene_to_device(scene), [cam])[0]
+    compare_to_oracle(to_numpy_images(out), oracle.render(scene, cam))
+    plain = dict(cam)
+    plain["dt"] = 0.0
+    ref_plain = gpu_render(renderer, R.scene_to_device(scene), [plain])[0]
+    assert not torch.equal(out["rgb"], ref_plain["rgb"])
