@@ -43,9 +43,10 @@ def load():
         lib.pvgo_time_eval.argtypes = [C.c_int64] + [P] * 6 + [C.c_double, C.c_double, P, P]
         lib.pvgo_sh_basis.argtypes = [C.c_int, C.c_int64, P, P, P]
         lib.pvgo_preprocess.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 9
-        lib.pvgo_render.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + [P] * 6
-        lib.pvgo_render_bwd.argtypes = ([C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + [P] * 3
-                                        + [P] * 10)
+        sky = [P, C.c_int, P]
+        lib.pvgo_render.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + sky + [P] * 6
+        lib.pvgo_render_bwd.argtypes = ([C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + sky
+                                        + [P] * 3 + [P] * 11)
         lib.pvgo_num_threads.argtypes = []
         for f in (lib.pvgo_time_eval, lib.pvgo_sh_basis, lib.pvgo_preprocess, lib.pvgo_render,
                   lib.pvgo_render_bwd, lib.pvgo_num_threads):
@@ -130,12 +131,25 @@ def preprocess(scene, cam, opts=None):
     return out
 
 
-def render(scene, cam, opts=None, mode="brute", pixels=None):
+def _sky_args(sky, jitter):
+    """sky: None or [6, R, R, 3] cube map; jitter: None or [2, H, W] pixel
+    offsets of the sky rays."""
+    if sky is None:
+        return None, 0, None, None
+    sk = _d(sky)
+    jt = None if jitter is None else _d(jitter)
+    return sk, int(sk.shape[1]), jt, (_p(sk), int(sk.shape[1]), _p(jt))
+
+
+def render(scene, cam, opts=None, mode="brute", pixels=None, sky=None, sky_jitter=None):
     """Steps 5/6.  mode 'brute' or 'culled'.  pixels: None for the full
     image (outputs shaped [H, W, ...]) or an int array [P, 2] of (px, py)
-    (outputs shaped [P, ...]).  Returns dict rgb, depth, alpha, T, nblend,
-    flag."""
+    (outputs shaped [P, ...]).  sky: optional cube map (see _sky_args).
+    Returns dict rgb, depth, alpha, T, nblend, flag."""
     n, deg, arrs = _scene_args(scene)
+    sk, res, jt, skp = _sky_args(sky, sky_jitter)
+    if skp is None:
+        skp = (None, 0, None)
     W, H = int(cam["width"]), int(cam["height"])
     if pixels is None:
         P = W * H
@@ -147,7 +161,7 @@ def render(scene, cam, opts=None, mode="brute", pixels=None):
                nblend=np.zeros(P, np.int32), flag=np.zeros(P, np.int32))
     ca, oa = cam_array(cam), opt_array(opts)
     m = {"brute": 0, "culled": 1}[mode]
-    rc = load().pvgo_render(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, P, _p(pix),
+    rc = load().pvgo_render(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, P, _p(pix), *skp,
                             *[_p(out[k]) for k in ("rgb", "depth", "alpha", "T", "nblend", "flag")])
     if rc != 0:
         raise ValueError("oracle render rejected its inputs")
@@ -160,7 +174,7 @@ GRAD_NAMES = ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", 
 
 
 def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=False, mode="brute",
-               pixels=None):
+               pixels=None, sky=None, sky_jitter=None):
     """Gradients of sum(dL_rgb*rgb) + sum(dL_depth*depth) + sum(dL_alpha*alpha)
     w.r.t. every parameter, as a dict keyed like the scene.  Full image
     (dL_rgb [H,W,3], others [H,W]) or, with ``pixels`` [P,2], only those
@@ -176,9 +190,16 @@ def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=Fal
     pix = None if pixels is None else np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
     npix = 0 if pix is None else pix.shape[0]
     m = {"brute": 0, "culled": 1}[mode]
-    rc = load().pvgo_render_bwd(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, npix, _p(pix),
+    sk, res, jt, skp = _sky_args(sky, sky_jitter)
+    dsky = None
+    if skp is None:
+        skp = (None, 0, None)
+    else:
+        dsky = np.zeros_like(sk)
+        g["sky"] = dsky
+    rc = load().pvgo_render_bwd(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, npix, _p(pix), *skp,
                                 _p(gr), _p(gd), _p(ga),
-                                *[_p(g[name]) for name in GRAD_NAMES], _p(g2d))
+                                *[_p(g[name]) for name in GRAD_NAMES], _p(g2d), _p(dsky))
     if rc != 0:
         raise ValueError("oracle backward rejected its inputs")
     if return_g2d:

@@ -400,14 +400,76 @@ int pvgo_preprocess(int64_t n, int degree, const double *mu, const double *vel, 
 /* ------------------------------------------------------------------ */
 static int near_gate(double v, double thr) { return fabs(v - thr) <= 1e-5 * thr; }
 
+/* ------------------------------------------------------------------ */
+/* sky cube map (Sec. 3.4, sky refinement)                             */
+/* ------------------------------------------------------------------ */
+/* Background C_f = C + (1 - O) f_sky(d): d is the world direction of the
+ * pixel's ray (sample point jittered by jitter[2][H][W] pixels if given),
+ * f_sky a cube map of 6 faces x res x res RGB texels, faces +X -X +Y -Y +Z
+ * -Z, face coordinates of the OpenGL cube-map convention, bilinear
+ * filtering inside a face with edge texels clamped. */
+typedef struct { const double *tex; int res; const double *jitter; } sky_t;
+
+static void sky_texels(const sky_t *K, const double *cam, int px, int py, int64_t idx[4], double w[4])
+{
+    const int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
+    double sx = px + 0.5, sy = py + 0.5;
+    if (K->jitter) {
+        sx += K->jitter[(int64_t)py * W + px];
+        sy += K->jitter[(int64_t)H * W + (int64_t)py * W + px];
+    }
+    const double dc[3] = {(sx - cam[CAM_CX]) / cam[CAM_FX], (sy - cam[CAM_CY]) / cam[CAM_FY], 1.0};
+    double d[3];
+    for (int k = 0; k < 3; k++) d[k] = cam[0 + k] * dc[0] + cam[4 + k] * dc[1] + cam[8 + k] * dc[2];
+    const double ax = fabs(d[0]), ay = fabs(d[1]), az = fabs(d[2]);
+    int face;
+    double sc, tc, ma;
+    if (ax >= ay && ax >= az) {
+        ma = ax;
+        if (d[0] > 0) { face = 0; sc = -d[2]; tc = -d[1]; } else { face = 1; sc = d[2]; tc = -d[1]; }
+    } else if (ay >= az) {
+        ma = ay;
+        if (d[1] > 0) { face = 2; sc = d[0]; tc = d[2]; } else { face = 3; sc = d[0]; tc = -d[2]; }
+    } else {
+        ma = az;
+        if (d[2] > 0) { face = 4; sc = d[0]; tc = -d[1]; } else { face = 5; sc = -d[0]; tc = -d[1]; }
+    }
+    const double s = 0.5 * (sc / ma + 1.0), t = 0.5 * (tc / ma + 1.0);
+    const int R = K->res;
+    const double x = s * R - 0.5, y = t * R - 0.5;
+    const double x0f = floor(x), y0f = floor(y);
+    const double fx = x - x0f, fy = y - y0f;
+    int x0 = (int)x0f, y0 = (int)y0f, x1 = x0 + 1, y1 = y0 + 1;
+    x0 = x0 < 0 ? 0 : (x0 > R - 1 ? R - 1 : x0);
+    x1 = x1 < 0 ? 0 : (x1 > R - 1 ? R - 1 : x1);
+    y0 = y0 < 0 ? 0 : (y0 > R - 1 ? R - 1 : y0);
+    y1 = y1 < 0 ? 0 : (y1 > R - 1 ? R - 1 : y1);
+    const int64_t base = (int64_t)face * R * R;
+    idx[0] = base + (int64_t)y0 * R + x0; w[0] = (1 - fx) * (1 - fy);
+    idx[1] = base + (int64_t)y0 * R + x1; w[1] = fx * (1 - fy);
+    idx[2] = base + (int64_t)y1 * R + x0; w[2] = (1 - fx) * fy;
+    idx[3] = base + (int64_t)y1 * R + x1; w[3] = fx * fy;
+}
+
+static void sky_value(const sky_t *K, const double *cam, int px, int py, double out[3])
+{
+    int64_t idx[4];
+    double w[4];
+    sky_texels(K, cam, px, py, idx, w);
+    for (int c = 0; c < 3; c++) {
+        out[c] = 0.0;
+        for (int k = 0; k < 4; k++) out[c] += w[k] * K->tex[idx[k] * 3 + c];
+    }
+}
+
 /* composite one pixel (px, py) over the depth-ordered list.  out receives
  * r, g, b, depth, opacity and the final transmittance; if `blend` is
  * non-NULL it receives the blended list (indices, alpha, T, G, offsets) */
 typedef struct { int64_t idx; double alpha, T, G, dx, dy; int capped; } blend_t;
 
 static void composite_pixel(const gauss_t *G, const int64_t *order, int64_t m, int culled, int px, int py,
-                            const double *cam, const double *opt, double out[6], int32_t *nblend,
-                            int32_t *flag, blend_t *blend)
+                            const double *cam, const double *opt, const sky_t *sky, double out[6],
+                            int32_t *nblend, int32_t *flag, blend_t *blend)
 {
     const double sx = px + 0.5, sy = py + 0.5;
     double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, O = 0.0, zprev = -1.0;
@@ -436,7 +498,13 @@ static void composite_pixel(const gauss_t *G, const int64_t *order, int64_t m, i
         T = Tn;
         nb++;
     }
-    for (int c = 0; c < 3; c++) out[c] = C[c] + T * cam[CAM_BG + c];
+    if (sky && sky->tex) {
+        double f[3];
+        sky_value(sky, cam, px, py, f);
+        for (int c = 0; c < 3; c++) out[c] = C[c] + (1.0 - O) * f[c];
+    } else {
+        for (int c = 0; c < 3; c++) out[c] = C[c] + T * cam[CAM_BG + c];
+    }
     out[3] = D;
     out[4] = O;
     out[5] = T;
@@ -453,9 +521,10 @@ static void composite_pixel(const gauss_t *G, const int64_t *order, int64_t m, i
 int pvgo_render(int64_t n, int degree, const double *mu, const double *vel, const double *tau,
                 const double *beta, const double *period, const double *scale, const double *quat,
                 const double *opac, const double *sh, const double *cam, const double *opt, int mode,
-                int64_t npix, const int32_t *pix, double *rgb, double *depth, double *alpha, double *Tout,
-                int32_t *nblend, int32_t *flag)
+                int64_t npix, const int32_t *pix, const double *sky_tex, int sky_res, const double *sky_jitter,
+                double *rgb, double *depth, double *alpha, double *Tout, int32_t *nblend, int32_t *flag)
 {
+    const sky_t sky = {sky_tex, sky_res, sky_jitter};
     if (degree < 0 || degree > 3 || n < 0) return -1;
     const int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
     if (W <= 0 || H <= 0) return -1;
@@ -471,7 +540,7 @@ int pvgo_render(int64_t n, int degree, const double *mu, const double *vel, cons
         const int py = pix ? pix[2 * k + 1] : (int)(k / W);
         double out[6];
         int32_t nb, fl;
-        composite_pixel(G, order, m, mode == 1, px, py, cam, opt, out, &nb, &fl, NULL);
+        composite_pixel(G, order, m, mode == 1, px, py, cam, opt, &sky, out, &nb, &fl, NULL);
         if (rgb) { rgb[3 * k] = out[0]; rgb[3 * k + 1] = out[1]; rgb[3 * k + 2] = out[2]; }
         if (depth) depth[k] = out[3];
         if (alpha) alpha[k] = out[4];
@@ -670,7 +739,8 @@ static void backward_one(const scene_t *S, int64_t i, const gauss_t *g, const do
 }
 
 /* exported: gradients of L = sum(dL_rgb . rgb) + sum(dL_depth depth) +
- * sum(dL_alpha alpha) w.r.t. every parameter, over the full image
+ * sum(dL_alpha alpha) w.r.t. every parameter (and the sky texels, if a sky
+ * map is given: dsky[6 res res 3]), over the full image
  * (pix = NULL, row-major pixels) or over the P listed (px, py) pixels
  * (dL arrays then indexed by list position); mode 0 brute force, 1 culled
  * (same result).  Gradient arrays are overwritten.  If g2d is non-NULL it
@@ -679,11 +749,14 @@ static void backward_one(const scene_t *S, int64_t i, const gauss_t *g, const do
 int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, const double *tau,
                     const double *beta, const double *period, const double *scale, const double *quat,
                     const double *opac, const double *sh, const double *cam, const double *opt, int mode,
-                    int64_t npix, const int32_t *pix,
-                    const double *dL_rgb, const double *dL_depth, const double *dL_alpha, double *dmu,
-                    double *dvel, double *dtau, double *dbeta, double *dperiod, double *dscale, double *dquat,
-                    double *dopac, double *dsh, double *g2d)
+                    int64_t npix, const int32_t *pix, const double *sky_tex, int sky_res,
+                    const double *sky_jitter, const double *dL_rgb, const double *dL_depth,
+                    const double *dL_alpha, double *dmu, double *dvel, double *dtau, double *dbeta,
+                    double *dperiod, double *dscale, double *dquat, double *dopac, double *dsh, double *g2d,
+                    double *dsky)
 {
+    const sky_t sky = {sky_tex, sky_res, sky_jitter};
+    if (sky_tex && dsky) memset(dsky, 0, sizeof(double) * 18 * (size_t)sky_res * (size_t)sky_res);
     if (degree < 0 || degree > 3 || n < 0) return -1;
     const int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
     const int K = (degree + 1) * (degree + 1);
@@ -716,12 +789,31 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
             const int py = pix ? pix[2 * k + 1] : (int)(k / W);
             double out[6];
             int32_t nb;
-            composite_pixel(G, order, m, mode == 1, px, py, cam, opt, out, &nb, NULL, bl);
+            composite_pixel(G, order, m, mode == 1, px, py, cam, opt, &sky, out, &nb, NULL, bl);
             const double Tfin = out[5];
             const double gC[3] = {dL_rgb[3 * k], dL_rgb[3 * k + 1], dL_rgb[3 * k + 2]};
-            const double gD = dL_depth[k], gO = dL_alpha[k];
+            const double gD = dL_depth[k];
+            double gO = dL_alpha[k];
             /* suffix sums S_j = sum_{m > j} x_m alpha_m T_m (+ bg T_final for colour) */
             double sC[3] = {Tfin * cam[CAM_BG], Tfin * cam[CAM_BG + 1], Tfin * cam[CAM_BG + 2]};
+            if (sky.tex) {
+                /* colour = C + (1 - O) f: dL/dO gains -gC.f, dL/df = (1 - O) gC,
+                 * and no constant background */
+                int64_t ti[4];
+                double tw[4], f[3] = {0, 0, 0};
+                sky_texels(&sky, cam, px, py, ti, tw);
+                for (int c = 0; c < 3; c++) {
+                    for (int q = 0; q < 4; q++) f[c] += tw[q] * sky.tex[ti[q] * 3 + c];
+                    gO -= gC[c] * f[c];
+                    sC[c] = 0.0;
+                }
+                if (dsky) {
+                    const double wO = 1.0 - out[4];
+#pragma omp critical(pvgo_sky)
+                    for (int q = 0; q < 4; q++)
+                        for (int c = 0; c < 3; c++) dsky[ti[q] * 3 + c] += tw[q] * wO * gC[c];
+                }
+            }
             double sD = 0.0, sO = 0.0;
             for (int j = nb - 1; j >= 0; j--) {
                 const blend_t *e = &bl[j];
