@@ -88,12 +88,19 @@ int pvg_version(void);
  *   opacity [N]    o in [0, 1] (physical, not a logit)
  *   sh      [N,(D+1)^2,3] colour coefficients, D = sh_degree in 0..3
  * Every array must be 4-byte aligned; mu, vel, scale, quat and sh may be
- * any alignment of float.  N = 0 is allowed (renders the background). */
+ * any alignment of float.  N = 0 is allowed (renders the background).
+ *   sky     [6,R,R,3] optional learnable sky cube map (Sec. 3.4, sky
+ *           refinement): when non-NULL the background of every view is
+ *           (1 - O) f_sky(d) instead of T_final bg, d the pixel's world ray
+ *           direction, faces +X -X +Y -Y +Z -Z with the OpenGL cube-map
+ *           face coordinates, bilinear inside a face, edges clamped;
+ *           R = sky_res (>= 1). */
 typedef struct {
     int64_t n;
     int32_t sh_degree;
-    int32_t reserved;
+    int32_t sky_res;
     const float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opacity, *sh;
+    const float *sky;
 } pvg_scene_t;
 
 /* A pinhole camera at time t (host memory). */
@@ -108,6 +115,9 @@ typedef struct {
                          * the flow-translated state: every point queried at
                          * t - dt and moved by v_bar dt, v_bar = v exp(-beta/(2 l))
                          * (Eq. 10), with its opacity at t - dt */
+    const float *sky_jitter; /* optional DEVICE array [2,H,W]: x and y offsets in
+                         * pixels of each pixel's sky ray (the paper jitters the
+                         * sky ray within its pixel during training); NULL = 0 */
 } pvg_camera_t;
 
 /* Output images of one view (device memory, caller-owned):
@@ -126,9 +136,11 @@ typedef struct {
 
 /* Parameter gradients, same layouts as pvg_scene_t (device, caller-owned).
  * pvg_render_bwd zeroes them and then writes dL/dparam summed over all
- * views.  A NULL array is neither zeroed nor written. */
+ * views.  A NULL array is neither zeroed nor written.  sky: dL/d(sky
+ * texels), used when the scene has a sky map. */
 typedef struct {
     float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opacity, *sh;
+    float *sky;
 } pvg_scene_grad_t;
 
 /* ------------------------------------------------------------------ */

@@ -28,14 +28,15 @@ class PVGError(RuntimeError):
 
 
 class Scene(C.Structure):
-    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("reserved", C.c_int32)] + [
-        (k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh")]
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("sky_res", C.c_int32)] + [
+        (k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh", "sky")]
 
 
 class Camera(C.Structure):
     _fields_ = [("viewmat", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
                 ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("t", C.c_float),
-                ("z_near", C.c_float), ("bg", C.c_float * 3), ("dt", C.c_float)]
+                ("z_near", C.c_float), ("bg", C.c_float * 3), ("dt", C.c_float),
+                ("sky_jitter", C.c_void_p)]
 
 
 class Image(C.Structure):
@@ -47,7 +48,8 @@ class ImageGrad(C.Structure):
 
 
 class SceneGrad(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh")]
+    _fields_ = [(k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh",
+                                          "sky")]
 
 
 class Config(C.Structure):
@@ -161,6 +163,8 @@ def camera(cam) -> Camera:
     bg = list(cam.get("bg", (0.0, 0.0, 0.0)))
     c.bg[:] = [float(b) for b in bg]
     c.dt = float(cam.get("dt", 0.0))
+    jit = cam.get("sky_jitter")
+    c.sky_jitter = jit.data_ptr() if jit is not None else None
     return c
 
 

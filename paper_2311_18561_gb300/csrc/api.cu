@@ -310,6 +310,7 @@ static bool finite3x4(const float *m) {
 
 static pvg_status_t validate_scene(const pvg_scene_t *sc) {
     if (!sc || sc->n < 0 || sc->sh_degree < 0 || sc->sh_degree > 3) return PVG_ERR_INVALID;
+    if (sc->sky && (sc->sky_res < 1 || sc->sky_res > 16384)) return PVG_ERR_INVALID;
     if (sc->n > 0 && (!sc->mu || !sc->vel || !sc->tau || !sc->beta || !sc->period || !sc->scale || !sc->quat ||
                       !sc->opacity || !sc->sh))
         return PVG_ERR_INVALID;
@@ -360,6 +361,9 @@ static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *scenes, int
         d.sh_degree = sc->sh_degree;
         d.mu = sc->mu; d.vel = sc->vel; d.tau = sc->tau; d.beta = sc->beta; d.period = sc->period;
         d.scale = sc->scale; d.quat = sc->quat; d.opac = sc->opacity; d.sh = sc->sh;
+        d.sky = sc->sky;
+        d.sky_res = sc->sky_res;
+        d.sky_jitter = c.sky_jitter;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
         pix += (uint64_t)c.width * c.height;
         items += (uint64_t)sc->n;
@@ -655,6 +659,8 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
         ViewDesc &d = views[v];
         d.mu = scene->mu; d.vel = scene->vel; d.tau = scene->tau; d.beta = scene->beta; d.period = scene->period;
         d.scale = scene->scale; d.quat = scene->quat; d.opac = scene->opacity; d.sh = scene->sh;
+        d.sky = scene->sky; d.sky_res = scene->sky_res;
+        d.g_sky = scene->sky ? grads->sky : nullptr;
         d.dl_rgb = dL[v].rgb; d.dl_depth = dL[v].depth; d.dl_alpha = dL[v].alpha;
         d.g_mu = grads->mu; d.g_vel = grads->vel; d.g_tau = grads->tau; d.g_beta = grads->beta;
         d.g_period = grads->period; d.g_scale = grads->scale; d.g_quat = grads->quat; d.g_opac = grads->opacity;
@@ -669,7 +675,9 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     if (n_views > 1 || f->n_items == 0)
         for (auto &z : zero)
             if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
-    if (f->n_items == 0) return PVG_OK;
+    if (scene->sky && grads->sky)
+        PVG_CUDA(cudaMemsetAsync(grads->sky, 0, sizeof(float) * 18 * (size_t)scene->sky_res * scene->sky_res, s));
+    if (f->n_items == 0 && !scene->sky) return PVG_OK;
     if (capturing && f->g2d.bytes < sizeof(float) * 10 * (size_t)f->n_items) return PVG_ERR_INVALID;
     PVG_TRY(ensure(f->g2d, sizeof(float) * 10 * (size_t)f->n_items));
     PVG_TRY(stage_views(*f->stage_bwd, views, s, capturing));

@@ -43,11 +43,15 @@ struct ViewDesc {
     int32_t pad0;
     // scene
     const float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opac, *sh;
+    const float *sky;        // [6][R][R][3] cube map or NULL (constant bg)
+    const float *sky_jitter; // [2][H][W] pixel offsets of the sky rays or NULL
+    int32_t sky_res, pad1;
     // outputs
     float *out_rgb, *out_depth, *out_alpha;
     // backward inputs / outputs
     const float *dl_rgb, *dl_depth, *dl_alpha;
     float *g_mu, *g_vel, *g_tau, *g_beta, *g_period, *g_scale, *g_quat, *g_opac, *g_sh;
+    float *g_sky;
 };
 
 // Launch-wide parameters.
@@ -121,6 +125,47 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float falloff_exp2(float ap, float bp, float cp, float dx, float dy) {
     const float t = __fmaf_rn(bp, dy, __fmul_rn(ap, dx));
     return __fmaf_rn(__fmul_rn(cp, dy), dy, __fmul_rn(dx, t));
+}
+
+// Sky background (Sec. 3.4, C_f = C + (1 - O) f_sky(d)): the four texels
+// (index of the texel's first channel) and bilinear weights that the ray of
+// pixel (px, py) samples.  d = R^T ((x - cx)/fx, (y - cy)/fy, 1) at the
+// (jittered) pixel centre; faces +X -X +Y -Y +Z -Z with the OpenGL
+// cube-map face coordinates; bilinear inside the face, edges clamped.
+__device__ __forceinline__ void sky_texels(const ViewDesc &V, int px, int py, size_t idx[4], float w[4]) {
+    float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    if (V.sky_jitter) {
+        const size_t q = (size_t)py * V.W + px;
+        sx += V.sky_jitter[q];
+        sy += V.sky_jitter[(size_t)V.W * V.H + q];
+    }
+    const float dcx = (sx - V.cx) / V.fx, dcy = (sy - V.cy) / V.fy;
+    float d[3];
+    for (int k = 0; k < 3; k++) d[k] = V.R[k] * dcx + V.R[3 + k] * dcy + V.R[6 + k];
+    const float ax = fabsf(d[0]), ay = fabsf(d[1]), az = fabsf(d[2]);
+    int face;
+    float sc, tc, ma;
+    if (ax >= ay && ax >= az) {
+        ma = ax;
+        if (d[0] > 0.f) { face = 0; sc = -d[2]; tc = -d[1]; } else { face = 1; sc = d[2]; tc = -d[1]; }
+    } else if (ay >= az) {
+        ma = ay;
+        if (d[1] > 0.f) { face = 2; sc = d[0]; tc = d[2]; } else { face = 3; sc = d[0]; tc = -d[2]; }
+    } else {
+        ma = az;
+        if (d[2] > 0.f) { face = 4; sc = d[0]; tc = -d[1]; } else { face = 5; sc = -d[0]; tc = -d[1]; }
+    }
+    const int R = V.sky_res;
+    const float x = 0.5f * (sc / ma + 1.0f) * R - 0.5f, y = 0.5f * (tc / ma + 1.0f) * R - 0.5f;
+    const float x0f = floorf(x), y0f = floorf(y);
+    const float fx = x - x0f, fy = y - y0f;
+    const int x0 = min(max((int)x0f, 0), R - 1), x1 = min(max((int)x0f + 1, 0), R - 1);
+    const int y0 = min(max((int)y0f, 0), R - 1), y1 = min(max((int)y0f + 1, 0), R - 1);
+    const size_t base = (size_t)face * R * R;
+    idx[0] = 3 * (base + (size_t)y0 * R + x0); w[0] = (1.f - fx) * (1.f - fy);
+    idx[1] = 3 * (base + (size_t)y0 * R + x1); w[1] = fx * (1.f - fy);
+    idx[2] = 3 * (base + (size_t)y1 * R + x0); w[2] = (1.f - fx) * fy;
+    idx[3] = 3 * (base + (size_t)y1 * R + x1); w[3] = fx * fy;
 }
 
 }  // namespace pvg

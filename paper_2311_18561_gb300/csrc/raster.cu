@@ -149,9 +149,24 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
             P.pix_neval[P.total_pix + V.pix_base + pix] = nblend[p];
             continue;
         }
-        V.out_rgb[pix] = C0[p] + T[p] * V.bg[0];
-        V.out_rgb[HW + pix] = C1[p] + T[p] * V.bg[1];
-        V.out_rgb[2 * HW + pix] = C2[p] + T[p] * V.bg[2];
+        if (V.sky) {  // C + (1 - O) f_sky(d)
+            size_t ti[4];
+            float tw[4];
+            sky_texels(V, G.px, py, ti, tw);
+            float f[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                f[c] = tw[0] * V.sky[ti[0] + c] + tw[1] * V.sky[ti[1] + c] + tw[2] * V.sky[ti[2] + c] +
+                       tw[3] * V.sky[ti[3] + c];
+            const float wo = 1.0f - O[p];
+            V.out_rgb[pix] = C0[p] + wo * f[0];
+            V.out_rgb[HW + pix] = C1[p] + wo * f[1];
+            V.out_rgb[2 * HW + pix] = C2[p] + wo * f[2];
+        } else {
+            V.out_rgb[pix] = C0[p] + T[p] * V.bg[0];
+            V.out_rgb[HW + pix] = C1[p] + T[p] * V.bg[1];
+            V.out_rgb[2 * HW + pix] = C2[p] + T[p] * V.bg[2];
+        }
         if (V.out_depth) V.out_depth[pix] = D[p];
         if (V.out_alpha) V.out_alpha[pix] = O[p];
         if (P.pix_T) {
@@ -240,6 +255,26 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
         sC1[p] = T[p] * V.bg[1];
         sC2[p] = T[p] * V.bg[2];
         sD[p] = sO[p] = 0.f;
+        if (V.sky && Gm.px < V.W && py < V.H) {
+            // colour = C + (1 - O) f: no constant background, dL/dO -= gC.f,
+            // dL/df = (1 - O) gC scattered to the four texels
+            size_t ti[4];
+            float tw[4];
+            sky_texels(V, Gm.px, py, ti, tw);
+            const float gc[3] = {gC0[p], gC1[p], gC2[p]};
+            const float wo = T[p];  // 1 - O = T_final
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float f = tw[0] * V.sky[ti[0] + c] + tw[1] * V.sky[ti[1] + c] + tw[2] * V.sky[ti[2] + c] +
+                                tw[3] * V.sky[ti[3] + c];
+                gO[p] -= gc[c] * f;
+                if (V.g_sky && gc[c] != 0.f)
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (tw[q] != 0.f) atomicAdd(V.g_sky + ti[q] + c, tw[q] * wo * gc[c]);
+            }
+            sC0[p] = sC1[p] = sC2[p] = 0.f;
+        }
         maxlast = max(maxlast, last[p]);
     }
     if (tid == 0) s_maxlast = 0;

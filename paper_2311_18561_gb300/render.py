@@ -55,6 +55,13 @@ def abi_scene(scene_t) -> abi.Scene:
     s.sh_degree = sh_degree(scene_t)
     for k in PARAM_NAMES:
         setattr(s, k, scene_t[k].data_ptr() if n > 0 else None)
+    sky = scene_t.get("sky")
+    if sky is not None:
+        if (sky.dim() != 4 or sky.shape[0] != 6 or sky.shape[1] != sky.shape[2] or sky.shape[3] != 3
+                or sky.dtype != torch.float32 or not sky.is_contiguous() or not sky.is_cuda):
+            raise ValueError("scene['sky'] must be a contiguous float32 CUDA tensor [6, R, R, 3]")
+        s.sky = sky.data_ptr()
+        s.sky_res = int(sky.shape[1])
     return s
 
 
@@ -125,8 +132,10 @@ class Renderer:
         ca = abi.cameras(cams)
         if grads is None:
             grads = {k: torch.empty_like(scene_t[k]) for k in PARAM_NAMES}
+            if scene_t.get("sky") is not None:
+                grads["sky"] = torch.empty_like(scene_t["sky"])
         g = abi.SceneGrad()
-        for k in PARAM_NAMES:
+        for k in PARAM_NAMES + ("sky",):
             setattr(g, k, grads[k].data_ptr() if (grads.get(k) is not None and grads[k].numel()) else None)
         dl = (abi.ImageGrad * len(cams))()
         for k, d in enumerate(grads_out):
@@ -205,33 +214,40 @@ def render(scene_t, cams, renderer=None, frame=None):
 
 class PVGRender(torch.autograd.Function):
     """images = Render({H_i(t)}; E, I) (Sec. 3.2, Eq. 8) for one camera,
-    differentiable w.r.t. all nine parameter arrays."""
+    differentiable w.r.t. all nine parameter arrays and the optional sky
+    cube map (Sec. 3.4)."""
 
     @staticmethod
-    def forward(ctx, cam, renderer, mu, vel, tau, beta, period, scale, quat, opacity, sh):
+    def forward(ctx, cam, renderer, mu, vel, tau, beta, period, scale, quat, opacity, sh, sky=None):
         scene_t = dict(mu=mu.contiguous(), vel=vel.contiguous(), tau=tau.contiguous(), beta=beta.contiguous(),
                        period=period.contiguous(), scale=scale.contiguous(), quat=quat.contiguous(),
                        opacity=opacity.contiguous(), sh=sh.contiguous())
+        if sky is not None:
+            scene_t["sky"] = sky.contiguous()
         frame = Frame()
         out = renderer.forward(scene_t, [cam], frame=frame)[0]
         ctx.cam, ctx.renderer, ctx.frame = cam, renderer, frame
-        ctx.save_for_backward(*[scene_t[k] for k in PARAM_NAMES])
+        ctx.has_sky = sky is not None
+        ctx.save_for_backward(*[scene_t[k] for k in PARAM_NAMES], *([scene_t["sky"]] if sky is not None else []))
         return out["rgb"], out["depth"], out["alpha"]
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_alpha):
         saved = ctx.saved_tensors
         scene_t = dict(zip(PARAM_NAMES, saved))
+        if ctx.has_sky:
+            scene_t["sky"] = saved[len(PARAM_NAMES)]
         grads = ctx.renderer.backward(scene_t, [ctx.cam], ctx.frame,
                                       [dict(rgb=g_rgb, depth=g_depth, alpha=g_alpha)])
         ctx.frame.close()
-        return (None, None) + tuple(grads[k] for k in PARAM_NAMES)
+        return (None, None) + tuple(grads[k] for k in PARAM_NAMES) + (grads.get("sky"),)
 
 
 def render_differentiable(params, cam, renderer=None):
-    """params: dict of tensors (may require grad).  Returns rgb, depth, alpha."""
+    """params: dict of tensors (may require grad; an optional "sky" cube map
+    [6, R, R, 3]).  Returns rgb, depth, alpha."""
     r = renderer or default_renderer()
-    return PVGRender.apply(cam, r, *[params[k] for k in PARAM_NAMES])
+    return PVGRender.apply(cam, r, *[params[k] for k in PARAM_NAMES], params.get("sky"))
 
 
 def l1_loss(pred, target, dl=None, loss=None, scale=None, stream=None):

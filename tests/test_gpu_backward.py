@@ -128,3 +128,26 @@ def test_backward_of_empty_scene_is_empty():
     r.forward(st, [cam], frame=fr)
     grads = r.backward(st, [cam], fr, [dict(rgb=torch.ones(3, 24, 32, device="cuda"))])
     assert all(g.numel() == 0 for g in grads.values())
+
+
+def test_backward_with_sky_cube_map():
+    rng = np.random.default_rng(16)
+    scene = synth.make_fd_scene(seed=8, n=400, sh_degree=1)
+    cam = synth.fd_camera(64, 48, t=0.5)
+    sky = rng.uniform(0, 1, size=(6, 8, 8, 3)).astype(np.float32)
+    H, W = cam["height"], cam["width"]
+    w_rgb, w_d, w_a = _weights(H, W, 17)
+    st = R.scene_to_device(scene)
+    st["sky"] = torch.tensor(sky, device="cuda")
+    r = R.Renderer()
+    fr = R.Frame()
+    r.forward(st, [cam], frame=fr)
+    dl = dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"),
+              depth=torch.tensor(w_d, dtype=torch.float32, device="cuda"),
+              alpha=torch.tensor(w_a, dtype=torch.float32, device="cuda"))
+    grads = r.backward(st, [cam], fr, [dl])
+    torch.cuda.synchronize()
+    ref = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), w_d, w_a, sky=sky)
+    _compare_grads(grads, ref)
+    g = grads["sky"].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - ref["sky"]) <= 1e-3 * np.linalg.norm(ref["sky"])

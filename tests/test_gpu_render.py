@@ -239,3 +239,33 @@ def test_flow_translated_state_matches_oracle(renderer, dt):
     plain["dt"] = 0.0
     ref_plain = gpu_render(renderer, R.scene_to_device(scene), [plain])[0]
     assert not torch.equal(out["rgb"], ref_plain["rgb"])
+
+
+@pytest.mark.parametrize("jitter", [False, True])
+def test_sky_cube_map_matches_oracle(renderer, jitter):
+    """Sky refinement (Sec. 3.4): C + (1 - O) f_sky(d)."""
+    rng = np.random.default_rng(14)
+    scene = synth.make_fd_scene(seed=14, n=600, sh_degree=2)
+    cam = synth.fd_camera(72, 56, t=0.5)
+    sky = rng.uniform(0, 1, size=(6, 16, 16, 3)).astype(np.float32)
+    jit = rng.uniform(-0.5, 0.5, size=(2, 56, 72)).astype(np.float32) if jitter else None
+    st = R.scene_to_device(scene)
+    st["sky"] = torch.tensor(sky, device="cuda")
+    gcam = dict(cam)
+    if jitter:
+        gcam["sky_jitter"] = torch.tensor(jit, device="cuda")
+    out = gpu_render(renderer, st, [gcam])[0]
+    ref = oracle.render(scene, cam, sky=sky, sky_jitter=jit)
+    compare_to_oracle(to_numpy_images(out), ref)
+
+
+def test_sky_behind_an_empty_scene_is_the_sky(renderer):
+    rng = np.random.default_rng(15)
+    empty = {k: v[:0] for k, v in synth.make_plain_scene(seed=0, n=4).items()}
+    sky = rng.uniform(0, 1, size=(6, 8, 8, 3)).astype(np.float32)
+    cam = synth.street_camera(0.3, 64, 40)
+    st = R.scene_to_device(empty)
+    st["sky"] = torch.tensor(sky, device="cuda")
+    out = gpu_render(renderer, st, [cam])[0]
+    ref = oracle.render(empty, cam, sky=sky)
+    np.testing.assert_allclose(to_numpy_images(out)["rgb"], ref["rgb"], atol=1e-5)
