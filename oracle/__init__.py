@@ -5,11 +5,12 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 (``paper_2311_18561_gb300``) and never imports it.
 
 ``pvg_oracle.c`` holds the arithmetic (time evaluation, projection, SH
-colour, brute-force and culled compositing, exact reverse mode); this module
+colour, brute-force and culled compositing, the extra v_bar / rho /
+semantic channels, exact reverse mode); this module
 only marshals numpy arrays through ctypes.  ``binning.py`` holds the integer
 side (tile keys, stable sort, tile ranges) written with numpy.
 """
 from .oracle import (  # noqa: F401
-    DEFAULT_OPTS, build, load, num_threads, preprocess, render, render_bwd,
-    sh_basis, time_eval, cam_array,
+    DEFAULT_OPTS, FEAT_RHO, FEAT_SEM, FEAT_VBAR, build, cam_array, feat_count, load,
+    num_threads, preprocess, render, render_bwd, sh_basis, time_eval,
 )

@@ -44,9 +44,11 @@ def load():
         lib.pvgo_sh_basis.argtypes = [C.c_int, C.c_int64, P, P, P]
         lib.pvgo_preprocess.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [P] * 9
         sky = [P, C.c_int, P]
-        lib.pvgo_render.argtypes = [C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + sky + [P] * 6
+        feat = [C.c_int, C.c_int, P]
+        lib.pvgo_render.argtypes = ([C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + sky + feat
+                                    + [P] * 7)
         lib.pvgo_render_bwd.argtypes = ([C.c_int64, C.c_int] + [P] * 11 + [C.c_int, C.c_int64, P] + sky
-                                        + [P] * 3 + [P] * 11)
+                                        + feat + [P] + [P] * 3 + [P] * 12)
         lib.pvgo_num_threads.argtypes = []
         for f in (lib.pvgo_time_eval, lib.pvgo_sh_basis, lib.pvgo_preprocess, lib.pvgo_render,
                   lib.pvgo_render_bwd, lib.pvgo_num_threads):
@@ -141,12 +143,36 @@ def _sky_args(sky, jitter):
     return sk, int(sk.shape[1]), jt, (_p(sk), int(sk.shape[1]), _p(jt))
 
 
-def render(scene, cam, opts=None, mode="brute", pixels=None, sky=None, sky_jitter=None):
-    """Steps 5/6.  mode 'brute' or 'culled'.  pixels: None for the full
-    image (outputs shaped [H, W, ...]) or an int array [P, 2] of (px, py)
-    (outputs shaped [P, ...]).  sky: optional cube map (see _sky_args).
-    Returns dict rgb, depth, alpha, T, nblend, flag."""
+# extra channels of step 8 (bit flags): v_bar (3), rho clamped to [0, 2] (1),
+# semantic vector (n_sem)
+FEAT_VBAR, FEAT_RHO, FEAT_SEM = 1, 2, 4
+
+
+def feat_count(mask, n_sem=0):
+    return (3 if mask & FEAT_VBAR else 0) + (1 if mask & FEAT_RHO else 0) + (n_sem if mask & FEAT_SEM else 0)
+
+
+def _feat_args(features, sem):
+    """features: channel mask; sem: [N, S] semantic vectors (FEAT_SEM)."""
+    mask = int(features or 0)
+    if mask & FEAT_SEM:
+        if sem is None:
+            raise ValueError("FEAT_SEM needs the semantic vectors")
+        sm = _d(sem)
+        return mask, int(sm.shape[1]), sm
+    return mask, 0, None
+
+
+def render(scene, cam, opts=None, mode="brute", pixels=None, sky=None, sky_jitter=None, features=0, sem=None):
+    """Steps 5/6 (and 8).  mode 'brute' or 'culled'.  pixels: None for the
+    full image (outputs shaped [H, W, ...]) or an int array [P, 2] of
+    (px, py) (outputs shaped [P, ...]).  sky: optional cube map (see
+    _sky_args).  features: mask of FEAT_* channels (sem: [N, S] for
+    FEAT_SEM), returned as 'feat' [..., F].
+    Returns dict rgb, depth, alpha, T, nblend, flag (, feat)."""
     n, deg, arrs = _scene_args(scene)
+    fmask, nsem, sm = _feat_args(features, sem)
+    F = feat_count(fmask, nsem)
     sk, res, jt, skp = _sky_args(sky, sky_jitter)
     if skp is None:
         skp = (None, 0, None)
@@ -159,10 +185,14 @@ def render(scene, cam, opts=None, mode="brute", pixels=None, sky=None, sky_jitte
         P = pix.shape[0]
     out = dict(rgb=np.zeros((P, 3)), depth=np.zeros(P), alpha=np.zeros(P), T=np.zeros(P),
                nblend=np.zeros(P, np.int32), flag=np.zeros(P, np.int32))
+    if F:
+        out["feat"] = np.zeros((P, F))
     ca, oa = cam_array(cam), opt_array(opts)
     m = {"brute": 0, "culled": 1}[mode]
     rc = load().pvgo_render(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, P, _p(pix), *skp,
-                            *[_p(out[k]) for k in ("rgb", "depth", "alpha", "T", "nblend", "flag")])
+                            fmask, nsem, _p(sm),
+                            *[_p(out[k]) for k in ("rgb", "depth", "alpha", "T", "nblend", "flag")],
+                            _p(out.get("feat")))
     if rc != 0:
         raise ValueError("oracle render rejected its inputs")
     if pixels is None:
@@ -174,12 +204,18 @@ GRAD_NAMES = ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", 
 
 
 def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=False, mode="brute",
-               pixels=None, sky=None, sky_jitter=None):
+               pixels=None, sky=None, sky_jitter=None, features=0, sem=None, dL_feat=None):
     """Gradients of sum(dL_rgb*rgb) + sum(dL_depth*depth) + sum(dL_alpha*alpha)
-    w.r.t. every parameter, as a dict keyed like the scene.  Full image
-    (dL_rgb [H,W,3], others [H,W]) or, with ``pixels`` [P,2], only those
-    pixels (dL_rgb [P,3], others [P]).  mode 'brute' or 'culled'."""
+    (+ sum(dL_feat*feat) for the channels in ``features``) w.r.t. every
+    parameter, as a dict keyed like the scene (plus 'sem' for FEAT_SEM).
+    Full image (dL_rgb [H,W,3], others [H,W], dL_feat [H,W,F]) or, with
+    ``pixels`` [P,2], only those pixels (dL_rgb [P,3], others [P],
+    dL_feat [P,F]).  mode 'brute' or 'culled'."""
     n, deg, arrs = _scene_args(scene)
+    fmask, nsem, sm = _feat_args(features, sem)
+    F = feat_count(fmask, nsem)
+    gf = _d(dL_feat) if F else None
+    dsem = np.zeros((n, nsem)) if fmask & FEAT_SEM else None
     k = (deg + 1) ** 2
     g = dict(mu=np.zeros((n, 3)), vel=np.zeros((n, 3)), tau=np.zeros(n), beta=np.zeros(n),
              period=np.zeros(n), scale=np.zeros((n, 3)), quat=np.zeros((n, 4)), opacity=np.zeros(n),
@@ -198,10 +234,12 @@ def render_bwd(scene, cam, dL_rgb, dL_depth, dL_alpha, opts=None, return_g2d=Fal
         dsky = np.zeros_like(sk)
         g["sky"] = dsky
     rc = load().pvgo_render_bwd(n, deg, *[_p(a) for a in arrs], _p(ca), _p(oa), m, npix, _p(pix), *skp,
-                                _p(gr), _p(gd), _p(ga),
-                                *[_p(g[name]) for name in GRAD_NAMES], _p(g2d), _p(dsky))
+                                fmask, nsem, _p(sm), _p(gf), _p(gr), _p(gd), _p(ga),
+                                *[_p(g[name]) for name in GRAD_NAMES], _p(g2d), _p(dsky), _p(dsem))
     if rc != 0:
         raise ValueError("oracle backward rejected its inputs")
+    if dsem is not None:
+        g["sem"] = dsem
     if return_g2d:
         return g, g2d
     return g

@@ -36,6 +36,13 @@
  *      o~ G_2D < 1/255, so the skipped evaluations could not have blended.
  *   7. Backward: exact FP64 reverse mode of steps 1-5 (the render function
  *      is differentiable, Sec. 3.1 Eq. 4 and Sec. 3.2 Eq. 8).
+ *   8. Extra channels composited with the same weights T_i alpha_i and no
+ *      background: the average velocity v_bar = v exp(-rho/2) (Eq. 10; its
+ *      rendered map is the velocity map of Sec. 3.4 and Sec. 4), the
+ *      staticness rho = beta / l clamped to [0, 2] (the rho map of the
+ *      dynamic-element analysis) and a per-Gaussian semantic vector
+ *      (semantic rendering, 19 classes in the paper), with their reverse
+ *      mode.
  *
  * Parameters are physical values (s > 0, o in (0,1), beta > 0, l > 0);
  * the quaternion (w,x,y,z) need not be normalised and is normalised here.
@@ -462,18 +469,85 @@ static void sky_value(const sky_t *K, const double *cam, int px, int py, double 
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* step 8: extra composited channels                                   */
+/* ------------------------------------------------------------------ */
+/* Channel order: v_bar (3, world frame) if FEAT_VBAR, rho clamped to
+ * [0, 2] (1) if FEAT_RHO, the n_sem semantic values if FEAT_SEM. */
+enum { FEAT_VBAR = 1, FEAT_RHO = 2, FEAT_SEM = 4 };
+typedef struct { int mask, n_sem, F; const double *sem; } feat_t;
+
+static int feat_count(int mask, int n_sem)
+{
+    return ((mask & FEAT_VBAR) ? 3 : 0) + ((mask & FEAT_RHO) ? 1 : 0) + ((mask & FEAT_SEM) ? n_sem : 0);
+}
+
+static void feat_values(const scene_t *S, int64_t i, const feat_t *Fs, double *f)
+{
+    int c = 0;
+    const double rho = S->beta[i] / S->period[i];
+    if (Fs->mask & FEAT_VBAR) {
+        const double w = exp(-0.5 * rho);
+        for (int k = 0; k < 3; k++) f[c++] = S->vel[3 * i + k] * w;
+    }
+    if (Fs->mask & FEAT_RHO) f[c++] = rho < 2.0 ? rho : 2.0;
+    if (Fs->mask & FEAT_SEM)
+        for (int k = 0; k < Fs->n_sem; k++) f[c++] = Fs->sem[i * Fs->n_sem + k];
+}
+
+/* adjoint of feat_values for Gaussian i given dL/df */
+static void feat_backward(const scene_t *S, int64_t i, const feat_t *Fs, const double *gf, double *dvel,
+                          double *dbeta, double *dperiod, double *dsem)
+{
+    int c = 0;
+    const double l = S->period[i], b = S->beta[i], rho = b / l;
+    if (Fs->mask & FEAT_VBAR) {
+        /* v_bar = v exp(-rho / 2): d/dv = exp(-rho/2), d/drho = -v_bar / 2 */
+        const double w = exp(-0.5 * rho);
+        double gr = 0.0;
+        for (int k = 0; k < 3; k++) {
+            dvel[3 * i + k] += gf[c + k] * w;
+            gr += gf[c + k] * S->vel[3 * i + k] * w * -0.5;
+        }
+        dbeta[i] += gr / l;
+        dperiod[i] += -gr * b / (l * l);
+        c += 3;
+    }
+    if (Fs->mask & FEAT_RHO) {
+        if (rho < 2.0) {
+            dbeta[i] += gf[c] / l;
+            dperiod[i] += -gf[c] * b / (l * l);
+        }
+        c += 1;
+    }
+    if (Fs->mask & FEAT_SEM)
+        for (int k = 0; k < Fs->n_sem; k++) dsem[i * Fs->n_sem + k] += gf[c + k];
+}
+
+/* per-Gaussian feature table [n, F] (rows of culled Gaussians unused) */
+static double *feat_table(const scene_t *S, const gauss_t *G, const feat_t *Fs)
+{
+    if (Fs->F == 0) return NULL;
+    double *FV = (double *)calloc((size_t)(S->n > 0 ? S->n : 1) * (size_t)Fs->F, sizeof(double));
+    for (int64_t i = 0; i < S->n; i++)
+        if (G[i].valid) feat_values(S, i, Fs, &FV[i * Fs->F]);
+    return FV;
+}
+
 /* composite one pixel (px, py) over the depth-ordered list.  out receives
- * r, g, b, depth, opacity and the final transmittance; if `blend` is
- * non-NULL it receives the blended list (indices, alpha, T, G, offsets) */
+ * r, g, b, depth, opacity and the final transmittance; phi (if F > 0) the
+ * F composited channels of the feature table FV; if `blend` is non-NULL
+ * it receives the blended list (indices, alpha, T, G, offsets) */
 typedef struct { int64_t idx; double alpha, T, G, dx, dy; int capped; } blend_t;
 
 static void composite_pixel(const gauss_t *G, const int64_t *order, int64_t m, int culled, int px, int py,
-                            const double *cam, const double *opt, const sky_t *sky, double out[6],
-                            int32_t *nblend, int32_t *flag, blend_t *blend)
+                            const double *cam, const double *opt, const sky_t *sky, const double *FV, int F,
+                            double out[6], double *phi, int32_t *nblend, int32_t *flag, blend_t *blend)
 {
     const double sx = px + 0.5, sy = py + 0.5;
     double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, O = 0.0, zprev = -1.0;
     int nb = 0, fl = 0;
+    for (int c = 0; c < F; c++) phi[c] = 0.0;
     for (int64_t j = 0; j < m; j++) {
         const gauss_t *g = &G[order[j]];
         if (culled && (fabs(sx - g->uv[0]) > g->rx || fabs(sy - g->uv[1]) > g->ry)) continue;
@@ -493,6 +567,7 @@ static void composite_pixel(const gauss_t *G, const int64_t *order, int64_t m, i
         }
         const double w = a * T;
         for (int c = 0; c < 3; c++) C[c] += g->rgb[c] * w;
+        for (int c = 0; c < F; c++) phi[c] += FV[order[j] * F + c] * w;
         D += g->z * w;
         O += w;
         T = Tn;
@@ -517,15 +592,21 @@ static void composite_pixel(const gauss_t *G, const int64_t *order, int64_t m, i
  * order (P = W H); otherwise P (px, py) int32 pairs.  Outputs per pixel:
  * rgb[P,3], depth[P] (sum T alpha z), alpha[P] (sum T alpha), T[P] (final
  * transmittance), nblend[P], flag[P] (1 if a gate was within 1e-5 relative
- * of its threshold or two blended depths were within 1e-6 relative). */
+ * of its threshold or two blended depths were within 1e-6 relative).
+ * feat_mask / n_sem / sem select the extra channels of step 8 (sem: [n,
+ * n_sem]); feat receives them [P, F] (NULL if feat_mask = 0). */
 int pvgo_render(int64_t n, int degree, const double *mu, const double *vel, const double *tau,
                 const double *beta, const double *period, const double *scale, const double *quat,
                 const double *opac, const double *sh, const double *cam, const double *opt, int mode,
                 int64_t npix, const int32_t *pix, const double *sky_tex, int sky_res, const double *sky_jitter,
-                double *rgb, double *depth, double *alpha, double *Tout, int32_t *nblend, int32_t *flag)
+                int feat_mask, int n_sem, const double *sem, double *rgb, double *depth, double *alpha,
+                double *Tout, int32_t *nblend, int32_t *flag, double *feat)
 {
     const sky_t sky = {sky_tex, sky_res, sky_jitter};
     if (degree < 0 || degree > 3 || n < 0) return -1;
+    if ((feat_mask & FEAT_SEM) && (n_sem <= 0 || !sem)) return -1;
+    const feat_t Fs = {feat_mask, n_sem, feat_count(feat_mask, n_sem), sem};
+    if (Fs.F > 0 && !feat) return -1;
     const int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
     if (W <= 0 || H <= 0) return -1;
     scene_t S = make_scene(n, degree, mu, vel, tau, beta, period, scale, quat, opac, sh);
@@ -533,6 +614,7 @@ int pvgo_render(int64_t n, int degree, const double *mu, const double *vel, cons
     preprocess_all(&S, cam, opt, G);
     int64_t *order = NULL;
     const int64_t m = depth_order(G, n, &order);
+    double *FV = feat_table(&S, G, &Fs);
     const int64_t P = pix ? npix : (int64_t)W * H;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < P; k++) {
@@ -540,7 +622,8 @@ int pvgo_render(int64_t n, int degree, const double *mu, const double *vel, cons
         const int py = pix ? pix[2 * k + 1] : (int)(k / W);
         double out[6];
         int32_t nb, fl;
-        composite_pixel(G, order, m, mode == 1, px, py, cam, opt, &sky, out, &nb, &fl, NULL);
+        composite_pixel(G, order, m, mode == 1, px, py, cam, opt, &sky, FV, Fs.F, out,
+                        feat ? &feat[k * Fs.F] : NULL, &nb, &fl, NULL);
         if (rgb) { rgb[3 * k] = out[0]; rgb[3 * k + 1] = out[1]; rgb[3 * k + 2] = out[2]; }
         if (depth) depth[k] = out[3];
         if (alpha) alpha[k] = out[4];
@@ -548,6 +631,7 @@ int pvgo_render(int64_t n, int degree, const double *mu, const double *vel, cons
         if (nblend) nblend[k] = nb;
         if (flag) flag[k] = fl;
     }
+    free(FV);
     free(order);
     free(G);
     return 0;
@@ -569,19 +653,20 @@ int pvgo_num_threads(void)
 /* per-Gaussian image-space gradient accumulator */
 enum { G2_U = 0, G2_V, G2_A, G2_B, G2_C, G2_O, G2_R, G2_G, G2_BL, G2_Z, G2_LEN };
 
-/* growable list of (Gaussian index, 10 image-space gradient terms) */
-typedef struct { int64_t len, cap; int64_t *idx; double *val; } contrib_list_t;
+/* growable list of (Gaussian index, `stride` gradient terms: the 10
+ * image-space terms, then dL/d(feature) of step 8) */
+typedef struct { int64_t len, cap; int stride; int64_t *idx; double *val; } contrib_list_t;
 
 static double *contrib_push(contrib_list_t *L, int64_t idx)
 {
     if (L->len == L->cap) {
         L->cap = L->cap ? 2 * L->cap : 1024;
         L->idx = (int64_t *)realloc(L->idx, sizeof(int64_t) * (size_t)L->cap);
-        L->val = (double *)realloc(L->val, sizeof(double) * G2_LEN * (size_t)L->cap);
+        L->val = (double *)realloc(L->val, sizeof(double) * (size_t)L->stride * (size_t)L->cap);
     }
     L->idx[L->len] = idx;
-    double *A = &L->val[L->len * G2_LEN];
-    for (int c = 0; c < G2_LEN; c++) A[c] = 0.0;
+    double *A = &L->val[L->len * L->stride];
+    for (int c = 0; c < L->stride; c++) A[c] = 0.0;
     L->len++;
     return A;
 }
@@ -739,7 +824,9 @@ static void backward_one(const scene_t *S, int64_t i, const gauss_t *g, const do
 }
 
 /* exported: gradients of L = sum(dL_rgb . rgb) + sum(dL_depth depth) +
- * sum(dL_alpha alpha) w.r.t. every parameter (and the sky texels, if a sky
+ * sum(dL_alpha alpha) (+ sum(dL_feat . feat) for the step-8 channels
+ * selected by feat_mask; dsem [n, n_sem] receives the semantic gradient)
+ * w.r.t. every parameter (and the sky texels, if a sky
  * map is given: dsky[6 res res 3]), over the full image
  * (pix = NULL, row-major pixels) or over the P listed (px, py) pixels
  * (dL arrays then indexed by list position); mode 0 brute force, 1 culled
@@ -750,14 +837,20 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
                     const double *beta, const double *period, const double *scale, const double *quat,
                     const double *opac, const double *sh, const double *cam, const double *opt, int mode,
                     int64_t npix, const int32_t *pix, const double *sky_tex, int sky_res,
-                    const double *sky_jitter, const double *dL_rgb, const double *dL_depth,
+                    const double *sky_jitter, int feat_mask, int n_sem, const double *sem,
+                    const double *dL_feat, const double *dL_rgb, const double *dL_depth,
                     const double *dL_alpha, double *dmu, double *dvel, double *dtau, double *dbeta,
                     double *dperiod, double *dscale, double *dquat, double *dopac, double *dsh, double *g2d,
-                    double *dsky)
+                    double *dsky, double *dsem)
 {
     const sky_t sky = {sky_tex, sky_res, sky_jitter};
     if (sky_tex && dsky) memset(dsky, 0, sizeof(double) * 18 * (size_t)sky_res * (size_t)sky_res);
     if (degree < 0 || degree > 3 || n < 0) return -1;
+    if ((feat_mask & FEAT_SEM) && (n_sem <= 0 || !sem || !dsem)) return -1;
+    const feat_t Fs = {feat_mask, n_sem, feat_count(feat_mask, n_sem), sem};
+    if (Fs.F > 0 && !dL_feat) return -1;
+    const int stride = G2_LEN + Fs.F;
+    if (dsem && (feat_mask & FEAT_SEM)) memset(dsem, 0, sizeof(double) * (size_t)n * (size_t)n_sem);
     const int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
     const int K = (degree + 1) * (degree + 1);
     scene_t S = make_scene(n, degree, mu, vel, tau, beta, period, scale, quat, opac, sh);
@@ -765,7 +858,8 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
     preprocess_all(&S, cam, opt, G);
     int64_t *order = NULL;
     const int64_t m = depth_order(G, n, &order);
-    double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * G2_LEN, sizeof(double));
+    double *FV = feat_table(&S, G, &Fs);
+    double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * (size_t)stride, sizeof(double));
     const int64_t P = pix ? npix : (int64_t)W * H;
     /* pixels are split into fixed contiguous chunks, one per thread; each
      * thread lists its per-(pixel, Gaussian) contributions and the lists are
@@ -783,13 +877,18 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
 #endif
         const int64_t k0 = P * tid / nthreads, k1 = P * (tid + 1) / nthreads;
         blend_t *bl = (blend_t *)malloc(sizeof(blend_t) * (size_t)(m > 0 ? m : 1));
+        double *phi = (double *)malloc(sizeof(double) * (size_t)(2 * Fs.F + 1));
+        double *sF = phi + Fs.F; /* feature suffix sums */
         contrib_list_t *L = &lists[tid];
+        L->stride = stride;
         for (int64_t k = k0; k < k1; k++) {
             const int px = pix ? pix[2 * k] : (int)(k % W);
             const int py = pix ? pix[2 * k + 1] : (int)(k / W);
             double out[6];
             int32_t nb;
-            composite_pixel(G, order, m, mode == 1, px, py, cam, opt, &sky, out, &nb, NULL, bl);
+            composite_pixel(G, order, m, mode == 1, px, py, cam, opt, &sky, FV, Fs.F, out, phi, &nb, NULL, bl);
+            const double *gF = Fs.F ? &dL_feat[k * Fs.F] : NULL;
+            for (int c = 0; c < Fs.F; c++) sF[c] = 0.0; /* no feature background */
             const double Tfin = out[5];
             const double gC[3] = {dL_rgb[3 * k], dL_rgb[3 * k + 1], dL_rgb[3 * k + 2]};
             const double gD = dL_depth[k];
@@ -825,6 +924,11 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
                 for (int c = 0; c < 3; c++) ga += gC[c] * (g->rgb[c] * e->T - sC[c] / (1.0 - e->alpha));
                 ga += gD * (g->z * e->T - sD / (1.0 - e->alpha));
                 ga += gO * (e->T - sO / (1.0 - e->alpha));
+                const double *f = Fs.F ? &FV[e->idx * Fs.F] : NULL;
+                for (int c = 0; c < Fs.F; c++) {
+                    ga += gF[c] * (f[c] * e->T - sF[c] / (1.0 - e->alpha));
+                    A[G2_LEN + c] = gF[c] * w;
+                }
                 for (int c = 0; c < 3; c++) A[G2_R + c] = gC[c] * w;
                 A[G2_Z] = gD * w;
                 if (!e->capped) {
@@ -838,16 +942,18 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
                     A[G2_V] = gpow * (g->conic[1] * dx + g->conic[2] * dy);
                 }
                 for (int c = 0; c < 3; c++) sC[c] += g->rgb[c] * w;
+                for (int c = 0; c < Fs.F; c++) sF[c] += f[c] * w;
                 sD += g->z * w;
                 sO += w;
             }
         }
+        free(phi);
         free(bl);
     }
     for (int t = 0; t < nthreads; t++) {
         for (int64_t q = 0; q < lists[t].len; q++) {
-            double *A = &acc[lists[t].idx[q] * G2_LEN];
-            for (int c = 0; c < G2_LEN; c++) A[c] += lists[t].val[q * G2_LEN + c];
+            double *A = &acc[lists[t].idx[q] * stride];
+            for (int c = 0; c < stride; c++) A[c] += lists[t].val[q * stride + c];
         }
         free(lists[t].idx);
         free(lists[t].val);
@@ -865,11 +971,13 @@ int pvgo_render_bwd(int64_t n, int degree, const double *mu, const double *vel, 
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         if (g2d)
-            for (int c = 0; c < G2_LEN; c++) g2d[i * G2_LEN + c] = acc[i * G2_LEN + c];
+            for (int c = 0; c < G2_LEN; c++) g2d[i * G2_LEN + c] = acc[i * stride + c];
         if (!G[i].valid) continue;
-        backward_one(&S, i, &G[i], cam, opt, &acc[i * G2_LEN], dmu, dvel, dtau, dbeta, dperiod, dscale, dquat,
+        backward_one(&S, i, &G[i], cam, opt, &acc[i * stride], dmu, dvel, dtau, dbeta, dperiod, dscale, dquat,
                      dopac, dsh);
+        if (Fs.F) feat_backward(&S, i, &Fs, &acc[i * stride + G2_LEN], dvel, dbeta, dperiod, dsem);
     }
+    free(FV);
     free(acc);
     free(order);
     free(G);

@@ -286,3 +286,17 @@ def random_image(height, width, seed=1):
     """Target image ~ U[0,1]^3, planar [3, H, W]."""
     rng = np.random.default_rng(seed)
     return rng.uniform(0.0, 1.0, size=(3, height, width)).astype(F32)
+
+
+def make_semantics(n, n_classes=19, seed=3, one_hot=False):
+    """Per-Gaussian class-probability vectors [n, n_classes] (19 classes in
+    the paper's semantic rendering): a softmax of N(0, 1.5^2) logits, or
+    one-hot rows of a uniformly drawn class."""
+    rng = np.random.default_rng(seed)
+    if one_hot:
+        out = np.zeros((n, n_classes))
+        out[np.arange(n), rng.integers(0, n_classes, size=n)] = 1.0
+        return out.astype(F32)
+    z = rng.normal(0.0, 1.5, size=(n, n_classes))
+    z = np.exp(z - z.max(axis=1, keepdims=True))
+    return (z / z.sum(axis=1, keepdims=True)).astype(F32)
