@@ -18,6 +18,9 @@
  *     front-to-back alpha blending C = sum_i T_i alpha_i c_i (Sec. 3.1,
  *     Eq. 3), plus the depth and opacity channels of "flexible rendering"
  *     (Sec. 3.1) and O = sum T_i alpha_i (Sec. 3.4, sky refinement);
+ *   - optional background from a sky cube map, temporal-smoothing shift
+ *     (Sec. 3.4) and extra channels: velocity, staticness and semantic maps
+ *     (Sec. 4);
  *   - the render function is differentiable (Sec. 3.1, Eq. 4): the backward
  *     entry point returns gradients for mu, v, tau, beta, l, s, q, o and
  *     the SH colour coefficients.
@@ -94,14 +97,36 @@ int pvg_version(void);
  *           (1 - O) f_sky(d) instead of T_final bg, d the pixel's world ray
  *           direction, faces +X -X +Y -Y +Z -Z with the OpenGL cube-map
  *           face coordinates, bilinear inside a face, edges clamped;
- *           R = sky_res (>= 1). */
+ *           R = sky_res (>= 1).
+ *   sem     [N,n_sem] optional per-point semantic vector (semantic
+ *           rendering, Sec. 4: 19 class probabilities in the paper),
+ *           1 <= n_sem <= PVG_MAX_SEM; needed only for PVG_FEAT_SEM. */
 typedef struct {
     int64_t n;
     int32_t sh_degree;
     int32_t sky_res;
     const float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opacity, *sh;
     const float *sky;
+    const float *sem;
+    int32_t n_sem;
+    int32_t reserved0;
 } pvg_scene_t;
+
+/* Extra composited channels (bit mask, pvg_image_t.feat_mask).  Each is a
+ * per-point value x_i composited with the colour's weights and no
+ * background, sum_i T_i alpha_i x_i:
+ *   PVG_FEAT_VBAR  3 channels, the average velocity v_bar = v exp(-rho/2),
+ *                  rho = beta / l (Eq. 10), world frame -- the velocity
+ *                  map of Sec. 3.4 / Sec. 4;
+ *   PVG_FEAT_RHO   1 channel, the staticness rho = beta / l clamped to
+ *                  [0, 2] (the rho map of the dynamic-element analysis,
+ *                  Sec. 4; small = dynamic, large = static);
+ *   PVG_FEAT_SEM   n_sem channels, the scene's semantic vectors.
+ * The feature image holds the selected channels in this order. */
+#define PVG_FEAT_VBAR 1
+#define PVG_FEAT_RHO 2
+#define PVG_FEAT_SEM 4
+#define PVG_MAX_SEM 32
 
 /* A pinhole camera at time t (host memory). */
 typedef struct {
@@ -124,23 +149,38 @@ typedef struct {
  *   rgb   [3,H,W] planar, required
  *   depth [H,W]  sum_i T_i alpha_i z_i (not normalised; divide by alpha
  *                for the normalised depth of Sec. 3.1), may be NULL
- *   alpha [H,W]  O = sum_i T_i alpha_i, may be NULL */
+ *   alpha [H,W]  O = sum_i T_i alpha_i, may be NULL
+ *   feat  [F,H,W] planar extra channels selected by feat_mask (PVG_FEAT_*;
+ *                F = 3 [VBAR] + 1 [RHO] + n_sem [SEM]); required when
+ *                feat_mask != 0.  Every view of one call must use the same
+ *                feat_mask; the scene(s) must carry sem for PVG_FEAT_SEM
+ *                (and, for several scenes, the same n_sem). */
 typedef struct {
     float *rgb, *depth, *alpha;
+    float *feat;
+    int32_t feat_mask;
+    int32_t reserved0;
 } pvg_image_t;
 
-/* dL/d(output) of one view, same layouts as pvg_image_t; NULL = zero. */
+/* dL/d(output) of one view, same layouts as pvg_image_t; NULL = zero.
+ * feat uses the channels of the forward pass that filled the frame. */
 typedef struct {
     const float *rgb, *depth, *alpha;
+    const float *feat;
 } pvg_image_grad_t;
 
 /* Parameter gradients, same layouts as pvg_scene_t (device, caller-owned).
  * pvg_render_bwd zeroes them and then writes dL/dparam summed over all
  * views.  A NULL array is neither zeroed nor written.  sky: dL/d(sky
- * texels), used when the scene has a sky map. */
+ * texels), used when the scene has a sky map.  sem: dL/d(semantic
+ * vectors) [N,n_sem], used when the frame's forward rendered
+ * PVG_FEAT_SEM.  The feature channels also reach vel, beta and period
+ * (through v_bar and rho; rho's clamp passes no gradient at rho >= 2) and
+ * the geometry (through the blending weights). */
 typedef struct {
     float *mu, *vel, *tau, *beta, *period, *scale, *quat, *opacity, *sh;
     float *sky;
+    float *sem;
 } pvg_scene_grad_t;
 
 /* ------------------------------------------------------------------ */

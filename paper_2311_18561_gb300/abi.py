@@ -29,7 +29,13 @@ class PVGError(RuntimeError):
 
 class Scene(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("sky_res", C.c_int32)] + [
-        (k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh", "sky")]
+        (k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh", "sky",
+                                  "sem")] + [("n_sem", C.c_int32), ("reserved0", C.c_int32)]
+
+
+# extra composited channels (pvg_image_t.feat_mask)
+FEAT_VBAR, FEAT_RHO, FEAT_SEM = 1, 2, 4
+MAX_SEM = 32
 
 
 class Camera(C.Structure):
@@ -40,16 +46,17 @@ class Camera(C.Structure):
 
 
 class Image(C.Structure):
-    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p)]
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p), ("feat", C.c_void_p),
+                ("feat_mask", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class ImageGrad(C.Structure):
-    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p)]
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p), ("feat", C.c_void_p)]
 
 
 class SceneGrad(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("mu", "vel", "tau", "beta", "period", "scale", "quat", "opacity", "sh",
-                                          "sky")]
+                                          "sky", "sem")]
 
 
 class Config(C.Structure):

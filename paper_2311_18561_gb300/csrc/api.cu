@@ -154,7 +154,9 @@ struct pvg_frame {
     DevBuf pix_T, pix_last;     // [pixels]
     DevBuf pix_neval;           // [pixels]
     DevBuf g2d;                 // [NV * 10]
+    DevBuf gfeat;               // [NV * F] dL/d(channel value)
     std::vector<ViewDesc> views;
+    int feat_mask = 0, n_feat = 0, n_sem = 0;  // extra channels of the forward
     bool one_scene = true;      // every view renders the same scene
     uint32_t n_items = 0, total_tiles = 0, total_pix = 0, pair_capacity = 0;
     int tile_w = 0, tile_h = 0, px = 1;
@@ -246,7 +248,7 @@ extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
     for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->rect, &f->vis_cnt, &f->pair_vals,
-                      &f->ranges, &f->tile_order, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d})
+                      &f->ranges, &f->tile_order, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d, &f->gfeat})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
     free_stage_ptr(f->stage_fwd);
@@ -311,6 +313,7 @@ static bool finite3x4(const float *m) {
 static pvg_status_t validate_scene(const pvg_scene_t *sc) {
     if (!sc || sc->n < 0 || sc->sh_degree < 0 || sc->sh_degree > 3) return PVG_ERR_INVALID;
     if (sc->sky && (sc->sky_res < 1 || sc->sky_res > 16384)) return PVG_ERR_INVALID;
+    if (sc->sem && (sc->n_sem < 1 || sc->n_sem > kMaxSem)) return PVG_ERR_INVALID;
     if (sc->n > 0 && (!sc->mu || !sc->vel || !sc->tau || !sc->beta || !sc->period || !sc->scale || !sc->quat ||
                       !sc->opacity || !sc->sh))
         return PVG_ERR_INVALID;
@@ -364,6 +367,8 @@ static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *scenes, int
         d.sky = sc->sky;
         d.sky_res = sc->sky_res;
         d.sky_jitter = c.sky_jitter;
+        d.sem = sc->sem;
+        d.n_sem = sc->n_sem;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
         pix += (uint64_t)c.width * c.height;
         items += (uint64_t)sc->n;
@@ -465,10 +470,22 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     uint32_t NV, tiles, pix;
     PVG_TRY(build_views(x, scenes, scene_stride, cams, n_views, views, &NV, &tiles, &pix));
     const pvg_scene_t *scene = &scenes[0];
+    // extra channels: one mask for the call, channel values of every scene
+    const int fmask = out[0].feat_mask;
+    if (fmask & ~(kFeatVbar | kFeatRho | kFeatSem)) return PVG_ERR_INVALID;
+    const int nsem = (fmask & kFeatSem) ? scene->n_sem : 0;
+    if ((fmask & kFeatSem) && (nsem < 1 || nsem > kMaxSem)) return PVG_ERR_INVALID;
+    for (int v = 0; v < n_views; v++) {
+        if (out[v].feat_mask != fmask || (fmask && !out[v].feat)) return PVG_ERR_INVALID;
+        if ((fmask & kFeatSem) && ((views[v].n > 0 && !views[v].sem) || views[v].n_sem != nsem))
+            return PVG_ERR_INVALID;
+    }
+    const int n_feat = fmask ? feat_count(fmask, nsem) : 0;
     for (int v = 0; v < n_views; v++) {
         views[v].out_rgb = out[v].rgb;
         views[v].out_depth = out[v].depth;
         views[v].out_alpha = out[v].alpha;
+        views[v].out_feat = fmask ? out[v].feat : nullptr;
     }
     // workspace
     PVG_TRY(ensure_c(x->item_cnt, sizeof(uint32_t) * NV, capturing));
@@ -511,6 +528,9 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     f->dilation = x->cfg.dilation;
     f->stream = s;
     f->valid = false;
+    f->feat_mask = fmask;
+    f->n_feat = n_feat;
+    f->n_sem = nsem;
 
     PVG_TRY(stage_views(*f->stage_fwd, views, s, capturing));
     PVG_CUDA(cudaMemsetAsync(f->counters.p, 0, 4 * sizeof(uint32_t), s));
@@ -541,6 +561,8 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.pix_neval = ptr<uint32_t>(f->pix_neval);
     p.vis_off = ptr<uint32_t>(x->vis_off);
+    p.feat_mask = fmask;
+    p.n_feat = n_feat;
     StageTimer &tm = x->timer;
     const bool timer_on = tm.on;
     if (capturing) tm.on = false;
@@ -615,6 +637,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     if (!frame) p.pix_T = nullptr;  // inference only: no state for a backward pass
     tm.begin(PVG_STAGE_COMPOSITE, s);
     launch_composite(p, s);
+    if (n_feat) launch_composite_feat(p, s);
     tm.end(PVG_STAGE_COMPOSITE, s);
     tm.on = timer_on;
     PVG_CUDA(cudaGetLastError());
@@ -636,10 +659,11 @@ extern "C" pvg_status_t pvg_render_fwd_multi(pvg_ctx_t *x, const pvg_scene_t *sc
 
 // ------------------------------------------------------------------ backward
 
-__global__ static void k_zero_g2d(float *g2d, const uint32_t *d_m) {
-    const size_t n = 10 * (size_t)*d_m;
+// zeroes rows [0, *d_m) of a [*, per] array (the visible items' rows)
+__global__ static void k_zero_rows(float *a, const uint32_t *d_m, int per) {
+    const size_t n = (size_t)per * *d_m;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-        g2d[k] = 0.f;
+        a[k] = 0.f;
 }
 
 extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cams,
@@ -654,8 +678,15 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     cudaStream_t s = (cudaStream_t)stream_;
     const bool capturing = is_capturing(s);
     std::vector<ViewDesc> views = f->views;
+    bool feat_bwd = false;
+    if ((f->feat_mask & kFeatSem) && ((scene->n > 0 && !scene->sem) || scene->n_sem != f->n_sem))
+        return PVG_ERR_INVALID;
     for (int v = 0; v < n_views; v++) {
         if (!cams || cams[v].width != views[v].W || cams[v].height != views[v].H) return PVG_ERR_INVALID;
+        if (dL[v].feat) {
+            if (!f->feat_mask) return PVG_ERR_INVALID;  // the forward rendered no extra channel
+            feat_bwd = true;
+        }
         ViewDesc &d = views[v];
         d.mu = scene->mu; d.vel = scene->vel; d.tau = scene->tau; d.beta = scene->beta; d.period = scene->period;
         d.scale = scene->scale; d.quat = scene->quat; d.opac = scene->opacity; d.sh = scene->sh;
@@ -665,6 +696,10 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
         d.g_mu = grads->mu; d.g_vel = grads->vel; d.g_tau = grads->tau; d.g_beta = grads->beta;
         d.g_period = grads->period; d.g_scale = grads->scale; d.g_quat = grads->quat; d.g_opac = grads->opacity;
         d.g_sh = grads->sh;
+        d.sem = scene->sem;
+        d.n_sem = scene->n_sem;
+        d.dl_feat = dL[v].feat;
+        d.g_sem = (f->feat_mask & kFeatSem) ? grads->sem : nullptr;
     }
     const size_t N = (size_t)scene->n, K = (size_t)(scene->sh_degree + 1) * (scene->sh_degree + 1);
     struct { float *p; size_t n; } zero[] = {
@@ -677,9 +712,11 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
             if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
     if (scene->sky && grads->sky)
         PVG_CUDA(cudaMemsetAsync(grads->sky, 0, sizeof(float) * 18 * (size_t)scene->sky_res * scene->sky_res, s));
+    if ((f->feat_mask & kFeatSem) && grads->sem)
+        PVG_CUDA(cudaMemsetAsync(grads->sem, 0, sizeof(float) * N * (size_t)f->n_sem, s));
     if (f->n_items == 0 && !scene->sky) return PVG_OK;
-    if (capturing && f->g2d.bytes < sizeof(float) * 10 * (size_t)f->n_items) return PVG_ERR_INVALID;
-    PVG_TRY(ensure(f->g2d, sizeof(float) * 10 * (size_t)f->n_items));
+    PVG_TRY(ensure_c(f->g2d, sizeof(float) * 10 * (size_t)f->n_items, capturing));
+    if (feat_bwd) PVG_TRY(ensure_c(f->gfeat, sizeof(float) * f->n_feat * (size_t)f->n_items, capturing));
     PVG_TRY(stage_views(*f->stage_bwd, views, s, capturing));
 
     Params p;
@@ -707,16 +744,27 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.g2d = ptr<float>(f->g2d);
+    if (feat_bwd) {
+        p.feat_mask = f->feat_mask;
+        p.n_feat = f->n_feat;
+        p.gfeat = ptr<float>(f->gfeat);
+    }
     StageTimer &tm = x->timer;
     const bool timer_on = tm.on;
     if (capturing) tm.on = false;
     tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
     note_launch();
-    k_zero_g2d<<<152 * 4, 256, 0, s>>>(p.g2d, &p.counters[0]);
+    k_zero_rows<<<152 * 4, 256, 0, s>>>(p.g2d, &p.counters[0], 10);
     launch_composite_bwd(p, s);
+    if (feat_bwd && f->n_items) {
+        note_launch();
+        k_zero_rows<<<152 * 4, 256, 0, s>>>(p.gfeat, &p.counters[0], p.n_feat);
+        launch_composite_feat_bwd(p, s);
+    }
     tm.end(PVG_STAGE_COMPOSITE_BWD, s);
     tm.begin(PVG_STAGE_PREPROCESS_BWD, s);
     launch_preprocess_bwd(p, n_views > 1, s);
+    if (feat_bwd) launch_feat_param_bwd(p, s);
     tm.end(PVG_STAGE_PREPROCESS_BWD, s);
     tm.on = timer_on;
     PVG_CUDA(cudaGetLastError());

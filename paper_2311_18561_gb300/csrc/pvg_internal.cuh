@@ -46,13 +46,21 @@ struct ViewDesc {
     const float *sky;        // [6][R][R][3] cube map or NULL (constant bg)
     const float *sky_jitter; // [2][H][W] pixel offsets of the sky rays or NULL
     int32_t sky_res, pad1;
+    const float *sem;        // [n][n_sem] semantic vectors or NULL
+    int32_t n_sem, pad2;
     // outputs
     float *out_rgb, *out_depth, *out_alpha;
+    float *out_feat;         // [F][H][W] extra channels or NULL
     // backward inputs / outputs
-    const float *dl_rgb, *dl_depth, *dl_alpha;
+    const float *dl_rgb, *dl_depth, *dl_alpha, *dl_feat;
     float *g_mu, *g_vel, *g_tau, *g_beta, *g_period, *g_scale, *g_quat, *g_opac, *g_sh;
-    float *g_sky;
+    float *g_sky, *g_sem;
 };
+
+// extra composited channels (bit mask): v_bar (3), min(rho, 2) (1), semantics (n_sem)
+constexpr int kFeatVbar = 1, kFeatRho = 2, kFeatSem = 4;
+constexpr int kMaxSem = 32;
+constexpr int kMaxFeatGroups = 9;  // channels padded to float4 groups: 3 + 1 + 32 = 36
 
 // Launch-wide parameters.
 struct Params {
@@ -90,6 +98,10 @@ struct Params {
     uint32_t *pix_neval;     // [2][sum HW] stats pass: in-footprint entries up to the stop, and blended ones
     // backward
     float *g2d;              // [M*10]
+    // extra channels
+    int32_t feat_mask;       // kFeat* bits (0: none)
+    int32_t n_feat;          // F
+    float *gfeat;            // [M*F] dL/d(channel value) per visible item
 };
 
 // view of a global item / tile by binary search over the per-view bases
@@ -116,6 +128,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// The compositor's terms of record m: (u, v, a', b'), (c', o~), (r, g, b, z)
+// with the conic pre-scaled, (a', b', c') = -log2(e) (a/2, b, c/2).  Every
+// kernel that blends takes its alpha from these terms, so the blending
+// weights agree bit for bit across kernels.
+__device__ __forceinline__ void record_terms(const float4 *rec, uint32_t m, float4 &s0, float2 &s1, float4 &s2) {
+    const float4 a = rec[3 * (size_t)m], b = rec[3 * (size_t)m + 1], c = rec[3 * (size_t)m + 2];
+    s0 = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
+    s1 = make_float2(-0.5f * kLog2e * b.x, b.y);
+    s2 = make_float4(c.x, c.y, c.z, b.z);
 }
 
 // Gaussian falloff exponent in base-2 units for the record's prescaled
@@ -195,4 +218,9 @@ bool composite_supported(int tw, int th, int px);
 void launch_composite(const Params &p, cudaStream_t s);
 void launch_composite_stats(const Params &p, cudaStream_t s);
 void launch_composite_bwd(const Params &p, cudaStream_t s);
+// extra channels
+int feat_count(int mask, int n_sem);
+void launch_composite_feat(const Params &p, cudaStream_t s);
+void launch_composite_feat_bwd(const Params &p, cudaStream_t s);
+void launch_feat_param_bwd(const Params &p, cudaStream_t s);
 }  // namespace pvg

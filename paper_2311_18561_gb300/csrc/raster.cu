@@ -57,10 +57,12 @@ __device__ __forceinline__ TileGeom tile_geom(const Params &P) {
 
 __device__ __forceinline__ void stage_record(const Params &P, uint32_t m, float4 *s0, float2 *s1, float4 *s2,
                                              int slot) {
-    const float4 a = P.rec[3 * (size_t)m], b = P.rec[3 * (size_t)m + 1], c = P.rec[3 * (size_t)m + 2];
-    s0[slot] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-    s1[slot] = make_float2(-0.5f * kLog2e * b.x, b.y);
-    s2[slot] = make_float4(c.x, c.y, c.z, b.z);
+    float4 a, c;
+    float2 b;
+    record_terms(P.rec, m, a, b, c);
+    s0[slot] = a;
+    s1[slot] = b;
+    s2[slot] = c;
 }
 
 // kStats: instead of images, write per pixel the number of list entries

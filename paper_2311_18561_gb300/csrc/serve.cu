@@ -232,6 +232,7 @@ extern "C" pvg_status_t pvg_serve_add_scene(pvg_server_t *S, const pvg_scene_t *
 extern "C" pvg_status_t pvg_serve_submit(pvg_server_t *S, int32_t scene_id, const pvg_camera_t *cam,
                                          const pvg_image_t *dst, uint64_t *req_id) {
     if (!S || !cam || !dst || !dst->rgb || !req_id) return PVG_ERR_INVALID;
+    if (dst->feat_mask != 0) return PVG_ERR_INVALID;  // served requests render colour, depth, opacity
     if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384) return PVG_ERR_INVALID;
     {
         std::lock_guard<std::mutex> lk(S->mu);

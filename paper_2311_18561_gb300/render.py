@@ -62,7 +62,33 @@ def abi_scene(scene_t) -> abi.Scene:
             raise ValueError("scene['sky'] must be a contiguous float32 CUDA tensor [6, R, R, 3]")
         s.sky = sky.data_ptr()
         s.sky_res = int(sky.shape[1])
+    sem = scene_t.get("sem")
+    if sem is not None:
+        if (sem.dim() != 2 or sem.shape[0] != n or not 1 <= sem.shape[1] <= abi.MAX_SEM
+                or sem.dtype != torch.float32 or not sem.is_contiguous() or not sem.is_cuda):
+            raise ValueError("scene['sem'] must be a contiguous float32 CUDA tensor [N, S], 1 <= S <= %d"
+                             % abi.MAX_SEM)
+        s.sem = sem.data_ptr() if n > 0 else None
+        s.n_sem = int(sem.shape[1])
     return s
+
+
+def feat_count(features, n_sem=0):
+    """Channels of the extra-channel image for a FEAT_* mask."""
+    return ((3 if features & abi.FEAT_VBAR else 0) + (1 if features & abi.FEAT_RHO else 0)
+            + (n_sem if features & abi.FEAT_SEM else 0))
+
+
+def _fill_images(imgs, outs, features):
+    for k, o in enumerate(outs):
+        imgs[k].rgb = o["rgb"].data_ptr()
+        imgs[k].depth = o["depth"].data_ptr() if o.get("depth") is not None else None
+        imgs[k].alpha = o["alpha"].data_ptr() if o.get("alpha") is not None else None
+        if features:
+            if o.get("feat") is None:
+                raise ValueError("features requested: every output needs a 'feat' tensor [F, H, W]")
+            imgs[k].feat = o["feat"].data_ptr()
+            imgs[k].feat_mask = int(features)
 
 
 def _stream_ptr(stream=None):
@@ -99,27 +125,30 @@ class Renderer:
             self.cfg.pixels_per_thread = int(pixels_per_thread)
         abi.check(self._lib.pvg_set_config(self.handle, C.byref(self.cfg)), "pvg_set_config")
 
-    def alloc_images(self, cams, device="cuda"):
+    def alloc_images(self, cams, device="cuda", features=0, n_sem=0):
         outs = []
+        F = feat_count(features, n_sem)
         for cam in cams:
             H, W = int(cam["height"]), int(cam["width"])
-            outs.append(dict(rgb=torch.empty(3, H, W, device=device), depth=torch.empty(H, W, device=device),
-                             alpha=torch.empty(H, W, device=device)))
+            o = dict(rgb=torch.empty(3, H, W, device=device), depth=torch.empty(H, W, device=device),
+                     alpha=torch.empty(H, W, device=device))
+            if F:
+                o["feat"] = torch.empty(F, H, W, device=device)
+            outs.append(o)
         return outs
 
-    def forward(self, scene_t, cams, outs=None, frame=None, stream=None):
-        """Render into ``outs`` (list of dicts rgb [3,H,W], depth, alpha);
-        returns ``outs``.  ``frame`` (a :class:`Frame`) keeps the state the
-        backward pass needs."""
+    def forward(self, scene_t, cams, outs=None, frame=None, stream=None, features=0):
+        """Render into ``outs`` (list of dicts rgb [3,H,W], depth, alpha and,
+        with ``features`` (a mask of abi.FEAT_*), feat [F,H,W]); returns
+        ``outs``.  ``frame`` (a :class:`Frame`) keeps the state the backward
+        pass needs."""
         if outs is None:
-            outs = self.alloc_images(cams)
+            sem = scene_t.get("sem")
+            outs = self.alloc_images(cams, features=features, n_sem=0 if sem is None else int(sem.shape[1]))
         sc = abi_scene(scene_t)
         ca = abi.cameras(cams)
         imgs = (abi.Image * len(cams))()
-        for k, o in enumerate(outs):
-            imgs[k].rgb = o["rgb"].data_ptr()
-            imgs[k].depth = o["depth"].data_ptr() if o.get("depth") is not None else None
-            imgs[k].alpha = o["alpha"].data_ptr() if o.get("alpha") is not None else None
+        _fill_images(imgs, outs, features)
         st = self._lib.pvg_render_fwd(self.handle, C.byref(sc), ca, len(cams), imgs,
                                       frame.handle if frame is not None else None, _stream_ptr(stream))
         abi.check(st, "pvg_render_fwd")
@@ -134,12 +163,14 @@ class Renderer:
             grads = {k: torch.empty_like(scene_t[k]) for k in PARAM_NAMES}
             if scene_t.get("sky") is not None:
                 grads["sky"] = torch.empty_like(scene_t["sky"])
+            if scene_t.get("sem") is not None:
+                grads["sem"] = torch.zeros_like(scene_t["sem"])
         g = abi.SceneGrad()
-        for k in PARAM_NAMES + ("sky",):
+        for k in PARAM_NAMES + ("sky", "sem"):
             setattr(g, k, grads[k].data_ptr() if (grads.get(k) is not None and grads[k].numel()) else None)
         dl = (abi.ImageGrad * len(cams))()
         for k, d in enumerate(grads_out):
-            for name in ("rgb", "depth", "alpha"):
+            for name in ("rgb", "depth", "alpha", "feat"):
                 t = d.get(name)
                 setattr(dl[k], name, t.contiguous().data_ptr() if t is not None else None)
         st = self._lib.pvg_render_bwd(self.handle, C.byref(sc), ca, len(cams), frame.handle, dl, C.byref(g),
@@ -206,10 +237,11 @@ def default_renderer():
     return _DEFAULT[dev]
 
 
-def render(scene_t, cams, renderer=None, frame=None):
-    """Render a list of cameras; returns a list of dicts (rgb, depth, alpha)."""
+def render(scene_t, cams, renderer=None, frame=None, features=0):
+    """Render a list of cameras; returns a list of dicts (rgb, depth, alpha
+    and, for a FEAT_* mask ``features``, feat)."""
     r = renderer or default_renderer()
-    return r.forward(scene_t, cams, frame=frame)
+    return r.forward(scene_t, cams, frame=frame, features=features)
 
 
 class PVGRender(torch.autograd.Function):
@@ -314,10 +346,7 @@ def render_multi(renderer, scenes, cams, outs=None, frame=None, stream=None):
         sc[k] = abi_scene(s)
     ca = abi.cameras(cams)
     imgs = (abi.Image * len(cams))()
-    for k, o in enumerate(outs):
-        imgs[k].rgb = o["rgb"].data_ptr()
-        imgs[k].depth = o["depth"].data_ptr() if o.get("depth") is not None else None
-        imgs[k].alpha = o["alpha"].data_ptr() if o.get("alpha") is not None else None
+    _fill_images(imgs, outs, 0)
     st = abi.lib().pvg_render_fwd_multi(renderer.handle, sc, ca, len(cams), imgs,
                                         frame.handle if frame is not None else None, _stream_ptr(stream))
     abi.check(st, "pvg_render_fwd_multi")
