@@ -5,8 +5,11 @@ linked into ``_lib/libpvg.so`` inside the package (in-tree, git-ignored).
 Flags: ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo
 --fmad=false``.  ``--fmad=false`` keeps the compiler from fusing a*b+c on
 its own, so the same expression rounds the same way in every kernel that
-evaluates it (the projection is recomputed in three kernels and must agree
-bit for bit); the hot loops spell out their fused multiply-adds.
+evaluates it (the projection is computed by two forward kernels that must
+agree bit for bit; the compositors spell out their fused multiply-adds).
+The adjoint translation units (``*_bwd.cu``) take no decision that another
+kernel must reproduce -- their blend decisions use the forward's explicitly
+rounded expressions -- and are compiled with ``--fmad=true``.
 """
 from __future__ import annotations
 
@@ -24,8 +27,11 @@ LIB = os.path.join(LIBDIR, "libpvg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-              "-Xptxas", "-warn-spills"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-Xptxas", "-warn-spills"]
+
+
+def fmad_flag(src) -> str:
+    return "--fmad=true" if os.path.basename(src).endswith("_bwd.cu") else "--fmad=false"
 
 
 def nvcc() -> str:
@@ -59,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, fmad_flag(src), *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

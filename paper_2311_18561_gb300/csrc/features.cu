@@ -1,5 +1,5 @@
 // features.cu -- extra composited channels: the velocity, staticness and
-// semantic maps, and their adjoint.
+// semantic maps (the adjoint is in features_bwd.cu).
 //
 // Each channel is a per-point value x_i composited with the colour's
 // weights w_i = T_i alpha_i and no background:
@@ -16,16 +16,7 @@
 // float4 groups.  Alpha comes from record_terms / falloff_exp2 / ex2 with
 // the colour pass's roundings, so the weights are the colour pass's bit
 // for bit.
-//
-// Adjoint: the same walk back to front as the colour adjoint, from the
-// pixel's final transmittance and last blended position.  The suffix sums
-// S = sum_{j > i} x_j w_j give
-//   dL/dalpha_i (channels) = T_i gF.x_i - gF.S / (1 - alpha_i),
-// whose effect on (u, v, conic, o~) is added to the image-space gradient
-// buffer in the colour adjoint's moment form, and dL/dx_i = sum gF w_i is
-// accumulated per visible point.  k_feat_param_bwd then maps dL/dx to v,
-// beta, l and the semantic vectors.
-#include "pvg_internal.cuh"
+#include "features_common.cuh"
 
 namespace pvg {
 
@@ -34,52 +25,6 @@ int feat_count(int mask, int n_sem) {
 }
 
 namespace {
-
-constexpr int kFB = 128;       // list entries staged per batch
-constexpr int kFeatBlock = 256;  // threads per CTA (fewer for small tiles)
-
-// channel values of item gid into dst[0 .. 4 NG) (zero padded)
-template <int NG>
-__device__ __forceinline__ void stage_feat(const ViewDesc &V, uint32_t gid, int mask, float *dst) {
-#pragma unroll
-    for (int c = 0; c < 4 * NG; c++) dst[c] = 0.f;
-    const uint32_t i = gid - V.item_base;
-    const float beta = V.beta[i], l = V.period[i];
-    const float rho = __fdiv_rn(beta, l);
-    int c = 0;
-    if (mask & kFeatVbar) {
-        const float w = expf(-0.5f * rho);
-        dst[0] = V.vel[3 * (size_t)i] * w;
-        dst[1] = V.vel[3 * (size_t)i + 1] * w;
-        dst[2] = V.vel[3 * (size_t)i + 2] * w;
-        c = 3;
-    }
-    if (mask & kFeatRho) dst[c++] = fminf(rho, 2.0f);
-    if (mask & kFeatSem)
-        for (int k = 0; k < V.n_sem; k++) dst[c + k] = V.sem[(size_t)i * V.n_sem + k];
-}
-
-struct FeatPixel {
-    const ViewDesc *V;
-    int px, py;
-    bool inside;
-    uint2 r;
-};
-
-__device__ __forceinline__ FeatPixel feat_pixel(const Params &P, int round) {
-    FeatPixel q;
-    const uint32_t tile = P.tile_order ? P.tile_order[blockIdx.x] : blockIdx.x;
-    q.V = &P.views[view_of_tile(P.views, P.n_views, tile)];
-    const uint32_t lt = tile - q.V->tile_base;
-    const int tx = (int)(lt % (uint32_t)q.V->tiles_x), ty = (int)(lt / (uint32_t)q.V->tiles_x);
-    const int k = round * (int)blockDim.x + (int)threadIdx.x;  // pixel of the tile, row-major
-    const bool in_tile = k < P.tile_w * P.tile_h;
-    q.px = tx * P.tile_w + k % P.tile_w;
-    q.py = ty * P.tile_h + k / P.tile_w;
-    q.inside = in_tile && q.px < q.V->W && q.py < q.V->H;
-    q.r = P.ranges[tile];
-    return q;
-}
 
 template <int NG>
 __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
@@ -142,247 +87,23 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
     }
 }
 
-// Sum over the warp of N terms (N a power of two <= 32): afterwards lane L
-// holds the total of term L & (N - 1).  Transposing butterfly: N - 1
-// shuffles, then 5 - log2(N) to fold the lane groups.
-template <int S, int N>
-__device__ __forceinline__ void transpose_level(float (&a)[N], int lane) {
-    if constexpr (S >= 1) {
-        const bool hi = lane & S;
-#pragma unroll
-        for (int i = 0; i < S; i++) {
-            const float send = hi ? a[i] : a[i + S];
-            a[i] = (hi ? a[i + S] : a[i]) + __shfl_xor_sync(0xffffffffu, send, S);
-        }
-        transpose_level<S / 2, N>(a, lane);
-    }
-}
-
-template <int N>
-__device__ __forceinline__ float warp_transpose_sum(float (&a)[N]) {
-    const int lane = threadIdx.x & 31;
-    transpose_level<N / 2, N>(a, lane);
-    float v = a[0];
-#pragma unroll
-    for (int s = N; s < 32; s <<= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-    return v;
-}
-
-__host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
-
-// adds terms [B, B + N) of gv (N a power of two) into s_acc[k * NT + term]
-template <int NT, int B, int N>
-__device__ __forceinline__ void reduce_chunk(const float (&gv)[NT], float *s_acc, int k) {
-    float a[N];
-#pragma unroll
-    for (int i = 0; i < N; i++) a[i] = B + i < NT ? gv[B + i] : 0.f;
-    const float v = warp_transpose_sum<N>(a);
-    const int lane = threadIdx.x & 31, term = B + (lane & (N - 1));
-    if (lane < N && term < NT && v != 0.f) atomicAdd(&s_acc[k * NT + term], v);
-}
-
-template <int NG>
-__global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
-    constexpr int F4 = 4 * NG;
-    constexpr int NT = 6 + F4;  // moments x, y, xx, xy, yy; opacity; channels
-    __shared__ float4 s0[kFB];
-    __shared__ float2 s1[kFB];
-    __shared__ float4 sf[kFB * NG];
-    __shared__ uint32_t s_m[kFB];
-    __shared__ float s_acc[kFB * NT];
-    __shared__ uint32_t s_maxlast;
-    const int rounds = (P.tile_w * P.tile_h + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int tid = threadIdx.x;
-    for (int round = 0; round < rounds; round++) {
-        const FeatPixel Q = feat_pixel(P, round);
-        const ViewDesc &V = *Q.V;
-        const float fx = (float)Q.px + 0.5f, fy = (float)Q.py + 0.5f;
-        float T = 1.0f, gF[F4], sF[F4];
-        uint32_t last = 0;
-#pragma unroll
-        for (int c = 0; c < F4; c++) gF[c] = sF[c] = 0.f;
-        if (Q.inside && V.dl_feat) {
-            const size_t HW = (size_t)V.W * V.H, pix = (size_t)Q.py * V.W + Q.px;
-            T = P.pix_T[V.pix_base + pix];
-            last = P.pix_last[V.pix_base + pix];
-#pragma unroll
-            for (int c = 0; c < F4; c++)
-                if (c < P.n_feat) gF[c] = V.dl_feat[c * HW + pix];
-        }
-        __syncthreads();  // previous round done with the shared arrays
-        if (tid == 0) s_maxlast = 0;
-        __syncthreads();
-        if (last) atomicMax(&s_maxlast, last);
-        __syncthreads();
-        const uint32_t n = s_maxlast;
-        for (uint32_t end = Q.r.x + n; end > Q.r.x;) {
-            const uint32_t start = end - Q.r.x > (uint32_t)kFB ? end - kFB : Q.r.x;
-            const int cnt = (int)(end - start);
-            __syncthreads();
-            for (int k = tid; k < cnt; k += blockDim.x) {
-                const uint32_t m = P.pair_vals[start + k];
-                float4 a, c;
-                float2 b;
-                record_terms(P.rec, m, a, b, c);
-                s0[k] = a;
-                s1[k] = b;
-                s_m[k] = m;
-                stage_feat<NG>(V, P.sgid[m], P.feat_mask, reinterpret_cast<float *>(&sf[k * NG]));
-            }
-            for (int k = tid; k < kFB * NT; k += blockDim.x) s_acc[k] = 0.f;
-            __syncthreads();
-            for (int k = cnt - 1; k >= 0; k--) {
-                const uint32_t pos = start + k - Q.r.x;
-                float gv[NT];
-#pragma unroll
-                for (int c = 0; c < NT; c++) gv[c] = 0.f;
-                bool contrib = false;
-                if (pos < last) {
-                    const float4 g = s0[k];
-                    const float2 q = s1[k];
-                    const float dx = __fsub_rn(fx, g.x), dy = __fsub_rn(fy, g.y);
-                    const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
-                    const float G = ex2_approx(e);
-                    const float raw = __fmul_rn(q.y, G);
-                    const float alpha = fminf(kAlphaCap, raw);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float inv = __frcp_rn(1.0f - alpha);
-                        const float Ti = T * inv;
-                        const float w = alpha * Ti;
-                        float df = 0.f, ds = 0.f;
-#pragma unroll
-                        for (int gi = 0; gi < NG; gi++) {
-                            const float4 f = sf[k * NG + gi];
-                            const float fv[4] = {f.x, f.y, f.z, f.w};
-#pragma unroll
-                            for (int j = 0; j < 4; j++) {
-                                const int c = 4 * gi + j;
-                                df += gF[c] * fv[j];
-                                ds += gF[c] * sF[c];
-                                gv[6 + c] = gF[c] * w;
-                                sF[c] += fv[j] * w;
-                            }
-                        }
-                        if (raw <= kAlphaCap) {
-                            const float ga = Ti * df - inv * ds;
-                            gv[5] = ga * G;
-                            const float gpow = ga * alpha;
-                            const float mx = gpow * dx, my = gpow * dy;
-                            gv[0] = mx;
-                            gv[1] = my;
-                            gv[2] = mx * dx;
-                            gv[3] = mx * dy;
-                            gv[4] = my * dy;
-                        }
-                        T = Ti;
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    constexpr int N0 = NT >= 32 ? 32 : pow2_at_least(NT);
-                    reduce_chunk<NT, 0, N0>(gv, s_acc, k);
-                    if constexpr (NT > 32) reduce_chunk<NT, 32, pow2_at_least(NT - 32)>(gv, s_acc, k);
-                }
-            }
-            __syncthreads();
-            // image-space terms from the moments (as in the colour adjoint)
-            // and the channel gradients of each staged point
-            for (int k = tid; k < cnt; k += blockDim.x) {
-                const float *a = &s_acc[k * NT];
-                const float ap = s0[k].z, bp = s0[k].w, cp = s1[k].x;
-                float gt[6];
-                gt[0] = -0.6931471805599453f * (2.f * ap * a[0] + bp * a[1]);
-                gt[1] = -0.6931471805599453f * (bp * a[0] + 2.f * cp * a[1]);
-                gt[2] = -0.5f * a[2];
-                gt[3] = -a[3];
-                gt[4] = -0.5f * a[4];
-                gt[5] = a[5];
-                float *dst = &P.g2d[10 * (size_t)s_m[k]];
-#pragma unroll
-                for (int c = 0; c < 6; c++)
-                    if (gt[c] != 0.f) atomicAdd(dst + c, gt[c]);
-                float *gf = &P.gfeat[(size_t)s_m[k] * P.n_feat];
-                for (int c = 0; c < P.n_feat; c++)
-                    if (a[6 + c] != 0.f) atomicAdd(gf + c, a[6 + c]);
-            }
-            end = start;
-        }
-    }
-}
-
-// dL/d(channel values) of each visible item -> v, beta, l, semantics
-__global__ void k_feat_param_bwd(Params P) {
-    const uint32_t M = P.counters[0];
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-        const uint32_t gid = P.sgid[m];
-        const ViewDesc &V = P.views[view_of_item(P.views, P.n_views, gid)];
-        const uint32_t i = gid - V.item_base;
-        const float *gf = &P.gfeat[(size_t)m * P.n_feat];
-        const float beta = V.beta[i], l = V.period[i];
-        const float rho = __fdiv_rn(beta, l);
-        float grho = 0.f;  // dL/drho
-        int c = 0;
-        if (P.feat_mask & kFeatVbar) {
-            // v_bar = v exp(-rho / 2): d/dv = exp(-rho / 2), d/drho = -v_bar / 2
-            const float w = expf(-0.5f * rho);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                if (V.g_vel && gf[k] != 0.f) atomicAdd(V.g_vel + 3 * (size_t)i + k, gf[k] * w);
-                grho -= 0.5f * gf[k] * V.vel[3 * (size_t)i + k] * w;
-            }
-            c = 3;
-        }
-        if (P.feat_mask & kFeatRho) {
-            if (rho < 2.0f) grho += gf[c];
-            c++;
-        }
-        if (grho != 0.f) {
-            // rho = beta / l
-            if (V.g_beta) atomicAdd(V.g_beta + i, grho / l);
-            if (V.g_period) atomicAdd(V.g_period + i, -grho * beta / (l * l));
-        }
-        if ((P.feat_mask & kFeatSem) && V.g_sem)
-            for (int k = 0; k < V.n_sem; k++)
-                if (gf[c + k] != 0.f) atomicAdd(V.g_sem + (size_t)i * V.n_sem + k, gf[c + k]);
-    }
-}
-
-template <int NG>
-void launch_feat_t(const Params &p, cudaStream_t s, bool bwd) {
-    note_launch();
-    const int block = min(kFeatBlock, p.tile_w * p.tile_h);
-    if (bwd)
-        k_composite_feat_bwd<NG><<<p.total_tiles, block, 0, s>>>(p);
-    else
-        k_composite_feat<NG><<<p.total_tiles, block, 0, s>>>(p);
-}
-
-void dispatch_feat(const Params &p, cudaStream_t s, bool bwd) {
-    if (p.total_tiles == 0 || p.n_feat <= 0) return;
-    switch ((p.n_feat + 3) / 4) {
-        case 1: return launch_feat_t<1>(p, s, bwd);
-        case 2: return launch_feat_t<2>(p, s, bwd);
-        case 3: return launch_feat_t<3>(p, s, bwd);
-        case 4: return launch_feat_t<4>(p, s, bwd);
-        case 5: return launch_feat_t<5>(p, s, bwd);
-        case 6: return launch_feat_t<6>(p, s, bwd);
-        case 7: return launch_feat_t<7>(p, s, bwd);
-        case 8: return launch_feat_t<8>(p, s, bwd);
-        case 9: return launch_feat_t<9>(p, s, bwd);
-        default: return;
-    }
-}
-
 }  // namespace
 
-void launch_composite_feat(const Params &p, cudaStream_t s) { dispatch_feat(p, s, false); }
-
-void launch_composite_feat_bwd(const Params &p, cudaStream_t s) { dispatch_feat(p, s, true); }
-
-void launch_feat_param_bwd(const Params &p, cudaStream_t s) {
-    if (p.n_items == 0 || p.n_feat <= 0) return;
+void launch_composite_feat(const Params &p, cudaStream_t s) {
+    if (p.total_tiles == 0 || p.n_feat <= 0) return;
     note_launch();
-    k_feat_param_bwd<<<152 * 4, 256, 0, s>>>(p);
+    const int block = min(kFeatBlock, p.tile_w * p.tile_h);
+    switch ((p.n_feat + 3) / 4) {
+        case 1: k_composite_feat<1><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 2: k_composite_feat<2><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 3: k_composite_feat<3><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 4: k_composite_feat<4><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 5: k_composite_feat<5><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 6: k_composite_feat<6><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 7: k_composite_feat<7><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 8: k_composite_feat<8><<<p.total_tiles, block, 0, s>>>(p); break;
+        default: k_composite_feat<9><<<p.total_tiles, block, 0, s>>>(p); break;
+    }
 }
 
 }  // namespace pvg

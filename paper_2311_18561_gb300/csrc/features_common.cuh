@@ -1,0 +1,56 @@
+// features_common.cuh -- staging of the extra channels shared by their
+// compositing pass (features.cu) and its adjoint (features_bwd.cu).
+#pragma once
+#include "pvg_internal.cuh"
+
+namespace pvg {
+namespace {
+
+constexpr int kFB = 128;       // list entries staged per batch
+constexpr int kFeatBlock = 256;  // threads per CTA (fewer for small tiles)
+
+// channel values of item gid into dst[0 .. 4 NG) (zero padded)
+template <int NG>
+__device__ __forceinline__ void stage_feat(const ViewDesc &V, uint32_t gid, int mask, float *dst) {
+#pragma unroll
+    for (int c = 0; c < 4 * NG; c++) dst[c] = 0.f;
+    const uint32_t i = gid - V.item_base;
+    const float beta = V.beta[i], l = V.period[i];
+    const float rho = __fdiv_rn(beta, l);
+    int c = 0;
+    if (mask & kFeatVbar) {
+        const float w = expf(-0.5f * rho);
+        dst[0] = V.vel[3 * (size_t)i] * w;
+        dst[1] = V.vel[3 * (size_t)i + 1] * w;
+        dst[2] = V.vel[3 * (size_t)i + 2] * w;
+        c = 3;
+    }
+    if (mask & kFeatRho) dst[c++] = fminf(rho, 2.0f);
+    if (mask & kFeatSem)
+        for (int k = 0; k < V.n_sem; k++) dst[c + k] = V.sem[(size_t)i * V.n_sem + k];
+}
+
+struct FeatPixel {
+    const ViewDesc *V;
+    int px, py;
+    bool inside;
+    uint2 r;
+};
+
+__device__ __forceinline__ FeatPixel feat_pixel(const Params &P, int round) {
+    FeatPixel q;
+    const uint32_t tile = P.tile_order ? P.tile_order[blockIdx.x] : blockIdx.x;
+    q.V = &P.views[view_of_tile(P.views, P.n_views, tile)];
+    const uint32_t lt = tile - q.V->tile_base;
+    const int tx = (int)(lt % (uint32_t)q.V->tiles_x), ty = (int)(lt / (uint32_t)q.V->tiles_x);
+    const int k = round * (int)blockDim.x + (int)threadIdx.x;  // pixel of the tile, row-major
+    const bool in_tile = k < P.tile_w * P.tile_h;
+    q.px = tx * P.tile_w + k % P.tile_w;
+    q.py = ty * P.tile_h + k / P.tile_w;
+    q.inside = in_tile && q.px < q.V->W && q.py < q.V->H;
+    q.r = P.ranges[tile];
+    return q;
+}
+
+}  // namespace
+}  // namespace pvg

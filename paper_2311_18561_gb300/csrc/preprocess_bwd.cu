@@ -1,0 +1,246 @@
+// preprocess_bwd.cu -- adjoint of the per-item projection and colour
+// (stage d2): in item order, from the image-space gradients of record
+// m = inv[g] to dL/d{mu, v, tau, beta, l, s, q, o, sh} (Sec. 3.1, Eq. 2-4;
+// Sec. 3.2, Eq. 6-8; the flow shift of Sec. 3.4).  Visibility comes from
+// inv[]; the projection is recomputed for its intermediate terms only, so
+// this file may contract a*b+c into fused multiply-adds.
+#include "preprocess_common.cuh"
+
+namespace pvg {
+
+cudaError_t set_sh_constants_bwd() {
+    float h[10];
+    sh_constant_values(h);
+    return cudaMemcpyToSymbol(c_sh, h, sizeof(h));
+}
+
+namespace {
+
+__device__ __forceinline__ void put(float *dst, size_t k, float v, bool atomic) {
+    if (atomic) atomicAdd(dst + k, v);
+    else dst[k] = v;
+}
+
+// Writes zero gradients for item g of view V (single-view calls, where
+// this kernel writes every gradient entry instead of a separate memset).
+template <int K>
+__device__ __forceinline__ void zero_grads(const ViewDesc &V, uint32_t i) {
+    if (V.g_mu) for (int k = 0; k < 3; k++) V.g_mu[3 * (size_t)i + k] = 0.f;
+    if (V.g_vel) for (int k = 0; k < 3; k++) V.g_vel[3 * (size_t)i + k] = 0.f;
+    if (V.g_scale) for (int k = 0; k < 3; k++) V.g_scale[3 * (size_t)i + k] = 0.f;
+    if (V.g_quat) {
+        const float z4[4] = {0.f, 0.f, 0.f, 0.f};
+        store_floats<4>(V.g_quat + 4 * (size_t)i, z4, aligned16(V.g_quat));
+    }
+    if (V.g_tau) V.g_tau[i] = 0.f;
+    if (V.g_beta) V.g_beta[i] = 0.f;
+    if (V.g_period) V.g_period[i] = 0.f;
+    if (V.g_opac) V.g_opac[i] = 0.f;
+    if (V.g_sh) {
+        float z[3 * K];
+#pragma unroll
+        for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
+        store_floats<3 * K>(V.g_sh + (size_t)i * 3 * K, z, aligned16(V.g_sh));
+    }
+}
+
+// Adjoint of the projection and colour, in item order: item g reads the
+// image-space gradients of its depth position m = inv[g].  With `atomic`
+// (several views share the gradients) the gradients were zeroed before and
+// are accumulated; otherwise every entry of item g is written, zeros for
+// invisible items.
+template <int D>
+__global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
+    constexpr int K = (D + 1) * (D + 1);
+    const uint32_t n = P.n_items;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const int view = view_of_item(P.views, P.n_views, g);
+        const ViewDesc &V = P.views[view];
+        const uint32_t i = g - V.item_base;
+        const uint32_t m = P.inv[g];
+        Fwd F;
+        if (m == 0xffffffffu || !project(V, i, P.dilation, P.tile_w, P.tile_h, F)) {
+            if (!atomic) zero_grads<K>(V, i);
+            continue;
+        }
+        const float *G2 = P.g2d + 10 * (size_t)m;
+        const float gu = G2[0], gv = G2[1], ga = G2[2], gb = G2[3], gc = G2[4];
+        const float got = G2[5], gz = G2[9];
+        float gmut[3] = {0.f, 0.f, 0.f};
+        float gp[3] = {0.f, 0.f, 0.f};
+
+        // ---- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5)
+        {
+            float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
+            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float inv = 1.0f / dist;
+            dx *= inv; dy *= inv; dz *= inv;
+            float Y[16], dY[16][3];
+            sh_eval<D, true>(dx, dy, dz, Y, dY);
+            float sh[3 * K];
+            load_floats<3 * K>(V.sh + (size_t)i * K * 3, sh, aligned16(V.sh));
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int k = 0; k < K; k++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) raw[c] += sh[3 * k + c] * Y[k];
+            float gcol[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) gcol[c] = raw[c] > 0.0f ? G2[6 + c] : 0.0f;
+            float gd[3] = {0.f, 0.f, 0.f};
+            if (V.g_sh) {
+                if (atomic) {
+#pragma unroll
+                    for (int k = 0; k < K; k++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) atomicAdd(V.g_sh + ((size_t)i * K + k) * 3 + c, gcol[c] * Y[k]);
+                } else {
+                    float gsh[3 * K];
+#pragma unroll
+                    for (int k = 0; k < K; k++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) gsh[3 * k + c] = gcol[c] * Y[k];
+                    store_floats<3 * K>(V.g_sh + (size_t)i * K * 3, gsh, aligned16(V.g_sh));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const float w = gcol[0] * sh[3 * k] + gcol[1] * sh[3 * k + 1] + gcol[2] * sh[3 * k + 2];
+                gd[0] += w * dY[k][0];
+                gd[1] += w * dY[k][1];
+                gd[2] += w * dY[k][2];
+            }
+            const float dot = dx * gd[0] + dy * gd[1] + dz * gd[2];
+            gmut[0] += (gd[0] - dx * dot) * inv;
+            gmut[1] += (gd[1] - dy * dot) * inv;
+            gmut[2] += (gd[2] - dz * dot) * inv;
+        }
+
+        // ---- conic = inverse(cov2): dL/dcov2 = -Q Ghat Q
+        const float a = F.ca, b = F.cb, c = F.cc;
+        const float gA = -(a * a * ga + a * b * gb + b * b * gc);
+        const float gB = -(a * b * ga + 0.5f * (a * c + b * b) * gb + b * c * gc);  // symmetric entry
+        const float gC = -(b * b * ga + b * c * gb + c * c * gc);
+        // ---- cov2 = Tm Sigma Tm^T: G_Sigma = Tm^T G2 Tm, G_Tm = 2 G2 Tm Sigma
+        const float *Tm = F.Tm, *S = F.Sig;
+        float GS[6];  // xx xy xz yy yz zz of the symmetric gradient
+        {
+            float U[6];  // G2 Tm (2x3)
+            for (int k = 0; k < 3; k++) {
+                U[k] = gA * Tm[k] + gB * Tm[3 + k];
+                U[3 + k] = gB * Tm[k] + gC * Tm[3 + k];
+            }
+            GS[0] = Tm[0] * U[0] + Tm[3] * U[3];
+            GS[1] = Tm[0] * U[1] + Tm[3] * U[4];
+            GS[2] = Tm[0] * U[2] + Tm[3] * U[5];
+            GS[3] = Tm[1] * U[1] + Tm[4] * U[4];
+            GS[4] = Tm[1] * U[2] + Tm[4] * U[5];
+            GS[5] = Tm[2] * U[2] + Tm[5] * U[5];
+            // G_Tm = 2 U Sigma
+            float GT[6];
+            for (int r = 0; r < 2; r++) {
+                const float *u = U + 3 * r;
+                GT[3 * r + 0] = 2.f * (u[0] * S[0] + u[1] * S[1] + u[2] * S[2]);
+                GT[3 * r + 1] = 2.f * (u[0] * S[1] + u[1] * S[3] + u[2] * S[4]);
+                GT[3 * r + 2] = 2.f * (u[0] * S[2] + u[1] * S[4] + u[2] * S[5]);
+            }
+            // Tm = J W: dL/dJ = G_Tm W^T (only J00, J02, J11, J12 are free)
+            const float *R = V.R;
+            const float gJ00 = GT[0] * R[0] + GT[1] * R[1] + GT[2] * R[2];
+            const float gJ02 = GT[0] * R[6] + GT[1] * R[7] + GT[2] * R[8];
+            const float gJ11 = GT[3] * R[3] + GT[4] * R[4] + GT[5] * R[5];
+            const float gJ12 = GT[3] * R[6] + GT[4] * R[7] + GT[5] * R[8];
+            const float z = F.p.z, iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+            gp[2] += gJ00 * (-V.fx * iz2) + gJ11 * (-V.fy * iz2);
+            if (F.clampx == 0) {
+                gp[0] += gJ02 * (-V.fx * iz2);
+                gp[2] += gJ02 * (2.f * V.fx * F.p.x * iz3);
+            } else {
+                gp[2] += gJ02 * (V.fx * F.clampx * V.limx * iz2);
+            }
+            if (F.clampy == 0) {
+                gp[1] += gJ12 * (-V.fy * iz2);
+                gp[2] += gJ12 * (2.f * V.fy * F.p.y * iz3);
+            } else {
+                gp[2] += gJ12 * (V.fy * F.clampy * V.limy * iz2);
+            }
+            // projected mean and depth
+            gp[0] += gu * V.fx * iz;
+            gp[1] += gv * V.fy * iz;
+            gp[2] += -(gu * V.fx * F.p.x + gv * V.fy * F.p.y) * iz2 + gz;
+        }
+        // ---- Sigma = M M^T, M = Rq diag(s): G_M = 2 G_Sigma M
+        {
+            float M[9];
+            for (int r = 0; r < 3; r++)
+                for (int k = 0; k < 3; k++) M[3 * r + k] = F.Rq[3 * r + k] * F.s[k];
+            const float Gs[9] = {GS[0], GS[1], GS[2], GS[1], GS[3], GS[4], GS[2], GS[4], GS[5]};
+            float GM[9];
+            for (int r = 0; r < 3; r++)
+                for (int k = 0; k < 3; k++)
+                    GM[3 * r + k] = 2.f * (Gs[3 * r] * M[k] + Gs[3 * r + 1] * M[3 + k] + Gs[3 * r + 2] * M[6 + k]);
+            float gsc[3], GR[9];
+            for (int k = 0; k < 3; k++) gsc[k] = GM[k] * F.Rq[k] + GM[3 + k] * F.Rq[3 + k] + GM[6 + k] * F.Rq[6 + k];
+            for (int r = 0; r < 3; r++)
+                for (int k = 0; k < 3; k++) GR[3 * r + k] = GM[3 * r + k] * F.s[k];
+            const float w = F.qn[0], x = F.qn[1], y = F.qn[2], zq = F.qn[3];
+            // dR/dw, dR/dx, dR/dy, dR/dz contracted with GR
+            const float gw = 2.f * (-zq * GR[1] + y * GR[2] + zq * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+            const float gx = 2.f * (y * GR[1] + zq * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + zq * GR[6] +
+                                    w * GR[7] - 2.f * x * GR[8]);
+            const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + zq * GR[5] - w * GR[6] +
+                                    zq * GR[7] - 2.f * y * GR[8]);
+            const float gzq = 2.f * (-2.f * zq * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * zq * GR[4] +
+                                     y * GR[5] + x * GR[6] + y * GR[7]);
+            const float dot = F.qn[0] * gw + F.qn[1] * gx + F.qn[2] * gy + F.qn[3] * gzq;
+            if (V.g_quat) {
+                const float gq[4] = {(gw - F.qn[0] * dot) * F.qinv, (gx - F.qn[1] * dot) * F.qinv,
+                                     (gy - F.qn[2] * dot) * F.qinv, (gzq - F.qn[3] * dot) * F.qinv};
+                if (atomic) {
+                    for (int k = 0; k < 4; k++) atomicAdd(V.g_quat + 4 * (size_t)i + k, gq[k]);
+                } else {
+                    store_floats<4>(V.g_quat + 4 * (size_t)i, gq, aligned16(V.g_quat));
+                }
+            }
+            if (V.g_scale)
+                for (int k = 0; k < 3; k++) put(V.g_scale, 3 * (size_t)i + k, gsc[k], atomic);
+        }
+        // ---- p = W mu~ + T
+        {
+            const float *R = V.R;
+            for (int k = 0; k < 3; k++) gmut[k] += R[k] * gp[0] + R[3 + k] * gp[1] + R[6 + k] * gp[2];
+        }
+        // ---- time evaluation (Eq. 6 / Eq. 7)
+        {
+            const float3 vel = ld3(V.vel, i);
+            const float l = V.period[i], beta = V.beta[i];
+            const float gvd = gmut[0] * vel.x + gmut[1] * vel.y + gmut[2] * vel.z;
+            if (V.g_mu)
+                for (int k = 0; k < 3; k++) put(V.g_mu, 3 * (size_t)i + k, gmut[k], atomic);
+            if (V.g_vel)
+                for (int k = 0; k < 3; k++) put(V.g_vel, 3 * (size_t)i + k, gmut[k] * F.amp, atomic);
+            const float ib2 = 1.0f / (beta * beta);
+            if (V.g_tau) put(V.g_tau, i, -F.cs * gvd + got * F.ot * F.delta * ib2, atomic);
+            // flow shift dt v exp(-beta / (2 l)): its beta and l terms
+            const float gsh = gvd * V.dt * F.vbw;
+            if (V.g_period)
+                put(V.g_period, i, gvd * (F.sn * kInv2Pi - F.delta / l * F.cs) + gsh * (0.5f * beta / (l * l)), atomic);
+            if (V.g_opac) put(V.g_opac, i, got * F.egate, atomic);
+            if (V.g_beta) put(V.g_beta, i, got * F.ot * F.delta * F.delta * ib2 / beta - gsh * (0.5f / l), atomic);
+        }
+    }
+}
+
+}  // namespace
+
+void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s) {
+    note_launch();
+    switch (p.sh_degree) {
+        case 0: k_preprocess_bwd<0><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        case 1: k_preprocess_bwd<1><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        case 2: k_preprocess_bwd<2><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        default: k_preprocess_bwd<3><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+    }
+}
+
+}  // namespace pvg

@@ -141,6 +141,14 @@ __device__ __forceinline__ void record_terms(const float4 *rec, uint32_t m, floa
     s2 = make_float4(c.x, c.y, c.z, b.z);
 }
 
+// 1/x on the SFU (PTX rcp.approx.ftz.f32, within 1 ulp); the adjoints use it
+// to walk the transmittance back, where no decision depends on the result
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Gaussian falloff exponent in base-2 units for the record's prescaled
 // conic (a', b', c') = -log2(e) (a/2, b, c/2): the pixel weight is
 // 2^(a' dx^2 + b' dx dy + c' dy^2).  Written with explicit roundings so
@@ -197,7 +205,8 @@ __device__ __forceinline__ void sky_texels(const ViewDesc &V, int px, int py, si
 namespace pvg {
 // counts every kernel launch of the library (reported by pvg_kernel_launches)
 void note_launch();
-cudaError_t set_sh_constants();
+cudaError_t set_sh_constants();      // both copies of the SH constants
+cudaError_t set_sh_constants_bwd();  // the adjoint's copy
 void launch_project_count(const Params &p, cudaStream_t s);
 void launch_scatter_inv(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);
