@@ -374,6 +374,20 @@ pvg_status_t pvg_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, i
 pvg_status_t pvg_l1_loss(const float *pred, const float *target, int64_t n, float scale, float *dl,
                          float *loss, void *stream);
 
+/* Photometric loss of the objective (Sec. 3.4):
+ *   L = (1 - lambda_r) L1 + lambda_r (1 - SSIM)   (the paper uses 0.2),
+ * L1 = mean |pred - target|, SSIM the mean of the per-channel SSIM map of
+ * 3D Gaussian Splatting (11x11 Gaussian window, sigma 1.5, zero padding,
+ * C1 = 0.01^2, C2 = 0.03^2).  pred, target: device [channels, H, W]
+ * planar float32; loss: device float[3] receiving (L, L1, SSIM); dl: device
+ * [channels, H, W] receiving dL/dpred (sign(0) = 0), or NULL.  One fused
+ * pass plus a fixed-order reduction (deterministic).  Uses ctx's workspace
+ * (must not overlap other calls on ctx); capturable once the workspace has
+ * grown to the image size.  PVG_ERR_INVALID for NULL pointers, sizes
+ * outside 1..16384 (channels 1..65535) or lambda_r outside [0, 1]. */
+pvg_status_t pvg_rgb_loss(pvg_ctx_t *ctx, const float *pred, const float *target, int32_t channels,
+                          int32_t height, int32_t width, float lambda_r, float *dl, float *loss, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* measurement and introspection                                       */
 /* ------------------------------------------------------------------ */

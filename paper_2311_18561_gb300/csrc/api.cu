@@ -179,6 +179,7 @@ struct pvg_ctx {
     DevBuf chunk_start;          // [K / 2048 + 1]
     DevBuf temp;
     DevBuf sort_n;               // u32: element count of pvg_sort_pairs
+    DevBuf loss_partials;        // float2 per CTA of pvg_rgb_loss
     uint32_t *h_pinned = nullptr;
     pvg_frame *own_frame = nullptr;
     StageTimer timer;
@@ -287,7 +288,8 @@ extern "C" void pvg_destroy(pvg_ctx_t *x) {
     if (!x) return;
     cudaDeviceSynchronize();
     for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->alt_keys, &x->alt_vals, &x->pair_keys,
-                      &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n, &x->vis_off, &x->chunk_start})
+                      &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n, &x->vis_off, &x->chunk_start,
+                      &x->loss_partials})
         release(*b);
     if (x->h_pinned) cudaFreeHost(x->h_pinned);
     pvg_frame_destroy(x->own_frame);
@@ -768,6 +770,21 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     tm.end(PVG_STAGE_PREPROCESS_BWD, s);
     tm.on = timer_on;
     PVG_CUDA(cudaGetLastError());
+    return PVG_OK;
+}
+
+// ------------------------------------------------------------------ loss
+
+extern "C" pvg_status_t pvg_rgb_loss(pvg_ctx_t *x, const float *pred, const float *target, int32_t channels,
+                                     int32_t height, int32_t width, float lambda_r, float *dl, float *loss,
+                                     void *stream) {
+    if (!x || !pred || !target || !loss || channels < 1 || height < 1 || width < 1 || channels > 65535 ||
+        height > 16384 || width > 16384 || !(lambda_r >= 0.f && lambda_r <= 1.f))
+        return PVG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool capturing = is_capturing(s);
+    PVG_TRY(ensure_c(x->loss_partials, 2 * sizeof(float) * rgb_loss_partials(channels, height, width), capturing));
+    PVG_CUDA(launch_rgb_loss(pred, target, channels, height, width, lambda_r, dl, loss, x->loss_partials.p, s));
     return PVG_OK;
 }
 

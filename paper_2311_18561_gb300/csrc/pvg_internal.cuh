@@ -227,6 +227,10 @@ bool composite_supported(int tw, int th, int px);
 void launch_composite(const Params &p, cudaStream_t s);
 void launch_composite_stats(const Params &p, cudaStream_t s);
 void launch_composite_bwd(const Params &p, cudaStream_t s);
+// photometric loss (1 - lambda_r) L1 + lambda_r (1 - SSIM)
+size_t rgb_loss_partials(int channels, int height, int width);
+cudaError_t launch_rgb_loss(const float *pred, const float *target, int channels, int height, int width,
+                            float lambda_r, float *dl, float *loss, void *partials, cudaStream_t s);
 // extra channels
 int feat_count(int mask, int n_sem);
 void launch_composite_feat(const Params &p, cudaStream_t s);

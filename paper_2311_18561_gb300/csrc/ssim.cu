@@ -1,0 +1,229 @@
+// ssim.cu -- the photometric loss of the objective (Sec. 3.4),
+//   L = (1 - lambda_r) L1 + lambda_r (1 - SSIM),
+// and dL/dpred in one fused pass, so a training step with the paper's RGB
+// supervision needs no kernel outside this library.
+//
+// SSIM follows 3D Gaussian Splatting, whose losses the paper reuses: per
+// channel, an 11 x 11 Gaussian window (sigma 1.5, normalised) applied with
+// zero padding, C1 = 0.01^2, C2 = 0.03^2, averaged over channels and
+// pixels; L1 is the mean absolute difference (sign(0) = 0).
+//
+// One CTA per 32 x 32 output tile and channel.  The window is separable
+// and symmetric, so the gradient of SSIM is itself a windowed sum:
+//   dSSIM/dx_p = sum_q G(q - p) [a_q + 2 x_p b_q + y_p c_q],
+// a, b, c the derivatives of S_q with respect to the windowed moments
+// G*x, G*x^2, G*xy.  The CTA stages x and y with a 10-pixel halo in
+// shared memory, computes the five moments (row pass, then column pass) on
+// the tile plus a 5-pixel halo, turns them into S, a, b, c (zero outside
+// the image), filters a, b, c the same way and writes the gradient of its
+// 32 x 32 pixels.  HBM traffic is one read of both images and one write of
+// the gradient; the per-CTA sums of S and |x - y| go to a partial array
+// that one small kernel adds in a fixed order (the loss is deterministic).
+#include "pvg_internal.cuh"
+
+namespace pvg {
+namespace {
+
+constexpr int kT = 32;               // output tile
+constexpr int kR = 5;                // window radius
+constexpr int kA = kT + 2 * kR;      // S / a / b / c region (42)
+constexpr int kX = kT + 4 * kR;      // staged input region (52)
+constexpr int kThreads = 256;
+constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
+
+// shared layout, in floats
+constexpr int kOffX = 0, kOffY = kX * kX;
+constexpr int kOffH = 2 * kX * kX;                 // 5 row-filtered moments [5][kX][kA]
+constexpr int kOffABC = kOffH + 5 * kX * kA;       // [3][kA][kA]
+constexpr int kOffH2 = kOffH;                      // row-filtered a, b, c [3][kA][kT] (reuses the moments)
+constexpr int kOffG = kOffABC + 3 * kA * kA;       // 11 window taps
+constexpr int kOffRed = kOffG + 12;                // 2 x 8 warp partials
+constexpr int kSmemFloats = kOffRed + 16;
+
+__global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__ pred,
+                                                       const float *__restrict__ tgt, int H, int W,
+                                                       float lambda_r, float inv_n, float *__restrict__ dl,
+                                                       float2 *__restrict__ partial) {
+    extern __shared__ float sm[];
+    float *sx = sm + kOffX, *sy = sm + kOffY, *hm = sm + kOffH, *abc = sm + kOffABC, *h2 = sm + kOffH2;
+    float *g = sm + kOffG, *red = sm + kOffRed;
+    const int tid = threadIdx.x;
+    const size_t plane = (size_t)H * W;
+    const float *X = pred + blockIdx.z * plane, *Y = tgt + blockIdx.z * plane;
+    const int tx0 = blockIdx.x * kT, ty0 = blockIdx.y * kT;
+    if (tid < 11) {
+        float s = 0.f;
+        for (int j = 0; j < 11; j++) s += expf(-(float)((j - kR) * (j - kR)) / (2.0f * 1.5f * 1.5f));
+        g[tid] = expf(-(float)((tid - kR) * (tid - kR)) / (2.0f * 1.5f * 1.5f)) / s;
+    }
+    // inputs with a 2R halo, zero outside the image
+    for (int k = tid; k < kX * kX; k += kThreads) {
+        const int r = k / kX, c = k % kX, gy = ty0 - 2 * kR + r, gx = tx0 - 2 * kR + c;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        sx[k] = in ? X[(size_t)gy * W + gx] : 0.f;
+        sy[k] = in ? Y[(size_t)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    // row pass of the five moments over every staged row
+    for (int k = tid; k < kX * kA; k += kThreads) {
+        const int r = k / kA, c = k % kA;
+        const float *px = sx + r * kX + c, *py = sy + r * kX + c;
+        float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+#pragma unroll
+        for (int j = 0; j < 11; j++) {
+            const float a = px[j], b = py[j], w = g[j];
+            mx = fmaf(w, a, mx);
+            my = fmaf(w, b, my);
+            mxx = fmaf(w, a * a, mxx);
+            myy = fmaf(w, b * b, myy);
+            mxy = fmaf(w, a * b, mxy);
+        }
+        hm[0 * kX * kA + k] = mx;
+        hm[1 * kX * kA + k] = my;
+        hm[2 * kX * kA + k] = mxx;
+        hm[3 * kX * kA + k] = myy;
+        hm[4 * kX * kA + k] = mxy;
+    }
+    __syncthreads();
+    // column pass -> S and its moment derivatives a, b, c on the tile + R halo
+    float ssum = 0.f, l1sum = 0.f;
+    for (int k = tid; k < kA * kA; k += kThreads) {
+        const int r = k / kA, c = k % kA, gy = ty0 - kR + r, gx = tx0 - kR + c;
+        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 11; i++) {
+            const float w = g[i];
+#pragma unroll
+            for (int q = 0; q < 5; q++) m[q] = fmaf(w, hm[q * kX * kA + (r + i) * kA + c], m[q]);
+        }
+        float a = 0.f, b = 0.f, cc = 0.f;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const float mx = m[0], my = m[1];
+            const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+            const float S = (A1 * A2) / (B1 * B2);
+            const float dmu = S * (2.f * my / A1 - 2.f * mx / B1);
+            const float dvx = -S / B2, dcxy = 2.f * S / A2;
+            a = dmu - 2.f * mx * dvx - my * dcxy;
+            b = dvx;
+            cc = dcxy;
+            if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {
+                ssum += S;
+                const int s_idx = (r + kR) * kX + (c + kR);
+                l1sum += fabsf(sx[s_idx] - sy[s_idx]);
+            }
+        }
+        abc[0 * kA * kA + k] = a;
+        abc[1 * kA * kA + k] = b;
+        abc[2 * kA * kA + k] = cc;
+    }
+    __syncthreads();
+    // row pass of a, b, c (into the moments' space, no longer needed)
+    for (int k = tid; k < kA * kT; k += kThreads) {
+        const int r = k / kT, c = k % kT;
+        float q[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 11; j++) {
+            const float w = g[j];
+#pragma unroll
+            for (int t = 0; t < 3; t++) q[t] = fmaf(w, abc[t * kA * kA + r * kA + c + j], q[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; t++) h2[t * kA * kT + k] = q[t];
+    }
+    __syncthreads();
+    // column pass and the gradient of the tile's pixels
+    if (dl) {
+        const float kl1 = (1.0f - lambda_r) * inv_n, kss = lambda_r * inv_n;
+        float *D = dl + blockIdx.z * plane;
+        for (int k = tid; k < kT * kT; k += kThreads) {
+            const int r = k / kT, c = k % kT, gy = ty0 + r, gx = tx0 + c;
+            if (gx >= W || gy >= H) continue;
+            float q[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 11; i++) {
+                const float w = g[i];
+#pragma unroll
+                for (int t = 0; t < 3; t++) q[t] = fmaf(w, h2[t * kA * kT + (r + i) * kT + c], q[t]);
+            }
+            const int s_idx = (r + 2 * kR) * kX + (c + 2 * kR);
+            const float x = sx[s_idx], y = sy[s_idx], d = x - y;
+            const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+            const float dssim = q[0] + 2.f * x * q[1] + y * q[2];
+            D[(size_t)gy * W + gx] = kl1 * sgn - kss * dssim;
+        }
+    }
+    // per-CTA sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+        l1sum += __shfl_xor_sync(0xffffffffu, l1sum, o);
+    }
+    if ((tid & 31) == 0) {
+        red[tid >> 5] = ssum;
+        red[8 + (tid >> 5)] = l1sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < kThreads / 32; w++) {
+            a += red[w];
+            b += red[8 + w];
+        }
+        partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = make_float2(a, b);
+    }
+}
+
+// loss[0..2] = (L, L1, SSIM) from the per-CTA partial sums, added in a
+// fixed order in double precision
+__global__ void __launch_bounds__(1024) k_rgb_loss_finish(const float2 *__restrict__ partial, int n,
+                                                          double inv_n, float lambda_r, float *loss) {
+    __shared__ double ss[1024], sl[1024];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += (double)partial[i].x;
+        b += (double)partial[i].y;
+    }
+    ss[threadIdx.x] = a;
+    sl[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            ss[threadIdx.x] += ss[threadIdx.x + s];
+            sl[threadIdx.x] += sl[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double ssim = ss[0] * inv_n, l1 = sl[0] * inv_n;
+        loss[0] = (float)((1.0 - lambda_r) * l1 + lambda_r * (1.0 - ssim));
+        loss[1] = (float)l1;
+        loss[2] = (float)ssim;
+    }
+}
+
+}  // namespace
+
+size_t rgb_loss_partials(int channels, int height, int width) {
+    return (size_t)channels * ((height + kT - 1) / kT) * ((width + kT - 1) / kT);
+}
+
+cudaError_t launch_rgb_loss(const float *pred, const float *target, int channels, int height, int width,
+                            float lambda_r, float *dl, float *loss, void *partials, cudaStream_t s) {
+    const size_t smem = sizeof(float) * kSmemFloats;
+    static_assert(sizeof(float) * kSmemFloats <= 227 * 1024, "shared memory of the loss kernel");
+    cudaError_t e = cudaFuncSetAttribute(k_rgb_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((width + kT - 1) / kT, (height + kT - 1) / kT, channels);
+    const double n = (double)channels * height * width;
+    note_launch();
+    k_rgb_loss<<<grid, kThreads, smem, s>>>(pred, target, height, width, lambda_r, (float)(1.0 / n), dl,
+                                            reinterpret_cast<float2 *>(partials));
+    note_launch();
+    k_rgb_loss_finish<<<1, 1024, 0, s>>>(reinterpret_cast<const float2 *>(partials),
+                                         (int)rgb_loss_partials(channels, height, width), 1.0 / n, lambda_r, loss);
+    return cudaGetLastError();
+}
+
+}  // namespace pvg

@@ -299,6 +299,23 @@ def l1_loss(pred, target, dl=None, loss=None, scale=None, stream=None):
     return loss, dl
 
 
+def rgb_loss(renderer, pred, target, lambda_r=0.2, dl=None, loss=None, stream=None):
+    """(1 - lambda_r) L1 + lambda_r (1 - SSIM) of planar [C, H, W] images
+    (``pvg_rgb_loss``); returns (loss [3] = (L, L1, SSIM), dL/dpred)."""
+    if (pred.shape != target.shape or pred.dim() != 3 or not pred.is_contiguous() or not target.is_contiguous()
+            or pred.dtype != torch.float32 or target.dtype != torch.float32):
+        raise ValueError("pred and target must be contiguous float32 tensors [C, H, W] of one shape")
+    if dl is None:
+        dl = torch.empty_like(pred)
+    if loss is None:
+        loss = torch.empty(3, device=pred.device, dtype=torch.float32)
+    C_, H, W = pred.shape
+    st = abi.lib().pvg_rgb_loss(renderer.handle, pred.data_ptr(), target.data_ptr(), int(C_), int(H), int(W),
+                               float(lambda_r), dl.data_ptr(), loss.data_ptr(), _stream_ptr(stream))
+    abi.check(st, "pvg_rgb_loss")
+    return loss, dl
+
+
 def kernel_launches() -> int:
     return int(abi.lib().pvg_kernel_launches())
 
