@@ -67,8 +67,9 @@ SM_MAX_MHZ = 2070.0
 # 1 - alpha, T (1 - alpha), alpha T, 4 FFMA (r g b z), O += w = 8;
 # backward: 1 - alpha, T / (1 - alpha), alpha T_i, dL/dalpha (13), 4 FFMA
 # (r g b z terms), o~ term, 5 moments (8), 5 suffix sums = 35.
+OPS_PER_LOSS_PIXEL = 207
 OPS_PER_EVAL = 8
-OPS_PER_BLEND = {"composite": 8, "composite_bwd": 35}
+OPS_PER_BLEND = {"composite": 8, "composite_bwd": 23}
 
 
 def parse_args():
@@ -289,6 +290,53 @@ def run_ours(args):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_s = float(te[0])
 
+    # ---- the same step with the paper's photometric loss (1 - 0.2) L1 + 0.2 (1 - SSIM)
+    def step_paper_loss():
+        r.forward(st, [cam], outs=outs, frame=fr)
+        R.rgb_loss(r, outs[0]["rgb"], target, lambda_r=0.2, dl=dl, loss=loss3)
+        r.backward(st, [cam], fr, [dict(rgb=dl)], grads=grads)
+
+    loss3 = torch.empty(3, device=dev)
+    for _ in range(3):
+        step_paper_loss()
+    paper_step_ms = timed(step_paper_loss, args.steps) / args.steps
+    loss_ms = timed(lambda: R.rgb_loss(r, outs[0]["rgb"], target, lambda_r=0.2, dl=dl, loss=loss3),
+                    args.steps) / args.steps
+    # separable filtering: 5 moments and 3 derivative maps x 2 passes x 11 taps,
+    # 3 products, ~20 for S and its derivatives, 5 for the gradient, 3 for L1
+    loss_ops = 3 * W_PIX * H_PIX * OPS_PER_LOSS_PIXEL
+    alu_peak = SM_COUNT * 128 * peaks()["sm_max_mhz"] * 1e6
+    paper_loss = {"step_ms": paper_step_ms, "loss_ms": loss_ms,
+                  "roofline_loss": {"kernel": "k_rgb_loss", "bound": "alu",
+                                    "achieved": loss_ops / (loss_ms * 1e-3) / 1e12, "peak": alu_peak / 1e12,
+                                    "unit": "T FP32-lane-instr/s",
+                                    "frac": loss_ops / (loss_ms * 1e-3) / alu_peak,
+                                    "work": "%d FP32 instructions per pixel and channel" % OPS_PER_LOSS_PIXEL,
+                                    "hbm_bytes": 3 * W_PIX * H_PIX * 12,
+                                    "note": "includes the fixed-order reduction kernel"}}
+
+    # ---- the same step rendering and differentiating the extra channels:
+    # velocity (3), staticness (1) and 19 semantic classes
+    from paper_2311_18561_gb300 import abi as A
+    st_f = dict(st)
+    st_f["sem"] = torch.tensor(synth.make_semantics(N_GAUSS, 19, seed=5), device=dev)
+    fmask = A.FEAT_VBAR | A.FEAT_RHO | A.FEAT_SEM
+    outs_f = r.alloc_images([cam], features=fmask, n_sem=19)
+    dl_feat = torch.randn(23, H_PIX, W_PIX, device=dev) * 1e-6
+    grads_f = dict(grads)
+    grads_f["sem"] = torch.empty_like(st_f["sem"])
+
+    def step_features():
+        r.forward(st_f, [cam], outs=outs_f, frame=fr, features=fmask)
+        R.l1_loss(outs_f[0]["rgb"], target, dl=dl, loss=loss)
+        r.backward(st_f, [cam], fr, [dict(rgb=dl, feat=dl_feat)], grads=grads_f)
+
+    for _ in range(3):
+        step_features()
+    features = {"channels": "v_bar (3) + rho (1) + 19 semantic classes",
+                "step_ms": timed(step_features, args.steps) / args.steps}
+    del st_f, outs_f, dl_feat, grads_f
+
     # ---- roofline of the dominant stage
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
     dominant = max(stage_ms, key=stage_ms.get)
@@ -342,6 +390,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "paper_loss_step": paper_loss,
+        "features_step": features,
     }
     if not args.no_serve:
         del st, grads, flush

@@ -28,7 +28,7 @@ constexpr int kT = 32;               // output tile
 constexpr int kR = 5;                // window radius
 constexpr int kA = kT + 2 * kR;      // S / a / b / c region (42)
 constexpr int kX = kT + 4 * kR;      // staged input region (52)
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;  // one round of the largest pass (364 strips)
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
 // shared layout, in floats
@@ -37,8 +37,8 @@ constexpr int kOffH = 2 * kX * kX;                 // 5 row-filtered moments [5]
 constexpr int kOffABC = kOffH + 5 * kX * kA;       // [3][kA][kA]
 constexpr int kOffH2 = kOffH;                      // row-filtered a, b, c [3][kA][kT] (reuses the moments)
 constexpr int kOffG = kOffABC + 3 * kA * kA;       // 11 window taps
-constexpr int kOffRed = kOffG + 12;                // 2 x 8 warp partials
-constexpr int kSmemFloats = kOffRed + 16;
+constexpr int kOffRed = kOffG + 12;                // 2 x 16 warp partials
+constexpr int kSmemFloats = kOffRed + 32;
 
 __global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__ pred,
                                                        const float *__restrict__ tgt, int H, int W,
@@ -64,94 +64,144 @@ __global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__
         sy[k] = in ? Y[(size_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    // row pass of the five moments over every staged row
-    for (int k = tid; k < kX * kA; k += kThreads) {
-        const int r = k / kA, c = k % kA;
-        const float *px = sx + r * kX + c, *py = sy + r * kX + c;
-        float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+    float gw[11];  // the taps, in registers
 #pragma unroll
-        for (int j = 0; j < 11; j++) {
-            const float a = px[j], b = py[j], w = g[j];
-            mx = fmaf(w, a, mx);
-            my = fmaf(w, b, my);
-            mxx = fmaf(w, a * a, mxx);
-            myy = fmaf(w, b * b, myy);
-            mxy = fmaf(w, a * b, mxy);
+    for (int j = 0; j < 11; j++) gw[j] = g[j];
+    // Each pass is register-blocked: a thread filters a strip of outputs
+    // along the pass direction from one run of staged values, so a value is
+    // read from shared memory once per strip instead of once per tap.
+    //
+    // row pass of the five moments: every staged row, strips of 6 columns
+    // of the 42-wide S region (7 per row)
+    for (int k = tid; k < kX * 7; k += kThreads) {
+        const int r = k / 7, c0 = (k % 7) * 6;
+        float xa[16], ya[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            xa[j] = sx[r * kX + c0 + j];
+            ya[j] = sy[r * kX + c0 + j];
         }
-        hm[0 * kX * kA + k] = mx;
-        hm[1 * kX * kA + k] = my;
-        hm[2 * kX * kA + k] = mxx;
-        hm[3 * kX * kA + k] = myy;
-        hm[4 * kX * kA + k] = mxy;
+        float m[5][6];
+#pragma unroll
+        for (int o = 0; o < 6; o++) {
+            float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+#pragma unroll
+            for (int j = 0; j < 11; j++) {
+                const float a = xa[o + j], b = ya[o + j], w = gw[j];
+                mx = fmaf(w, a, mx);
+                my = fmaf(w, b, my);
+                mxx = fmaf(w, a * a, mxx);
+                myy = fmaf(w, b * b, myy);
+                mxy = fmaf(w, a * b, mxy);
+            }
+            m[0][o] = mx; m[1][o] = my; m[2][o] = mxx; m[3][o] = myy; m[4][o] = mxy;
+        }
+#pragma unroll
+        for (int q = 0; q < 5; q++)
+#pragma unroll
+            for (int o = 0; o < 6; o++) hm[q * kX * kA + r * kA + c0 + o] = m[q][o];
     }
     __syncthreads();
-    // column pass -> S and its moment derivatives a, b, c on the tile + R halo
+    // column pass -> S and its moment derivatives a, b, c on the tile + R
+    // halo: every column, strips of 6 rows (7 per column)
     float ssum = 0.f, l1sum = 0.f;
-    for (int k = tid; k < kA * kA; k += kThreads) {
-        const int r = k / kA, c = k % kA, gy = ty0 - kR + r, gx = tx0 - kR + c;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = tid; k < kA * 7; k += kThreads) {
+        const int c = k % kA, r0 = (k / kA) * 6;
+        float m[5][6];
 #pragma unroll
-        for (int i = 0; i < 11; i++) {
-            const float w = g[i];
+        for (int q = 0; q < 5; q++) {
+            float v[16];
 #pragma unroll
-            for (int q = 0; q < 5; q++) m[q] = fmaf(w, hm[q * kX * kA + (r + i) * kA + c], m[q]);
-        }
-        float a = 0.f, b = 0.f, cc = 0.f;
-        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-            const float mx = m[0], my = m[1];
-            const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
-            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-            const float S = (A1 * A2) / (B1 * B2);
-            const float dmu = S * (2.f * my / A1 - 2.f * mx / B1);
-            const float dvx = -S / B2, dcxy = 2.f * S / A2;
-            a = dmu - 2.f * mx * dvx - my * dcxy;
-            b = dvx;
-            cc = dcxy;
-            if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {
-                ssum += S;
-                const int s_idx = (r + kR) * kX + (c + kR);
-                l1sum += fabsf(sx[s_idx] - sy[s_idx]);
+            for (int i = 0; i < 16; i++) v[i] = hm[q * kX * kA + (r0 + i) * kA + c];
+#pragma unroll
+            for (int o = 0; o < 6; o++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < 11; i++) acc = fmaf(gw[i], v[o + i], acc);
+                m[q][o] = acc;
             }
         }
-        abc[0 * kA * kA + k] = a;
-        abc[1 * kA * kA + k] = b;
-        abc[2 * kA * kA + k] = cc;
-    }
-    __syncthreads();
-    // row pass of a, b, c (into the moments' space, no longer needed)
-    for (int k = tid; k < kA * kT; k += kThreads) {
-        const int r = k / kT, c = k % kT;
-        float q[3] = {0.f, 0.f, 0.f};
+        const int gx = tx0 - kR + c;
 #pragma unroll
-        for (int j = 0; j < 11; j++) {
-            const float w = g[j];
-#pragma unroll
-            for (int t = 0; t < 3; t++) q[t] = fmaf(w, abc[t * kA * kA + r * kA + c + j], q[t]);
+        for (int o = 0; o < 6; o++) {
+            const int r = r0 + o, gy = ty0 - kR + r;
+            float a = 0.f, b = 0.f, cc = 0.f;
+            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+                const float mx = m[0][o], my = m[1][o];
+                const float vx = fmaf(-mx, mx, m[2][o]), vy = fmaf(-my, my, m[3][o]);
+                const float cxy = fmaf(-mx, my, m[4][o]);
+                const float A1 = fmaf(2.f * mx, my, kC1), A2 = fmaf(2.f, cxy, kC2);
+                const float B1 = fmaf(mx, mx, fmaf(my, my, kC1)), B2 = vx + vy + kC2;
+                // SFU reciprocals (within 2 ulp)
+                const float iA1 = __fdividef(1.f, A1), iA2 = __fdividef(1.f, A2);
+                const float iB1 = __fdividef(1.f, B1), iB2 = __fdividef(1.f, B2);
+                const float S = A1 * A2 * iB1 * iB2;
+                const float dmu = 2.f * S * fmaf(my, iA1, -mx * iB1);
+                const float dvx = -S * iB2, dcxy = 2.f * S * iA2;
+                a = fmaf(-2.f * mx, dvx, fmaf(-my, dcxy, dmu));
+                b = dvx;
+                cc = dcxy;
+                if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {
+                    ssum += S;
+                    const int s_idx = (r + kR) * kX + (c + kR);
+                    l1sum += fabsf(sx[s_idx] - sy[s_idx]);
+                }
+            }
+            abc[0 * kA * kA + r * kA + c] = a;
+            abc[1 * kA * kA + r * kA + c] = b;
+            abc[2 * kA * kA + r * kA + c] = cc;
         }
-#pragma unroll
-        for (int t = 0; t < 3; t++) h2[t * kA * kT + k] = q[t];
     }
     __syncthreads();
-    // column pass and the gradient of the tile's pixels
+    // row pass of a, b, c (into the moments' space, no longer needed):
+    // every row of the S region, strips of 8 of the 32 tile columns
+    for (int k = tid; k < kA * 4; k += kThreads) {
+        const int r = k / 4, c0 = (k % 4) * 8;
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            float v[18];
+#pragma unroll
+            for (int j = 0; j < 18; j++) v[j] = abc[t * kA * kA + r * kA + c0 + j];
+#pragma unroll
+            for (int o = 0; o < 8; o++) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < 11; j++) acc = fmaf(gw[j], v[o + j], acc);
+                h2[t * kA * kT + r * kT + c0 + o] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // column pass and the gradient of the tile's pixels: strips of 4 rows
     if (dl) {
         const float kl1 = (1.0f - lambda_r) * inv_n, kss = lambda_r * inv_n;
         float *D = dl + blockIdx.z * plane;
-        for (int k = tid; k < kT * kT; k += kThreads) {
-            const int r = k / kT, c = k % kT, gy = ty0 + r, gx = tx0 + c;
-            if (gx >= W || gy >= H) continue;
-            float q[3] = {0.f, 0.f, 0.f};
+        for (int k = tid; k < kT * 8; k += kThreads) {
+            const int c = k % kT, r0 = (k / kT) * 4, gx = tx0 + c;
+            float q[3][4];
 #pragma unroll
-            for (int i = 0; i < 11; i++) {
-                const float w = g[i];
+            for (int t = 0; t < 3; t++) {
+                float v[14];
 #pragma unroll
-                for (int t = 0; t < 3; t++) q[t] = fmaf(w, h2[t * kA * kT + (r + i) * kT + c], q[t]);
+                for (int i = 0; i < 14; i++) v[i] = h2[t * kA * kT + (r0 + i) * kT + c];
+#pragma unroll
+                for (int o = 0; o < 4; o++) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 11; i++) acc = fmaf(gw[i], v[o + i], acc);
+                    q[t][o] = acc;
+                }
             }
-            const int s_idx = (r + 2 * kR) * kX + (c + 2 * kR);
-            const float x = sx[s_idx], y = sy[s_idx], d = x - y;
-            const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            const float dssim = q[0] + 2.f * x * q[1] + y * q[2];
-            D[(size_t)gy * W + gx] = kl1 * sgn - kss * dssim;
+#pragma unroll
+            for (int o = 0; o < 4; o++) {
+                const int r = r0 + o, gy = ty0 + r;
+                if (gx >= W || gy >= H) continue;
+                const int s_idx = (r + 2 * kR) * kX + (c + 2 * kR);
+                const float x = sx[s_idx], y = sy[s_idx], d = x - y;
+                const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                const float dssim = q[0][o] + 2.f * x * q[1][o] + y * q[2][o];
+                D[(size_t)gy * W + gx] = kl1 * sgn - kss * dssim;
+            }
         }
     }
     // per-CTA sums
@@ -162,14 +212,14 @@ __global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__
     }
     if ((tid & 31) == 0) {
         red[tid >> 5] = ssum;
-        red[8 + (tid >> 5)] = l1sum;
+        red[16 + (tid >> 5)] = l1sum;
     }
     __syncthreads();
     if (tid == 0) {
         float a = 0.f, b = 0.f;
         for (int w = 0; w < kThreads / 32; w++) {
             a += red[w];
-            b += red[8 + w];
+            b += red[16 + w];
         }
         partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = make_float2(a, b);
     }
