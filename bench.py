@@ -84,6 +84,8 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving leg (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="duration of the serving leg")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the paper-loss and extra-channel legs (timed after the headline step)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall-clock budget of the oracle's bounded sample")
     return ap.parse_args()
@@ -159,24 +161,30 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash():
+# the sources that decide the compositor kernels' memory traffic
+COMPOSITOR_SOURCES = ("pvg_internal.cuh", "raster_common.cuh", "raster.cu", "raster_bwd.cu")
+
+
+def kernel_source_hash(files=COMPOSITOR_SOURCES):
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2311_18561_gb300", "csrc"))):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2311_18561_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current kernel sources (else None)."""
+def ncu_traffic(kernel, config):
+    """DRAM bytes (read + write) per launch of `kernel` in compositing
+    configuration `config` ("16x32x4") on the urban workload, from the
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("source_hash") != kernel_source_hash():
             return None
-        return d["kernels"][kernel]["dram_bytes_per_launch"]
+        return d["kernels"][kernel][config]
     except Exception:
         return None
 
@@ -297,45 +305,47 @@ def run_ours(args):
         r.backward(st, [cam], fr, [dict(rgb=dl)], grads=grads)
 
     loss3 = torch.empty(3, device=dev)
-    for _ in range(3):
+    paper_loss = features = None
+    for _ in range(0 if args.no_legs else 3):
         step_paper_loss()
-    paper_step_ms = timed(step_paper_loss, args.steps) / args.steps
-    loss_ms = timed(lambda: R.rgb_loss(r, outs[0]["rgb"], target, lambda_r=0.2, dl=dl, loss=loss3),
-                    args.steps) / args.steps
-    # separable filtering: 5 moments and 3 derivative maps x 2 passes x 11 taps,
-    # 3 products, ~20 for S and its derivatives, 5 for the gradient, 3 for L1
-    loss_ops = 3 * W_PIX * H_PIX * OPS_PER_LOSS_PIXEL
-    alu_peak = SM_COUNT * 128 * peaks()["sm_max_mhz"] * 1e6
-    paper_loss = {"step_ms": paper_step_ms, "loss_ms": loss_ms,
-                  "roofline_loss": {"kernel": "k_rgb_loss", "bound": "alu",
-                                    "achieved": loss_ops / (loss_ms * 1e-3) / 1e12, "peak": alu_peak / 1e12,
-                                    "unit": "T FP32-lane-instr/s",
-                                    "frac": loss_ops / (loss_ms * 1e-3) / alu_peak,
-                                    "work": "%d FP32 instructions per pixel and channel" % OPS_PER_LOSS_PIXEL,
-                                    "hbm_bytes": 3 * W_PIX * H_PIX * 12,
-                                    "note": "includes the fixed-order reduction kernel"}}
+    if not args.no_legs:
+        paper_step_ms = timed(step_paper_loss, args.steps) / args.steps
+        loss_ms = timed(lambda: R.rgb_loss(r, outs[0]["rgb"], target, lambda_r=0.2, dl=dl, loss=loss3),
+                        args.steps) / args.steps
+        # separable filtering: 5 moments and 3 derivative maps x 2 passes x 11 taps,
+        # 3 products, ~20 for S and its derivatives, 5 for the gradient, 3 for L1
+        loss_ops = 3 * W_PIX * H_PIX * OPS_PER_LOSS_PIXEL
+        alu_peak = SM_COUNT * 128 * peaks()["sm_max_mhz"] * 1e6
+        paper_loss = {"step_ms": paper_step_ms, "loss_ms": loss_ms,
+                      "roofline_loss": {"kernel": "k_rgb_loss", "bound": "alu",
+                                        "achieved": loss_ops / (loss_ms * 1e-3) / 1e12, "peak": alu_peak / 1e12,
+                                        "unit": "T FP32-lane-instr/s",
+                                        "frac": loss_ops / (loss_ms * 1e-3) / alu_peak,
+                                        "work": "%d FP32 instructions per pixel and channel" % OPS_PER_LOSS_PIXEL,
+                                        "hbm_bytes": 3 * W_PIX * H_PIX * 12,
+                                        "note": "includes the fixed-order reduction kernel"}}
 
-    # ---- the same step rendering and differentiating the extra channels:
-    # velocity (3), staticness (1) and 19 semantic classes
-    from paper_2311_18561_gb300 import abi as A
-    st_f = dict(st)
-    st_f["sem"] = torch.tensor(synth.make_semantics(N_GAUSS, 19, seed=5), device=dev)
-    fmask = A.FEAT_VBAR | A.FEAT_RHO | A.FEAT_SEM
-    outs_f = r.alloc_images([cam], features=fmask, n_sem=19)
-    dl_feat = torch.randn(23, H_PIX, W_PIX, device=dev) * 1e-6
-    grads_f = dict(grads)
-    grads_f["sem"] = torch.empty_like(st_f["sem"])
+        # ---- the same step rendering and differentiating the extra channels:
+        # velocity (3), staticness (1) and 19 semantic classes
+        from paper_2311_18561_gb300 import abi as A
+        st_f = dict(st)
+        st_f["sem"] = torch.tensor(synth.make_semantics(N_GAUSS, 19, seed=5), device=dev)
+        fmask = A.FEAT_VBAR | A.FEAT_RHO | A.FEAT_SEM
+        outs_f = r.alloc_images([cam], features=fmask, n_sem=19)
+        dl_feat = torch.randn(23, H_PIX, W_PIX, device=dev) * 1e-6
+        grads_f = dict(grads)
+        grads_f["sem"] = torch.empty_like(st_f["sem"])
 
-    def step_features():
-        r.forward(st_f, [cam], outs=outs_f, frame=fr, features=fmask)
-        R.l1_loss(outs_f[0]["rgb"], target, dl=dl, loss=loss)
-        r.backward(st_f, [cam], fr, [dict(rgb=dl, feat=dl_feat)], grads=grads_f)
+        def step_features():
+            r.forward(st_f, [cam], outs=outs_f, frame=fr, features=fmask)
+            R.l1_loss(outs_f[0]["rgb"], target, dl=dl, loss=loss)
+            r.backward(st_f, [cam], fr, [dict(rgb=dl, feat=dl_feat)], grads=grads_f)
 
-    for _ in range(3):
-        step_features()
-    features = {"channels": "v_bar (3) + rho (1) + 19 semantic classes",
-                "step_ms": timed(step_features, args.steps) / args.steps}
-    del st_f, outs_f, dl_feat, grads_f
+        for _ in range(3):
+            step_features()
+        features = {"channels": "v_bar (3) + rho (1) + 19 semantic classes",
+                    "step_ms": timed(step_features, args.steps) / args.steps}
+        del st_f, outs_f, dl_feat, grads_f
 
     # ---- roofline of the dominant stage
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
@@ -349,7 +359,8 @@ def run_ours(args):
         ach = ops / (stage_ms[stage] * 1e-3)
         kern = "k_composite" if stage == "composite" else "k_composite_bwd"
         return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak / 1e12,
-                "unit": "T FP32-lane-instr/s", "frac": ach / alu_peak, "traffic": ncu_traffic(kern),
+                "unit": "T FP32-lane-instr/s", "frac": ach / alu_peak,
+                "traffic": ncu_traffic(kern, "%dx%dx%d" % best) if args.workload == "urban" else None,
                 "work": "E=%d in-footprint evaluations x %d + %d blended x %d FP32 instructions"
                         % (E, OPS_PER_EVAL, B, OPS_PER_BLEND[stage]),
                 "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (derived)" % pk["sm_max_mhz"]}
@@ -364,7 +375,7 @@ def run_ours(args):
         b = algo.get(dominant, 0)
         ach = b / (stage_ms[dominant] * 1e-3) / 1e9
         roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic(dominant)}
+                "frac": ach / pk["hbm_gbs"], "traffic": None}
     roof["peak_kind"] = pk["source"]
 
     out = {
