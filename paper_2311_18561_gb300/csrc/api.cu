@@ -153,7 +153,7 @@ struct pvg_frame {
     DevBuf tile_order;          // [tiles] compositor launch order
     DevBuf pix_T, pix_last;     // [pixels]
     DevBuf pix_neval;           // [pixels]
-    DevBuf g2d;                 // [NV * 10]
+    DevBuf g2d;                 // [NV * 10] image-space gradients by depth position
     DevBuf gfeat;               // [NV * F] dL/d(channel value)
     std::vector<ViewDesc> views;
     int feat_mask = 0, n_feat = 0, n_sem = 0;  // extra channels of the forward

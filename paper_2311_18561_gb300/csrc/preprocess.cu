@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_scatter_inv(Params P) {
 // Records in depth order, computed in item order (coalesced parameter
 // reads; the 48-byte record goes to its depth position m = inv[g]).
 template <int D>
-__global__ void __launch_bounds__(256) k_finalize(Params P) {
+__global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
     constexpr int K = (D + 1) * (D + 1);
     const uint32_t n = P.n_items;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {

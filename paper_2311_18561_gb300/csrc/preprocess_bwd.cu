@@ -44,6 +44,73 @@ __device__ __forceinline__ void zero_grads(const ViewDesc &V, uint32_t i) {
     }
 }
 
+// dL/dsh[k][c] = gcol[c] Y_k(d), written (or accumulated) in groups of four
+// basis functions (three float4) when the rows allow it
+template <int D>
+__device__ __forceinline__ void sh_coef_adjoint(float x, float y, float z, const float (&gcol)[3], float *gsh,
+                                                bool vec, bool atomic) {
+    constexpr int K = (D + 1) * (D + 1);
+    float Y[16], dY[16][3];
+    sh_eval<D, false>(x, y, z, Y, dY);
+    if constexpr (K % 4 == 0) {
+        if (vec && !atomic) {
+            float4 *g4 = reinterpret_cast<float4 *>(gsh);
+#pragma unroll
+            for (int q = 0; q < K / 4; q++) {
+                float g[12];
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) g[3 * j + c] = gcol[c] * Y[4 * q + j];
+                g4[3 * q] = make_float4(g[0], g[1], g[2], g[3]);
+                g4[3 * q + 1] = make_float4(g[4], g[5], g[6], g[7]);
+                g4[3 * q + 2] = make_float4(g[8], g[9], g[10], g[11]);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) put(gsh, 3 * (size_t)k + c, gcol[c] * Y[k], atomic);
+}
+
+// dL/ddir = sum_k (gcol . sh_k) dY_k(d), reading the coefficients in
+// groups of four basis functions (three float4) when the rows allow it
+template <int D>
+__device__ __forceinline__ void sh_dir_adjoint(float x, float y, float z, const float (&gcol)[3], const float *sh,
+                                               bool vec, float (&gd)[3]) {
+    constexpr int K = (D + 1) * (D + 1);
+    float Y[16], dY[16][3];
+    sh_eval<D, true>(x, y, z, Y, dY);
+    gd[0] = gd[1] = gd[2] = 0.f;
+    if constexpr (K % 4 == 0) {
+        if (vec) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(sh);
+#pragma unroll
+            for (int q = 0; q < K / 4; q++) {
+                const float4 a = s4[3 * q], b = s4[3 * q + 1], c = s4[3 * q + 2];
+                const float s[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float w = gcol[0] * s[3 * j] + gcol[1] * s[3 * j + 1] + gcol[2] * s[3 * j + 2];
+                    gd[0] += w * dY[4 * q + j][0];
+                    gd[1] += w * dY[4 * q + j][1];
+                    gd[2] += w * dY[4 * q + j][2];
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const float w = gcol[0] * sh[3 * k] + gcol[1] * sh[3 * k + 1] + gcol[2] * sh[3 * k + 2];
+        gd[0] += w * dY[k][0];
+        gd[1] += w * dY[k][1];
+        gd[2] += w * dY[k][2];
+    }
+}
+
 // Adjoint of the projection and colour, in item order: item g reads the
 // image-space gradients of its depth position m = inv[g].  With `atomic`
 // (several views share the gradients) the gradients were zeroed before and
@@ -68,53 +135,6 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
         const float got = G2[5], gz = G2[9];
         float gmut[3] = {0.f, 0.f, 0.f};
         float gp[3] = {0.f, 0.f, 0.f};
-
-        // ---- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5)
-        {
-            float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
-            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float inv = 1.0f / dist;
-            dx *= inv; dy *= inv; dz *= inv;
-            float Y[16], dY[16][3];
-            sh_eval<D, true>(dx, dy, dz, Y, dY);
-            float sh[3 * K];
-            load_floats<3 * K>(V.sh + (size_t)i * K * 3, sh, aligned16(V.sh));
-            float raw[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-            for (int k = 0; k < K; k++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) raw[c] += sh[3 * k + c] * Y[k];
-            float gcol[3];
-#pragma unroll
-            for (int c = 0; c < 3; c++) gcol[c] = raw[c] > 0.0f ? G2[6 + c] : 0.0f;
-            float gd[3] = {0.f, 0.f, 0.f};
-            if (V.g_sh) {
-                if (atomic) {
-#pragma unroll
-                    for (int k = 0; k < K; k++)
-#pragma unroll
-                        for (int c = 0; c < 3; c++) atomicAdd(V.g_sh + ((size_t)i * K + k) * 3 + c, gcol[c] * Y[k]);
-                } else {
-                    float gsh[3 * K];
-#pragma unroll
-                    for (int k = 0; k < K; k++)
-#pragma unroll
-                        for (int c = 0; c < 3; c++) gsh[3 * k + c] = gcol[c] * Y[k];
-                    store_floats<3 * K>(V.g_sh + (size_t)i * K * 3, gsh, aligned16(V.g_sh));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < K; k++) {
-                const float w = gcol[0] * sh[3 * k] + gcol[1] * sh[3 * k + 1] + gcol[2] * sh[3 * k + 2];
-                gd[0] += w * dY[k][0];
-                gd[1] += w * dY[k][1];
-                gd[2] += w * dY[k][2];
-            }
-            const float dot = dx * gd[0] + dy * gd[1] + dz * gd[2];
-            gmut[0] += (gd[0] - dx * dot) * inv;
-            gmut[1] += (gd[1] - dy * dot) * inv;
-            gmut[2] += (gd[2] - dz * dot) * inv;
-        }
 
         // ---- conic = inverse(cov2): dL/dcov2 = -Q Ghat Q
         const float a = F.ca, b = F.cb, c = F.cc;
@@ -209,6 +229,26 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
         {
             const float *R = V.R;
             for (int k = 0; k < 3; k++) gmut[k] += R[k] * gp[0] + R[3 + k] * gp[1] + R[6 + k] * gp[2];
+        }
+        // ---- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5).  The compositor's
+        // adjoint already zeroed the colour terms where the forward clamped;
+        // two streaming passes over the coefficients (dL/dsh from Y, then
+        // dL/ddir from dY) keep few values live at a time.
+        {
+            const float gcol[3] = {G2[6], G2[7], G2[8]};
+            float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
+            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float inv = 1.0f / dist;
+            dx *= inv; dy *= inv; dz *= inv;
+            const float *shp = V.sh + (size_t)i * K * 3;
+            const bool vec = aligned16(V.sh) && (!V.g_sh || aligned16(V.g_sh));
+            if (V.g_sh) sh_coef_adjoint<D>(dx, dy, dz, gcol, V.g_sh + (size_t)i * K * 3, vec, atomic);
+            float gd[3];
+            sh_dir_adjoint<D>(dx, dy, dz, gcol, shp, vec, gd);
+            const float dot = dx * gd[0] + dy * gd[1] + dz * gd[2];
+            gmut[0] += (gd[0] - dx * dot) * inv;
+            gmut[1] += (gd[1] - dy * dot) * inv;
+            gmut[2] += (gd[2] - dz * dot) * inv;
         }
         // ---- time evaluation (Eq. 6 / Eq. 7)
         {

@@ -97,7 +97,8 @@ struct Params {
     uint32_t *pix_last;      // [sum HW] list position after the last blend
     uint32_t *pix_neval;     // [2][sum HW] stats pass: in-footprint entries up to the stop, and blended ones
     // backward
-    float *g2d;              // [M*10]
+    float *g2d;              // [M*10] image-space gradients by depth position (u, v, conic a b c,
+                             // o~, colour with the forward's clamp applied, z)
     // extra channels
     int32_t feat_mask;       // kFeat* bits (0: none)
     int32_t n_feat;          // F

@@ -198,8 +198,13 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
             gt[2] = -0.5f * a[2];
             gt[3] = -a[3];
             gt[4] = -0.5f * a[4];
-#pragma unroll
-            for (int c = 5; c < NG; c++) gt[c] = a[c];
+            gt[5] = a[5];
+            // colour = max(0, raw): no gradient where the forward clamped
+            const float4 col = s2[k];
+            gt[6] = col.x > 0.f ? a[6] : 0.f;
+            gt[7] = col.y > 0.f ? a[7] : 0.f;
+            gt[8] = col.z > 0.f ? a[8] : 0.f;
+            gt[9] = a[9];
             float *dst = &P.g2d[10 * (size_t)s_m[k]];
 #pragma unroll
             for (int c = 0; c < NG; c++)
