@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
         for (int k = 0; k < cnt && done != ALL; k++) {
             const float4 g = s0[k];
             const float2 q = s1[k];
+            const float4 col = s2[k];
+            const uint32_t pos = base + k + 1 - r.x;  // list position after this entry
             const float dx = __fsub_rn(fx, g.x);
 #pragma unroll
             for (int p = 0; p < PX; p++) {
@@ -83,14 +85,13 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
                     continue;
                 }
                 const float w = __fmul_rn(alpha, T[p]);
-                const float4 col = s2[k];
                 C0[p] = __fmaf_rn(col.x, w, C0[p]);
                 C1[p] = __fmaf_rn(col.y, w, C1[p]);
                 C2[p] = __fmaf_rn(col.z, w, C2[p]);
                 D[p] = __fmaf_rn(col.w, w, D[p]);
                 O[p] = __fadd_rn(O[p], w);
                 T[p] = Tn;
-                last[p] = base + k + 1 - r.x;
+                last[p] = pos;
             }
         }
     }
