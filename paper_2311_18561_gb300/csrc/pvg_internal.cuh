@@ -150,6 +150,38 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// Pairs of FP32 values in one instruction (PTX .f32x2 arithmetic, sm_100
+// and later).  Each half is rounded exactly as the scalar __f*_rn
+// intrinsic rounds it, so packed and scalar code give identical bits.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 // Gaussian falloff exponent in base-2 units for the record's prescaled
 // conic (a', b', c') = -log2(e) (a/2, b, c/2): the pixel weight is
 // 2^(a' dx^2 + b' dx dy + c' dy^2).  Written with explicit roundings so
@@ -157,6 +189,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 __device__ __forceinline__ float falloff_exp2(float ap, float bp, float cp, float dx, float dy) {
     const float t = __fmaf_rn(bp, dy, __fmul_rn(ap, dx));
     return __fmaf_rn(__fmul_rn(cp, dy), dy, __fmul_rn(dx, t));
+}
+
+// falloff_exp2 for two pixels of one column (same dx, rows dy.x, dy.y),
+// operands given as pairs: adx = (a' dx, a' dx), bp = (b', b'),
+// cp = (c', c'), dx2 = (dx, dx); the same roundings in each half
+__device__ __forceinline__ float2 falloff_exp2_x2(float2 adx, float2 bp, float2 cp, float2 dx2, float2 dy) {
+    const float2 t = fma2(bp, dy, adx);
+    return fma2(mul2(cp, dy), dy, mul2(dx2, t));
 }
 
 // Sky background (Sec. 3.4, C_f = C + (1 - O) f_sky(d)): the four texels

@@ -21,6 +21,48 @@
 namespace pvg {
 namespace {
 
+// Writes the images (and the saved per-pixel state) of a thread's PX pixels.
+template <int PX>
+__device__ __forceinline__ void composite_epilogue(const Params &P, const ViewDesc &V, const TileGeom &G,
+                                                   const float (&T)[PX], const float (&C0)[PX],
+                                                   const float (&C1)[PX], const float (&C2)[PX],
+                                                   const float (&D)[PX], const float (&O)[PX],
+                                                   const uint32_t (&last)[PX]) {
+    if (G.px >= V.W) return;
+    const size_t HW = (size_t)V.W * V.H;
+#pragma unroll
+    for (int p = 0; p < PX; p++) {
+        const int py = G.py0 + p;
+        if (py >= V.H) break;
+        const size_t pix = (size_t)py * V.W + G.px;
+        if (V.sky) {  // C + (1 - O) f_sky(d)
+            size_t ti[4];
+            float tw[4];
+            sky_texels(V, G.px, py, ti, tw);
+            float f[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                f[c] = tw[0] * V.sky[ti[0] + c] + tw[1] * V.sky[ti[1] + c] + tw[2] * V.sky[ti[2] + c] +
+                       tw[3] * V.sky[ti[3] + c];
+            const float wo = 1.0f - O[p];
+            V.out_rgb[pix] = C0[p] + wo * f[0];
+            V.out_rgb[HW + pix] = C1[p] + wo * f[1];
+            V.out_rgb[2 * HW + pix] = C2[p] + wo * f[2];
+        } else {
+            V.out_rgb[pix] = C0[p] + T[p] * V.bg[0];
+            V.out_rgb[HW + pix] = C1[p] + T[p] * V.bg[1];
+            V.out_rgb[2 * HW + pix] = C2[p] + T[p] * V.bg[2];
+        }
+        if (V.out_depth) V.out_depth[pix] = D[p];
+        if (V.out_alpha) V.out_alpha[pix] = O[p];
+        if (P.pix_T) {
+            P.pix_T[V.pix_base + pix] = T[p];
+            P.pix_last[V.pix_base + pix] = last[p];
+        }
+    }
+}
+
+// kStats: instead of images, write per pixel the number of list entries
 // whose footprint box contains the pixel, up to and including the one
 // that stopped it (the compositing work E), and the number of those with
 // alpha >= 1/255 (blended, or stopping the pixel).
@@ -95,49 +137,135 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
             }
         }
     }
-    if (G.px >= V.W) return;
-    const size_t HW = (size_t)V.W * V.H;
+    if constexpr (kStats) {
+        if (G.px >= V.W) return;
 #pragma unroll
-    for (int p = 0; p < PX; p++) {
-        const int py = G.py0 + p;
-        if (py >= V.H) break;
-        const size_t pix = (size_t)py * V.W + G.px;
-        if (kStats) {
+        for (int p = 0; p < PX; p++) {
+            const int py = G.py0 + p;
+            if (py >= V.H) break;
+            const size_t pix = (size_t)py * V.W + G.px;
             P.pix_neval[V.pix_base + pix] = neval[p];
             P.pix_neval[P.total_pix + V.pix_base + pix] = nblend[p];
-            continue;
         }
-        if (V.sky) {  // C + (1 - O) f_sky(d)
-            size_t ti[4];
-            float tw[4];
-            sky_texels(V, G.px, py, ti, tw);
-            float f[3];
+    } else {
+        composite_epilogue<PX>(P, V, G, T, C0, C1, C2, D, O, last);
+    }
+}
+
+// The compositor for an even number of pixels per thread, on packed pairs
+// of vertically adjacent pixels: the falloff, alpha, transmittance and
+// accumulation of both pixels of a pair take one .f32x2 instruction each.
+// The records are staged with their per-pixel operands duplicated into
+// pairs.  A pixel of a pair that does not blend (alpha < 1/255, stopped,
+// outside the image) adds a zero weight and keeps its T, which leaves its
+// sums bit-identical to skipping it, so the images equal the scalar
+// kernel's bit for bit.
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
+    static_assert(PX % 2 == 0, "pairs of pixels");
+    constexpr int BLOCK = TW * TH / PX;
+    constexpr int NP = PX / 2;
+    constexpr uint32_t ALL = (1u << PX) - 1u;
+    __shared__ float4 sA[BLOCK];  // (u, a', v, v)
+    __shared__ float4 sB[BLOCK];  // (b', b', c', c')
+    __shared__ float4 sC[BLOCK];  // (o~, o~, r, r)
+    __shared__ float4 sD[BLOCK];  // (g, g, b, b)
+    __shared__ float2 sE[BLOCK];  // (z, z)
+    const TileGeom G = tile_geom<TW, TH, PX>(P);
+    const ViewDesc &V = *G.V;
+    const uint2 r = G.r;
+    const int tid = threadIdx.x;
+    const float fx = (float)G.px + 0.5f;
+    const float2 one2 = make_float2(1.0f, 1.0f);
+    float2 fy[NP], T[NP], C0[NP], C1[NP], C2[NP], D[NP], O[NP];
+    uint32_t last[PX];
+    uint32_t done = 0;
 #pragma unroll
-            for (int c = 0; c < 3; c++)
-                f[c] = tw[0] * V.sky[ti[0] + c] + tw[1] * V.sky[ti[1] + c] + tw[2] * V.sky[ti[2] + c] +
-                       tw[3] * V.sky[ti[3] + c];
-            const float wo = 1.0f - O[p];
-            V.out_rgb[pix] = C0[p] + wo * f[0];
-            V.out_rgb[HW + pix] = C1[p] + wo * f[1];
-            V.out_rgb[2 * HW + pix] = C2[p] + wo * f[2];
-        } else {
-            V.out_rgb[pix] = C0[p] + T[p] * V.bg[0];
-            V.out_rgb[HW + pix] = C1[p] + T[p] * V.bg[1];
-            V.out_rgb[2 * HW + pix] = C2[p] + T[p] * V.bg[2];
+    for (int q = 0; q < NP; q++) {
+        fy[q] = make_float2((float)(G.py0 + 2 * q) + 0.5f, (float)(G.py0 + 2 * q + 1) + 0.5f);
+        T[q] = one2;
+        C0[q] = C1[q] = C2[q] = D[q] = O[q] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int p = 0; p < PX; p++) {
+        last[p] = 0;
+        if (!(G.px < V.W && G.py0 + p < V.H)) done |= 1u << p;
+    }
+    for (uint32_t base = r.x; base < r.y; base += BLOCK) {
+        if (__syncthreads_count(done != ALL) == 0) break;
+        const uint32_t j = base + tid;
+        if (j < r.y) {
+            float4 a, c;
+            float2 b;
+            record_terms(P.rec, P.pair_vals[j], a, b, c);
+            sA[tid] = make_float4(a.x, a.z, a.y, a.y);
+            sB[tid] = make_float4(a.w, a.w, b.x, b.x);
+            sC[tid] = make_float4(b.y, b.y, c.x, c.x);
+            sD[tid] = make_float4(c.y, c.y, c.z, c.z);
+            sE[tid] = make_float2(c.w, c.w);
         }
-        if (V.out_depth) V.out_depth[pix] = D[p];
-        if (V.out_alpha) V.out_alpha[pix] = O[p];
-        if (P.pix_T) {
-            P.pix_T[V.pix_base + pix] = T[p];
-            P.pix_last[V.pix_base + pix] = last[p];
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)BLOCK, r.y - base);
+        for (int k = 0; k < cnt && done != ALL; k++) {
+            const float4 A = sA[k], B = sB[k], Cq = sC[k], Dq = sD[k];
+            const float2 E = sE[k];
+            const uint32_t pos = base + k + 1 - r.x;  // list position after this entry
+            const float dx = __fsub_rn(fx, A.x);
+            const float adx = __fmul_rn(A.y, dx);
+            const float2 dx2 = make_float2(dx, dx), adx2 = make_float2(adx, adx);
+            const float2 v2 = make_float2(A.z, A.w), bp2 = make_float2(B.x, B.y), cp2 = make_float2(B.z, B.w);
+            const float2 o2 = make_float2(Cq.x, Cq.y), r2 = make_float2(Cq.z, Cq.w);
+            const float2 g2 = make_float2(Dq.x, Dq.y), b2 = make_float2(Dq.z, Dq.w);
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                const uint32_t bits = (done >> (2 * q)) & 3u;
+                if (bits == 3u) continue;
+                const float2 dy = sub2(fy[q], v2);
+                const float2 e = falloff_exp2_x2(adx2, bp2, cp2, dx2, dy);
+                const float2 a = mul2(o2, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                const float ax = fminf(kAlphaCap, a.x), ay = fminf(kAlphaCap, a.y);
+                bool bx = !(bits & 1u) && ax >= kAlphaMin, by = !(bits & 2u) && ay >= kAlphaMin;
+                if (!(bx || by)) continue;
+                const float2 al = make_float2(ax, ay);
+                const float2 Tn = mul2(T[q], sub2(one2, al));
+                const bool sx = bx && Tn.x < kTStop, sy = by && Tn.y < kTStop;
+                done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
+                bx = bx && !sx;
+                by = by && !sy;
+                float2 w = mul2(al, T[q]);
+                w.x = bx ? w.x : 0.f;
+                w.y = by ? w.y : 0.f;
+                C0[q] = fma2(r2, w, C0[q]);
+                C1[q] = fma2(g2, w, C1[q]);
+                C2[q] = fma2(b2, w, C2[q]);
+                D[q] = fma2(E, w, D[q]);
+                O[q] = add2(O[q], w);
+                T[q] = make_float2(bx ? Tn.x : T[q].x, by ? Tn.y : T[q].y);
+                last[2 * q] = bx ? pos : last[2 * q];
+                last[2 * q + 1] = by ? pos : last[2 * q + 1];
+            }
         }
     }
+    float Ts[PX], C0s[PX], C1s[PX], C2s[PX], Ds[PX], Os[PX];
+#pragma unroll
+    for (int q = 0; q < NP; q++) {
+        Ts[2 * q] = T[q].x; Ts[2 * q + 1] = T[q].y;
+        C0s[2 * q] = C0[q].x; C0s[2 * q + 1] = C0[q].y;
+        C1s[2 * q] = C1[q].x; C1s[2 * q + 1] = C1[q].y;
+        C2s[2 * q] = C2[q].x; C2s[2 * q + 1] = C2[q].y;
+        Ds[2 * q] = D[q].x; Ds[2 * q + 1] = D[q].y;
+        Os[2 * q] = O[q].x; Os[2 * q + 1] = O[q].y;
+    }
+    composite_epilogue<PX>(P, V, G, Ts, C0s, C1s, C2s, Ds, Os, last);
 }
 
 template <int TW, int TH, int PX>
 void launch_fwd_t(const Params &p, cudaStream_t s) {
     note_launch();
-    k_composite<TW, TH, PX, false><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+    if constexpr (PX % 2 == 0)
+        k_composite_x2<TW, TH, PX><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+    else
+        k_composite<TW, TH, PX, false><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
 }
 
 template <int TW, int TH, int PX>
