@@ -10,9 +10,9 @@
 // so one scalar per pixel carries what the colour, depth and opacity
 // suffix sums would.  The 10 image-space gradient terms of an entry
 // (moments of dL/dpower for u, v, conic a b c; o~; r g b; z) are summed
-// over a thread's PX pixels, then over the warp by a transposing butterfly
-// (16 shuffles; afterwards lane 2s holds term s), added to per-CTA shared
-// accumulators by 10 lanes at once, and reach global memory with one
+// over a thread's PX pixels, then over the warp by two transposing
+// butterflies (12 shuffles; afterwards lane s holds term s), added to
+// per-CTA shared accumulators by 10 lanes at once, and reach global memory with one
 // atomic per (Gaussian, tile, term).  Alpha is the forward's expression
 // (explicit roundings), so the blend decisions are the forward's; the rest
 // of this file may contract a*b+c into fused multiply-adds.
@@ -21,39 +21,36 @@
 namespace pvg {
 namespace {
 
-// Sum of v[0..9] over the warp.  On return lane L holds the total of term
-// L >> 1 (terms 10..15 are padding and hold 0).
-__device__ __forceinline__ float warp_sum10(const float (&v)[10]) {
+// Sum of v[0..9] over the warp, as two transposing butterflies: terms 0..7
+// within groups of 8 lanes (4 + 2 + 1 exchanges, then two folds across the
+// groups) and terms 8, 9 between lane pairs (1 exchange, four folds).  On
+// return lane L holds in .x the total of term L & 7 and in .y that of term
+// 8 + (L & 1); lanes 0..9 therefore hold term L in .x (L < 8) or .y.
+// 12 shuffles and 44 instructions instead of one 16-slot butterfly's 62.
+__device__ __forceinline__ float2 warp_sum10(const float (&v)[10]) {
     const int lane = threadIdx.x & 31;
-    float a[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) a[i] = i < 10 ? v[i] : 0.f;
-    bool hi = lane & 16;
-    float b[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        const float send = hi ? a[i] : a[i + 8];
-        b[i] = (hi ? a[i + 8] : a[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    hi = lane & 8;
-    float c[4];
+    bool hi = lane & 4;
+    float b[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        const float send = hi ? b[i] : b[i + 4];
-        c[i] = (hi ? b[i + 4] : b[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    hi = lane & 4;
-    float d[2];
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const float send = hi ? c[i] : c[i + 2];
-        d[i] = (hi ? c[i + 2] : c[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
+        const float send = hi ? v[i] : v[i + 4];
+        b[i] = (hi ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
     }
     hi = lane & 2;
-    const float send = hi ? d[0] : d[1];
-    float e = (hi ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
-    e += __shfl_xor_sync(0xffffffffu, e, 1);
-    return e;
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float send = hi ? b[i] : b[i + 2];
+        c[i] = (hi ? b[i + 2] : b[i]) + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    hi = lane & 1;
+    float d = (hi ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, hi ? c[0] : c[1], 1);
+    d += __shfl_xor_sync(0xffffffffu, d, 8);
+    d += __shfl_xor_sync(0xffffffffu, d, 16);
+    float e = (hi ? v[9] : v[8]) + __shfl_xor_sync(0xffffffffu, hi ? v[8] : v[9], 1);
+#pragma unroll
+    for (int o = 2; o < 32; o <<= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    return make_float2(d, e);
 }
 
 template <int TW, int TH, int PX>
@@ -180,8 +177,8 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
                 T[p] = Ti;
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_sum10(gv);
-                if ((lane & 1) == 0 && (lane >> 1) < NG) atomicAdd(&s_acc[k * NG + (lane >> 1)], tot);
+                const float2 tot = warp_sum10(gv);
+                if (lane < NG) atomicAdd(&s_acc[k * NG + lane], lane < 8 ? tot.x : tot.y);
             }
         }
         __syncthreads();
