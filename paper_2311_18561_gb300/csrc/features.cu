@@ -10,8 +10,8 @@
 //
 // A pass of its own over the per-tile lists of the colour pass, so the
 // colour compositor keeps its registers when no channel is asked for: one
-// CTA of up to 256 threads per tile, one pixel per thread (tiles larger
-// than the CTA are covered in rounds), the list staged in batches of kFB
+// CTA of up to 256 threads per tile, two vertically adjacent pixels per
+// thread (tiles larger than the CTA are covered in rounds), the list staged in batches of kFB
 // entries: the record's blending terms and the channel values, padded to
 // float4 groups.  Alpha comes from record_terms / falloff_exp2 / ex2 with
 // the colour pass's roundings, so the weights are the colour pass's bit
@@ -31,17 +31,24 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
     __shared__ float4 s0[kFB];
     __shared__ float2 s1[kFB];
     __shared__ float4 sf[kFB * NG];
-    const int rounds = (P.tile_w * P.tile_h + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int rounds = feat_rounds(P);
+    constexpr uint32_t ALL = (1u << kFPX) - 1u;
     for (int round = 0; round < rounds; round++) {
-        const FeatPixel Q = feat_pixel(P, round);
+        const FeatPixels Q = feat_pixels(P, round);
         const ViewDesc &V = *Q.V;
-        const float fx = (float)Q.px + 0.5f, fy = (float)Q.py + 0.5f;
-        float T = 1.0f, acc[4 * NG];
+        const float fx = (float)Q.px + 0.5f;
+        float fy[kFPX], T[kFPX], acc[kFPX][4 * NG];
+        uint32_t done = 0;
 #pragma unroll
-        for (int c = 0; c < 4 * NG; c++) acc[c] = 0.f;
-        bool done = !Q.inside;
+        for (int p = 0; p < kFPX; p++) {
+            fy[p] = (float)(Q.py0 + p) + 0.5f;
+            T[p] = 1.0f;
+#pragma unroll
+            for (int c = 0; c < 4 * NG; c++) acc[p][c] = 0.f;
+            if (!Q.inside[p]) done |= 1u << p;
+        }
         for (uint32_t base = Q.r.x; base < Q.r.y; base += kFB) {
-            if (__syncthreads_count(!done) == 0) break;
+            if (__syncthreads_count(done != ALL) == 0) break;
             const int cnt = (int)min((uint32_t)kFB, Q.r.y - base);
             for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
                 const uint32_t m = P.pair_vals[base + k];
@@ -53,36 +60,53 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
                 stage_feat<NG>(V, P.sgid[m], P.feat_mask, reinterpret_cast<float *>(&sf[k * NG]));
             }
             __syncthreads();
-            for (int k = 0; k < cnt && !done; k++) {
+            for (int k = 0; k < cnt && done != ALL; k++) {
                 const float4 g = s0[k];
                 const float2 q = s1[k];
-                const float dx = __fsub_rn(fx, g.x), dy = __fsub_rn(fy, g.y);
-                const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
-                const float alpha = fminf(kAlphaCap, __fmul_rn(q.y, ex2_approx(e)));
-                if (alpha < kAlphaMin) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                if (Tn < kTStop) {
-                    done = true;
-                    break;
+                const float dx = __fsub_rn(fx, g.x);
+                float w[kFPX];
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < kFPX; p++) {
+                    w[p] = 0.f;
+                    if (done & (1u << p)) continue;
+                    const float dy = __fsub_rn(fy[p], g.y);
+                    const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
+                    const float alpha = fminf(kAlphaCap, __fmul_rn(q.y, ex2_approx(e)));
+                    if (alpha < kAlphaMin) continue;
+                    const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
+                    if (Tn < kTStop) {
+                        done |= 1u << p;
+                        continue;
+                    }
+                    w[p] = __fmul_rn(alpha, T[p]);
+                    T[p] = Tn;
+                    any = true;
                 }
-                const float w = __fmul_rn(alpha, T);
+                if (!any) continue;
+                // a pixel that did not blend adds a zero weight: its sums are unchanged
 #pragma unroll
                 for (int gi = 0; gi < NG; gi++) {
                     const float4 f = sf[k * NG + gi];
-                    acc[4 * gi] = __fmaf_rn(f.x, w, acc[4 * gi]);
-                    acc[4 * gi + 1] = __fmaf_rn(f.y, w, acc[4 * gi + 1]);
-                    acc[4 * gi + 2] = __fmaf_rn(f.z, w, acc[4 * gi + 2]);
-                    acc[4 * gi + 3] = __fmaf_rn(f.w, w, acc[4 * gi + 3]);
+#pragma unroll
+                    for (int p = 0; p < kFPX; p++) {
+                        acc[p][4 * gi] = __fmaf_rn(f.x, w[p], acc[p][4 * gi]);
+                        acc[p][4 * gi + 1] = __fmaf_rn(f.y, w[p], acc[p][4 * gi + 1]);
+                        acc[p][4 * gi + 2] = __fmaf_rn(f.z, w[p], acc[p][4 * gi + 2]);
+                        acc[p][4 * gi + 3] = __fmaf_rn(f.w, w[p], acc[p][4 * gi + 3]);
+                    }
                 }
-                T = Tn;
             }
         }
         __syncthreads();  // the next round restages
-        if (Q.inside) {
-            const size_t HW = (size_t)V.W * V.H, pix = (size_t)Q.py * V.W + Q.px;
+        const size_t HW = (size_t)V.W * V.H;
+#pragma unroll
+        for (int p = 0; p < kFPX; p++) {
+            if (!Q.inside[p]) continue;
+            const size_t pix = (size_t)(Q.py0 + p) * V.W + Q.px;
 #pragma unroll
             for (int c = 0; c < 4 * NG; c++)
-                if (c < P.n_feat) V.out_feat[c * HW + pix] = acc[c];
+                if (c < P.n_feat) V.out_feat[c * HW + pix] = acc[p][c];
         }
     }
 }
@@ -92,7 +116,7 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
 void launch_composite_feat(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0 || p.n_feat <= 0) return;
     note_launch();
-    const int block = min(kFeatBlock, p.tile_w * p.tile_h);
+    const int block = min(kFeatBlock, p.tile_w * p.tile_h / kFPX);
     switch ((p.n_feat + 3) / 4) {
         case 1: k_composite_feat<1><<<p.total_tiles, block, 0, s>>>(p); break;
         case 2: k_composite_feat<2><<<p.total_tiles, block, 0, s>>>(p); break;

@@ -1,7 +1,8 @@
 // features_bwd.cu -- adjoint of the extra composited channels.
 //
 // The walk of the colour adjoint, back to front from the pixel's final
-// transmittance and last blended position.  With X_i = gF.x_i and the
+// transmittance and last blended position, two vertically adjacent pixels
+// per thread (their terms are summed before the warp reduction).  With X_i = gF.x_i and the
 // scalar suffix sum S_i = sum_{j > i} X_j w_j,
 //   dL/dalpha_i (channels) = T_i X_i - S_i / (1 - alpha_i),
 // whose effect on (u, v, conic, o~) is added to the image-space gradient
@@ -63,28 +64,36 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
     __shared__ uint32_t s_m[kFB];
     __shared__ float s_acc[kFB * NT];
     __shared__ uint32_t s_maxlast;
-    const int rounds = (P.tile_w * P.tile_h + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int rounds = feat_rounds(P);
     const int tid = threadIdx.x;
     for (int round = 0; round < rounds; round++) {
-        const FeatPixel Q = feat_pixel(P, round);
+        const FeatPixels Q = feat_pixels(P, round);
         const ViewDesc &V = *Q.V;
-        const float fx = (float)Q.px + 0.5f, fy = (float)Q.py + 0.5f;
-        float T = 1.0f, gF[F4], S = 0.f;  // S: suffix sum of X_j w_j (no background)
-        uint32_t last = 0;
+        const float fx = (float)Q.px + 0.5f;
+        float fy[kFPX], T[kFPX], S[kFPX], gF[kFPX][F4];  // S: suffix sum of X_j w_j (no background)
+        uint32_t last[kFPX], maxlast = 0;
 #pragma unroll
-        for (int c = 0; c < F4; c++) gF[c] = 0.f;
-        if (Q.inside && V.dl_feat) {
-            const size_t HW = (size_t)V.W * V.H, pix = (size_t)Q.py * V.W + Q.px;
-            T = P.pix_T[V.pix_base + pix];
-            last = P.pix_last[V.pix_base + pix];
+        for (int p = 0; p < kFPX; p++) {
+            fy[p] = (float)(Q.py0 + p) + 0.5f;
+            T[p] = 1.0f;
+            S[p] = 0.f;
+            last[p] = 0;
 #pragma unroll
-            for (int c = 0; c < F4; c++)
-                if (c < P.n_feat) gF[c] = V.dl_feat[c * HW + pix];
+            for (int c = 0; c < F4; c++) gF[p][c] = 0.f;
+            if (Q.inside[p] && V.dl_feat) {
+                const size_t HW = (size_t)V.W * V.H, pix = (size_t)(Q.py0 + p) * V.W + Q.px;
+                T[p] = P.pix_T[V.pix_base + pix];
+                last[p] = P.pix_last[V.pix_base + pix];
+#pragma unroll
+                for (int c = 0; c < F4; c++)
+                    if (c < P.n_feat) gF[p][c] = V.dl_feat[c * HW + pix];
+            }
+            maxlast = max(maxlast, last[p]);
         }
         __syncthreads();  // previous round done with the shared arrays
         if (tid == 0) s_maxlast = 0;
         __syncthreads();
-        if (last) atomicMax(&s_maxlast, last);
+        if (maxlast) atomicMax(&s_maxlast, maxlast);
         __syncthreads();
         const uint32_t n = s_maxlast;
         for (uint32_t end = Q.r.x + n; end > Q.r.x;) {
@@ -109,45 +118,47 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
 #pragma unroll
                 for (int c = 0; c < NT; c++) gv[c] = 0.f;
                 bool contrib = false;
-                if (pos < last) {
-                    const float4 g = s0[k];
-                    const float2 q = s1[k];
-                    const float dx = __fsub_rn(fx, g.x), dy = __fsub_rn(fy, g.y);
+                const float4 g = s0[k];
+                const float2 q = s1[k];
+                const float dx = __fsub_rn(fx, g.x);
+#pragma unroll
+                for (int p = 0; p < kFPX; p++) {
+                    if (pos >= last[p]) continue;
+                    const float dy = __fsub_rn(fy[p], g.y);
                     const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
                     const float G = ex2_approx(e);
                     const float raw = __fmul_rn(q.y, G);
                     const float alpha = fminf(kAlphaCap, raw);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float inv = rcp_approx(1.0f - alpha);
-                        const float Ti = T * inv;
-                        const float w = alpha * Ti;
-                        float X = 0.f;
+                    if (alpha < kAlphaMin) continue;
+                    contrib = true;
+                    const float inv = rcp_approx(1.0f - alpha);
+                    const float Ti = T[p] * inv;
+                    const float w = alpha * Ti;
+                    float X = 0.f;
 #pragma unroll
-                        for (int gi = 0; gi < NG; gi++) {
-                            const float4 f = sf[k * NG + gi];
-                            const float fv[4] = {f.x, f.y, f.z, f.w};
+                    for (int gi = 0; gi < NG; gi++) {
+                        const float4 f = sf[k * NG + gi];
+                        const float fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
-                            for (int j = 0; j < 4; j++) {
-                                const int c = 4 * gi + j;
-                                X += gF[c] * fv[j];
-                                gv[6 + c] = gF[c] * w;
-                            }
+                        for (int j = 0; j < 4; j++) {
+                            const int c = 4 * gi + j;
+                            X += gF[p][c] * fv[j];
+                            gv[6 + c] += gF[p][c] * w;
                         }
-                        if (raw <= kAlphaCap) {
-                            const float ga = Ti * X - inv * S;
-                            gv[5] = ga * G;
-                            const float gpow = ga * alpha;
-                            const float mx = gpow * dx, my = gpow * dy;
-                            gv[0] = mx;
-                            gv[1] = my;
-                            gv[2] = mx * dx;
-                            gv[3] = mx * dy;
-                            gv[4] = my * dy;
-                        }
-                        S += X * w;
-                        T = Ti;
                     }
+                    if (raw <= kAlphaCap) {
+                        const float ga = Ti * X - inv * S[p];
+                        gv[5] += ga * G;
+                        const float gpow = ga * alpha;
+                        const float mx = gpow * dx, my = gpow * dy;
+                        gv[0] += mx;
+                        gv[1] += my;
+                        gv[2] += mx * dx;
+                        gv[3] += mx * dy;
+                        gv[4] += my * dy;
+                    }
+                    S[p] += X * w;
+                    T[p] = Ti;
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     constexpr int N0 = NT >= 32 ? 32 : pow2_at_least(NT);
@@ -223,7 +234,7 @@ __global__ void k_feat_param_bwd(Params P) {
 void launch_composite_feat_bwd(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0 || p.n_feat <= 0) return;
     note_launch();
-    const int block = min(kFeatBlock, p.tile_w * p.tile_h);
+    const int block = min(kFeatBlock, p.tile_w * p.tile_h / kFPX);
     switch ((p.n_feat + 3) / 4) {
         case 1: k_composite_feat_bwd<1><<<p.total_tiles, block, 0, s>>>(p); break;
         case 2: k_composite_feat_bwd<2><<<p.total_tiles, block, 0, s>>>(p); break;

@@ -30,26 +30,37 @@ __device__ __forceinline__ void stage_feat(const ViewDesc &V, uint32_t gid, int 
         for (int k = 0; k < V.n_sem; k++) dst[c + k] = V.sem[(size_t)i * V.n_sem + k];
 }
 
-struct FeatPixel {
+constexpr int kFPX = 2;  // vertically adjacent pixels per thread
+
+// The kFPX pixels (column px, rows py0 .. py0 + kFPX - 1) that thread
+// threadIdx.x handles in `round` of its tile (pixel pairs in row-major
+// order), and the tile's list range.
+struct FeatPixels {
     const ViewDesc *V;
-    int px, py;
-    bool inside;
+    int px, py0;
+    bool inside[kFPX];
     uint2 r;
 };
 
-__device__ __forceinline__ FeatPixel feat_pixel(const Params &P, int round) {
-    FeatPixel q;
+__device__ __forceinline__ FeatPixels feat_pixels(const Params &P, int round) {
+    FeatPixels q;
     const uint32_t tile = P.tile_order ? P.tile_order[blockIdx.x] : blockIdx.x;
     q.V = &P.views[view_of_tile(P.views, P.n_views, tile)];
     const uint32_t lt = tile - q.V->tile_base;
     const int tx = (int)(lt % (uint32_t)q.V->tiles_x), ty = (int)(lt / (uint32_t)q.V->tiles_x);
-    const int k = round * (int)blockDim.x + (int)threadIdx.x;  // pixel of the tile, row-major
-    const bool in_tile = k < P.tile_w * P.tile_h;
+    const int k = round * (int)blockDim.x + (int)threadIdx.x;  // pixel group of the tile
+    const bool in_tile = k < P.tile_w * (P.tile_h / kFPX);
     q.px = tx * P.tile_w + k % P.tile_w;
-    q.py = ty * P.tile_h + k / P.tile_w;
-    q.inside = in_tile && q.px < q.V->W && q.py < q.V->H;
+    q.py0 = ty * P.tile_h + (k / P.tile_w) * kFPX;
+#pragma unroll
+    for (int p = 0; p < kFPX; p++) q.inside[p] = in_tile && q.px < q.V->W && q.py0 + p < q.V->H;
     q.r = P.ranges[tile];
     return q;
+}
+
+__device__ __forceinline__ int feat_rounds(const Params &P) {
+    const int groups = P.tile_w * (P.tile_h / kFPX);
+    return (groups + (int)blockDim.x - 1) / (int)blockDim.x;
 }
 
 }  // namespace
