@@ -53,6 +53,80 @@ __device__ __forceinline__ float2 warp_sum10(const float (&v)[10]) {
     return make_float2(d, e);
 }
 
+// Per-pixel state of the adjoint walk: final transmittance, last blended
+// position, output gradients and the initial suffix sum (the background's
+// share); with a sky map, its gradient is scattered here and its effect on
+// dL/dO folded into gO.
+struct PixelAdjoint {
+    float T, gC0, gC1, gC2, gD, gO, S;
+    uint32_t last;
+};
+
+__device__ __forceinline__ PixelAdjoint pixel_adjoint(const Params &P, const ViewDesc &V, int px, int py) {
+    PixelAdjoint a;
+    a.T = 1.0f;
+    a.gC0 = a.gC1 = a.gC2 = a.gD = a.gO = 0.f;
+    a.last = 0;
+    const bool inside = px < V.W && py < V.H;
+    if (inside) {
+        const size_t HW = (size_t)V.W * V.H, pix = (size_t)py * V.W + px;
+        a.T = P.pix_T[V.pix_base + pix];
+        a.last = P.pix_last[V.pix_base + pix];
+        if (V.dl_rgb) {
+            a.gC0 = V.dl_rgb[pix];
+            a.gC1 = V.dl_rgb[HW + pix];
+            a.gC2 = V.dl_rgb[2 * HW + pix];
+        }
+        if (V.dl_depth) a.gD = V.dl_depth[pix];
+        if (V.dl_alpha) a.gO = V.dl_alpha[pix];
+    }
+    a.S = a.T * (a.gC0 * V.bg[0] + a.gC1 * V.bg[1] + a.gC2 * V.bg[2]);
+    if (V.sky && inside) {
+        // colour = C + (1 - O) f: no constant background, dL/dO -= gC.f,
+        // dL/df = (1 - O) gC scattered to the four texels
+        size_t ti[4];
+        float tw[4];
+        sky_texels(V, px, py, ti, tw);
+        const float gc[3] = {a.gC0, a.gC1, a.gC2};
+        const float wo = a.T;  // 1 - O = T_final
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float f = tw[0] * V.sky[ti[0] + c] + tw[1] * V.sky[ti[1] + c] + tw[2] * V.sky[ti[2] + c] +
+                            tw[3] * V.sky[ti[3] + c];
+            a.gO -= gc[c] * f;
+            if (V.g_sky && gc[c] != 0.f)
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (tw[q] != 0.f) atomicAdd(V.g_sky + ti[q] + c, tw[q] * wo * gc[c]);
+        }
+        a.S = 0.f;
+    }
+    return a;
+}
+
+// Image-space gradients of a staged entry from its CTA-summed terms:
+//   d/da = -m_xx / 2, d/db = -m_xy, d/dc = -m_yy / 2,
+//   d/du = (a m_x + b m_y) = -(2 a' m_x + b' m_y) / log2(e),
+//   d/dv = (b m_x + c m_y) = -(b' m_x + 2 c' m_y) / log2(e);
+// colour terms are zeroed where the forward clamped (col <= 0).
+__device__ __forceinline__ void flush_entry(float *dst, const float *a, float ap, float bp, float cp, float r,
+                                            float g, float b) {
+    float gt[10];
+    gt[0] = -0.6931471805599453f * (2.f * ap * a[0] + bp * a[1]);
+    gt[1] = -0.6931471805599453f * (bp * a[0] + 2.f * cp * a[1]);
+    gt[2] = -0.5f * a[2];
+    gt[3] = -a[3];
+    gt[4] = -0.5f * a[4];
+    gt[5] = a[5];
+    gt[6] = r > 0.f ? a[6] : 0.f;
+    gt[7] = g > 0.f ? a[7] : 0.f;
+    gt[8] = b > 0.f ? a[8] : 0.f;
+    gt[9] = a[9];
+#pragma unroll
+    for (int c = 0; c < 10; c++)
+        if (gt[c] != 0.f) atomicAdd(dst + c, gt[c]);
+}
+
 template <int TW, int TH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
     constexpr int BLOCK = TW * TH / PX;
@@ -68,7 +142,6 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
     const uint2 r = Gm.r;
     const int tid = threadIdx.x, lane = tid & 31;
     const float fx = (float)Gm.px + 0.5f;
-    const size_t HW = (size_t)V.W * V.H;
 
     float fy[PX], T[PX], gC0[PX], gC1[PX], gC2[PX], gD[PX], gO[PX];
     float S[PX];  // suffix sum of X_j alpha_j T_j
@@ -76,44 +149,10 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
     uint32_t maxlast = 0;
 #pragma unroll
     for (int p = 0; p < PX; p++) {
-        const int py = Gm.py0 + p;
-        fy[p] = (float)py + 0.5f;
-        T[p] = 1.0f;
-        gC0[p] = gC1[p] = gC2[p] = gD[p] = gO[p] = 0.f;
-        last[p] = 0;
-        if (Gm.px < V.W && py < V.H) {
-            const size_t pix = (size_t)py * V.W + Gm.px;
-            T[p] = P.pix_T[V.pix_base + pix];
-            last[p] = P.pix_last[V.pix_base + pix];
-            if (V.dl_rgb) {
-                gC0[p] = V.dl_rgb[pix];
-                gC1[p] = V.dl_rgb[HW + pix];
-                gC2[p] = V.dl_rgb[2 * HW + pix];
-            }
-            if (V.dl_depth) gD[p] = V.dl_depth[pix];
-            if (V.dl_alpha) gO[p] = V.dl_alpha[pix];
-        }
-        S[p] = T[p] * (gC0[p] * V.bg[0] + gC1[p] * V.bg[1] + gC2[p] * V.bg[2]);
-        if (V.sky && Gm.px < V.W && py < V.H) {
-            // colour = C + (1 - O) f: no constant background, dL/dO -= gC.f,
-            // dL/df = (1 - O) gC scattered to the four texels
-            size_t ti[4];
-            float tw[4];
-            sky_texels(V, Gm.px, py, ti, tw);
-            const float gc[3] = {gC0[p], gC1[p], gC2[p]};
-            const float wo = T[p];  // 1 - O = T_final
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float f = tw[0] * V.sky[ti[0] + c] + tw[1] * V.sky[ti[1] + c] + tw[2] * V.sky[ti[2] + c] +
-                                tw[3] * V.sky[ti[3] + c];
-                gO[p] -= gc[c] * f;
-                if (V.g_sky && gc[c] != 0.f)
-#pragma unroll
-                    for (int q = 0; q < 4; q++)
-                        if (tw[q] != 0.f) atomicAdd(V.g_sky + ti[q] + c, tw[q] * wo * gc[c]);
-            }
-            S[p] = 0.f;
-        }
+        fy[p] = (float)(Gm.py0 + p) + 0.5f;
+        PixelAdjoint a = pixel_adjoint(P, V, Gm.px, Gm.py0 + p);
+        T[p] = a.T; last[p] = a.last; S[p] = a.S;
+        gC0[p] = a.gC0; gC1[p] = a.gC1; gC2[p] = a.gC2; gD[p] = a.gD; gO[p] = a.gO;
         maxlast = max(maxlast, last[p]);
     }
     if (tid == 0) s_maxlast = 0;
@@ -182,31 +221,9 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
             }
         }
         __syncthreads();
-        // image-space gradients of each staged Gaussian from its moments:
-        //   d/da = -m_xx / 2, d/db = -m_xy, d/dc = -m_yy / 2,
-        //   d/du = (a m_x + b m_y) = -(2 a' m_x + b' m_y) / log2(e),
-        //   d/dv = (b m_x + c m_y) = -(b' m_x + 2 c' m_y) / log2(e)
-        for (int k = tid; k < cnt; k += BLOCK) {
-            const float *a = &s_acc[k * NG];
-            const float ap = s0[k].z, bp = s0[k].w, cp = s1[k].x;
-            float gt[NG];
-            gt[0] = -0.6931471805599453f * (2.f * ap * a[0] + bp * a[1]);
-            gt[1] = -0.6931471805599453f * (bp * a[0] + 2.f * cp * a[1]);
-            gt[2] = -0.5f * a[2];
-            gt[3] = -a[3];
-            gt[4] = -0.5f * a[4];
-            gt[5] = a[5];
-            // colour = max(0, raw): no gradient where the forward clamped
-            const float4 col = s2[k];
-            gt[6] = col.x > 0.f ? a[6] : 0.f;
-            gt[7] = col.y > 0.f ? a[7] : 0.f;
-            gt[8] = col.z > 0.f ? a[8] : 0.f;
-            gt[9] = a[9];
-            float *dst = &P.g2d[10 * (size_t)s_m[k]];
-#pragma unroll
-            for (int c = 0; c < NG; c++)
-                if (gt[c] != 0.f) atomicAdd(dst + c, gt[c]);
-        }
+        for (int k = tid; k < cnt; k += BLOCK)
+            flush_entry(&P.g2d[10 * (size_t)s_m[k]], &s_acc[k * NG], s0[k].z, s0[k].w, s1[k].x, s2[k].x, s2[k].y,
+                        s2[k].z);
         end = start;
     }
 }
