@@ -10,8 +10,8 @@
 //
 // A pass of its own over the per-tile lists of the colour pass, so the
 // colour compositor keeps its registers when no channel is asked for: one
-// CTA of up to 256 threads per tile, two vertically adjacent pixels per
-// thread (tiles larger than the CTA are covered in rounds), the list staged in batches of kFB
+// CTA of up to 256 threads per tile, one pixel per thread (tiles larger
+// than the CTA are covered in rounds), the list staged in batches of kFB
 // entries: the record's blending terms and the channel values, padded to
 // float4 groups.  Alpha comes from record_terms / falloff_exp2 / ex2 with
 // the colour pass's roundings, so the weights are the colour pass's bit
@@ -31,10 +31,11 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
     __shared__ float4 s0[kFB];
     __shared__ float2 s1[kFB];
     __shared__ float4 sf[kFB * NG];
-    const int rounds = feat_rounds(P);
+    constexpr int kFPX = kFwdFPX;
+    const int rounds = feat_rounds<kFPX>(P);
     constexpr uint32_t ALL = (1u << kFPX) - 1u;
     for (int round = 0; round < rounds; round++) {
-        const FeatPixels Q = feat_pixels(P, round);
+        const FeatPixels<kFPX> Q = feat_pixels<kFPX>(P, round);
         const ViewDesc &V = *Q.V;
         const float fx = (float)Q.px + 0.5f;
         float fy[kFPX], T[kFPX], acc[kFPX][4 * NG];
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
 void launch_composite_feat(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0 || p.n_feat <= 0) return;
     note_launch();
-    const int block = min(kFeatBlock, p.tile_w * p.tile_h / kFPX);
+    const int block = min(kFeatBlock, p.tile_w * p.tile_h / kFwdFPX);
     switch ((p.n_feat + 3) / 4) {
         case 1: k_composite_feat<1><<<p.total_tiles, block, 0, s>>>(p); break;
         case 2: k_composite_feat<2><<<p.total_tiles, block, 0, s>>>(p); break;

@@ -64,10 +64,11 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
     __shared__ uint32_t s_m[kFB];
     __shared__ float s_acc[kFB * NT];
     __shared__ uint32_t s_maxlast;
-    const int rounds = feat_rounds(P);
+    constexpr int kFPX = kBwdFPX;
+    const int rounds = feat_rounds<kFPX>(P);
     const int tid = threadIdx.x;
     for (int round = 0; round < rounds; round++) {
-        const FeatPixels Q = feat_pixels(P, round);
+        const FeatPixels<kFPX> Q = feat_pixels<kFPX>(P, round);
         const ViewDesc &V = *Q.V;
         const float fx = (float)Q.px + 0.5f;
         float fy[kFPX], T[kFPX], S[kFPX], gF[kFPX][F4];  // S: suffix sum of X_j w_j (no background)
@@ -234,7 +235,7 @@ __global__ void k_feat_param_bwd(Params P) {
 void launch_composite_feat_bwd(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0 || p.n_feat <= 0) return;
     note_launch();
-    const int block = min(kFeatBlock, p.tile_w * p.tile_h / kFPX);
+    const int block = min(kFeatBlock, p.tile_w * p.tile_h / kBwdFPX);
     switch ((p.n_feat + 3) / 4) {
         case 1: k_composite_feat_bwd<1><<<p.total_tiles, block, 0, s>>>(p); break;
         case 2: k_composite_feat_bwd<2><<<p.total_tiles, block, 0, s>>>(p); break;

@@ -30,38 +30,43 @@ __device__ __forceinline__ void stage_feat(const ViewDesc &V, uint32_t gid, int 
         for (int k = 0; k < V.n_sem; k++) dst[c + k] = V.sem[(size_t)i * V.n_sem + k];
 }
 
-constexpr int kFPX = 2;  // vertically adjacent pixels per thread
-
-// The kFPX pixels (column px, rows py0 .. py0 + kFPX - 1) that thread
-// threadIdx.x handles in `round` of its tile (pixel pairs in row-major
-// order), and the tile's list range.
+// The FPX vertically adjacent pixels (column px, rows py0 .. py0 + FPX - 1)
+// that thread threadIdx.x handles in `round` of its tile (pixel groups in
+// row-major order), and the tile's list range.
+template <int FPX>
 struct FeatPixels {
     const ViewDesc *V;
     int px, py0;
-    bool inside[kFPX];
+    bool inside[FPX];
     uint2 r;
 };
 
-__device__ __forceinline__ FeatPixels feat_pixels(const Params &P, int round) {
-    FeatPixels q;
+template <int FPX>
+__device__ __forceinline__ FeatPixels<FPX> feat_pixels(const Params &P, int round) {
+    FeatPixels<FPX> q;
     const uint32_t tile = P.tile_order ? P.tile_order[blockIdx.x] : blockIdx.x;
     q.V = &P.views[view_of_tile(P.views, P.n_views, tile)];
     const uint32_t lt = tile - q.V->tile_base;
     const int tx = (int)(lt % (uint32_t)q.V->tiles_x), ty = (int)(lt / (uint32_t)q.V->tiles_x);
     const int k = round * (int)blockDim.x + (int)threadIdx.x;  // pixel group of the tile
-    const bool in_tile = k < P.tile_w * (P.tile_h / kFPX);
+    const bool in_tile = k < P.tile_w * (P.tile_h / FPX);
     q.px = tx * P.tile_w + k % P.tile_w;
-    q.py0 = ty * P.tile_h + (k / P.tile_w) * kFPX;
+    q.py0 = ty * P.tile_h + (k / P.tile_w) * FPX;
 #pragma unroll
-    for (int p = 0; p < kFPX; p++) q.inside[p] = in_tile && q.px < q.V->W && q.py0 + p < q.V->H;
+    for (int p = 0; p < FPX; p++) q.inside[p] = in_tile && q.px < q.V->W && q.py0 + p < q.V->H;
     q.r = P.ranges[tile];
     return q;
 }
 
+template <int FPX>
 __device__ __forceinline__ int feat_rounds(const Params &P) {
-    const int groups = P.tile_w * (P.tile_h / kFPX);
+    const int groups = P.tile_w * (P.tile_h / FPX);
     return (groups + (int)blockDim.x - 1) / (int)blockDim.x;
 }
+
+// pixels per thread: the channel compositor keeps one (its per-pixel
+// accumulators are many), its adjoint two (to amortise its warp reduction)
+constexpr int kFwdFPX = 1, kBwdFPX = 2;
 
 }  // namespace
 }  // namespace pvg
