@@ -232,15 +232,16 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
                 done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
                 bx = bx && !sx;
                 by = by && !sy;
-                float2 w = mul2(al, T[q]);
-                w.x = bx ? w.x : 0.f;
-                w.y = by ? w.y : 0.f;
+                // a pixel that does not blend takes alpha 0: w = +0 and T * (1 - 0) = T,
+                // bit for bit; a blending one gets the scalar kernel's w and T'
+                const float2 am = make_float2(bx ? ax : 0.f, by ? ay : 0.f);
+                const float2 w = mul2(am, T[q]);
                 C0[q] = fma2(r2, w, C0[q]);
                 C1[q] = fma2(g2, w, C1[q]);
                 C2[q] = fma2(b2, w, C2[q]);
                 D[q] = fma2(E, w, D[q]);
                 O[q] = add2(O[q], w);
-                T[q] = make_float2(bx ? Tn.x : T[q].x, by ? Tn.y : T[q].y);
+                T[q] = mul2(T[q], sub2(one2, am));
                 last[2 * q] = bx ? pos : last[2 * q];
                 last[2 * q + 1] = by ? pos : last[2 * q + 1];
             }
