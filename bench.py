@@ -82,7 +82,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="tile_w,tile_h,pixels_per_thread (default: autotune)")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving leg (req/s)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="duration of the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="seconds of arrivals per serving leg (default 2 for the leg after the headline "
+                         "step, 10 per rate for --workload serving)")
+    ap.add_argument("--dp", action="store_true",
+                    help="with N > 1 ranks: data-parallel training step, the per-Gaussian gradients "
+                         "summed over ranks in the step (default: independent replicas)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the paper-loss and extra-channel legs (timed after the headline step)")
@@ -252,7 +257,10 @@ def run_ours(args):
     r = R.Renderer(tile=best[:2], pixels_per_thread=best[2], sync_sizes=False, pair_capacity=pair_capacity)
     fr = R.Frame()
     outs = r.alloc_images([cam])
-    grads = {k: torch.empty_like(st[k]) for k in R.PARAM_NAMES}
+    # gradients as views of one flat buffer, so that a data-parallel step
+    # sums them over ranks with a single all-reduce
+    grad_flat, grads = R.flat_gradients(st)
+    dp = args.dp and world > 1
     dl = torch.empty(3, H_PIX, W_PIX, device=dev)
     loss = torch.empty(1, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -261,6 +269,8 @@ def run_ours(args):
         r.forward(st, [cam], outs=outs, frame=fr)
         R.l1_loss(outs[0]["rgb"], target, dl=dl, loss=loss)
         r.backward(st, [cam], fr, [dict(rgb=dl)], grads=grads)
+        if dp:
+            R.allreduce_gradients(grad_flat)
 
     def fwd_only():
         r.forward(st, [cam], outs=outs, frame=fr)
@@ -301,7 +311,8 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         step()
     barrier()
-    step_graph, launches_per_step = capture(step)
+    # (a data-parallel step keeps its collective outside a captured graph)
+    step_graph, launches_per_step = capture(step) if not dp else (None, 35)
     fwd_graph, _ = capture(fwd_only)
     barrier()
 
@@ -310,7 +321,7 @@ def run_ours(args):
     clocks.start()
     barrier()
     t0 = time.perf_counter()
-    step_ms = timed(step_graph.replay, args.steps)
+    step_ms = timed(step_graph.replay if step_graph is not None else step, args.steps)
     barrier()
     wall = time.perf_counter() - t0
     launches = launches_per_step * args.steps
@@ -441,7 +452,8 @@ def run_ours(args):
                                                          "given" if table is None else "autotuned"),
                    "l2": "flushed before every step (256 MB write)",
                    "step": "one CUDA-graph replay of forward + L1 + backward (pair capacity %d = 2x the measured K, no host round trip)" % pair_capacity,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": ("data parallel, gradients all-reduced" if dp else "replicas")
+                   if world > 1 else "single GPU"},
         "fwd_bwd_step_ms": ms_step,
         "autotune_ms": None if table is None else {"%dx%dx%d" % k: round(v, 4) for k, v in table.items()},
         "render_fwd": {"ms": fwd_ms, "mpix_s": job_value(world, mpix, fwd_ms)},
@@ -461,7 +473,7 @@ def run_ours(args):
     if not args.no_serve:
         del st, grads, flush
         torch.cuda.empty_cache()
-        out["serving"] = serving_leg(dev, args.serve_rate, args.serve_seconds, config=best)
+        out["serving"] = serving_leg(dev, args.serve_rate, args.serve_seconds or 2.0, config=best)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, cam, args.cpu_seconds)
     if world > 1:
@@ -591,7 +603,7 @@ def run_serving(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rates = [200.0, 500.0, 1000.0, 2000.0]
-    res = [serving_leg(dev, rt, args.serve_seconds) for rt in rates]
+    res = [serving_leg(dev, rt, args.serve_seconds or 10.0) for rt in rates]
     if rank == 0:
         print(json.dumps({"metric": METRIC, "workload": "serving sweep", "legs": res}), flush=True)
 

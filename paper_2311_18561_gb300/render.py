@@ -282,6 +282,32 @@ def render_differentiable(params, cam, renderer=None):
     return PVGRender.apply(cam, r, *[params[k] for k in PARAM_NAMES], params.get("sky"))
 
 
+def flat_gradients(scene_t):
+    """(flat, grads): one float32 buffer and the per-parameter gradient
+    tensors (shaped like ``scene_t``'s nine parameter arrays) as views of
+    it, ready for :meth:`Renderer.backward` and a single all-reduce."""
+    n = sum(scene_t[k].numel() for k in PARAM_NAMES)
+    flat = torch.empty(n, dtype=torch.float32, device=scene_t["mu"].device)
+    grads, o = {}, 0
+    for k in PARAM_NAMES:
+        t = scene_t[k]
+        grads[k] = flat[o:o + t.numel()].view(t.shape)
+        o += t.numel()
+    return flat, grads
+
+
+def allreduce_gradients(flat, group=None):
+    """Sums a flat gradient buffer over the ranks of ``group`` in place (the
+    exchange step of data-parallel training: every rank renders its own
+    views of the shared scene and the per-Gaussian gradients are added).
+    Uses the process group's backend (NCCL on GPUs, gloo on CPU)."""
+    import torch.distributed as dist
+
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    return flat
+
+
 def l1_loss(pred, target, dl=None, loss=None, scale=None, stream=None):
     """loss = scale * sum|pred - target| (default scale = 1/numel) and
     dl = scale * sign(pred - target), computed by ``pvg_l1_loss``."""

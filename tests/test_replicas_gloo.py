@@ -74,3 +74,49 @@ def test_single_process_defaults(monkeypatch):
     assert bench.dist_env() == (0, 1, 0)
     assert bench.max_over_ranks([1.25, 2.5], 1, "cpu") == [1.25, 2.5]
     assert bench.job_value(1, 2.4576, 2.0) == pytest.approx(1228.8)
+
+
+def _dp_rank_main(rank, world, port, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2311_18561_gb300 import render as R
+    from paper_2311_18561_gb300 import synth
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        scene = {k: torch.from_numpy(np.ascontiguousarray(v)) for k, v in synth.make_fd_scene(seed=0, n=7).items()}
+        flat, grads = R.flat_gradients(scene)
+        for j, k in enumerate(R.PARAM_NAMES):  # a rank's gradients: (rank + 1) (j + 1) everywhere
+            assert grads[k].shape == scene[k].shape and grads[k].data_ptr() >= flat.data_ptr()
+            grads[k].fill_((rank + 1) * (j + 1))
+        R.allreduce_gradients(flat)
+        out.put((rank, {k: grads[k].clone().numpy() for k in R.PARAM_NAMES}))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_data_parallel_gradient_sum():
+    """The exchange step of a data-parallel training step: each rank's
+    per-Gaussian gradients (views of one flat buffer) are summed over the
+    ranks by one all-reduce."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 2
+    procs = [ctx.Process(target=_dp_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    from paper_2311_18561_gb300 import render as R
+
+    total = sum(r + 1 for r in range(world))  # 1 + 2
+    for _, g in res:
+        for j, k in enumerate(R.PARAM_NAMES):
+            assert (g[k] == total * (j + 1)).all(), k
