@@ -74,6 +74,12 @@ const char *pvg_status_str(pvg_status_t s);
 const char *pvg_last_error(void);
 /* Library version as major*10000 + minor*100 + patch. */
 int pvg_version(void);
+/* Test hook for failure handling: the next n device allocations the library
+ * attempts (workspace and frame growth in any context) fail as if the
+ * device were out of memory, so the calls that needed them return
+ * PVG_ERR_OOM; n <= 0 clears the hook.  Allocations that are not needed
+ * (buffers already large enough) are not counted. */
+void pvg_debug_fail_allocations(int32_t n);
 
 /* ------------------------------------------------------------------ */
 /* data                                                                */

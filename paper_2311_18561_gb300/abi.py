@@ -82,6 +82,7 @@ _SIGS = {
     "pvg_status_str": (C.c_char_p, [C.c_int]),
     "pvg_last_error": (C.c_char_p, []),
     "pvg_version": (C.c_int, []),
+    "pvg_debug_fail_allocations": (None, [C.c_int32]),
     "pvg_config_default": (None, [C.POINTER(Config)]),
     "pvg_create": (C.c_int, [C.POINTER(_P), C.POINTER(Config)]),
     "pvg_destroy": (None, [_P]),

@@ -46,11 +46,25 @@ void release(DevBuf &b) {
     b.bytes = 0;
 }
 
+// test hook: the next g_fail_allocs device allocations fail (PVG_ERR_OOM)
+std::atomic<int> g_fail_allocs{0};
+
+bool injected_alloc_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
 // grow to at least `bytes` (x1.25 headroom); contents are not kept
 pvg_status_t ensure(DevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return PVG_OK;
     release(b);
+    if (injected_alloc_failure()) {
+        g_last_error = "device allocation failed (injected)";
+        return PVG_ERR_OOM;
+    }
     const size_t want = bytes + bytes / 4;
     if (cudaMalloc(&b.p, want) != cudaSuccess) {
         cudaGetLastError();
@@ -204,6 +218,8 @@ extern "C" const char *pvg_status_str(pvg_status_t s) {
 extern "C" const char *pvg_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int pvg_version(void) { return 100; }
+
+extern "C" void pvg_debug_fail_allocations(int32_t n) { g_fail_allocs.store(n > 0 ? n : 0); }
 
 extern "C" void pvg_config_default(pvg_config_t *cfg) {
     if (!cfg) return;
