@@ -82,3 +82,30 @@ def tile_lists_brute(gid, z, rect, tiles_x, tiles_y):
                     lst.append(int(g))
             lists.append(lst)
     return lists
+
+
+def contributing_tiles(uv, conic, ot, width, height, tile_w, tile_h, shrink=1.0):
+    """Per Gaussian, the set of tile ids (row-major, ``ceil(width / tile_w)``
+    tiles a row) holding at least one pixel centre where it is blended:
+    ``o~ exp(-q / 2) >= 1/255`` with ``q = d^T conic d`` and d the offset of
+    the pixel centre (px + 0.5, py + 0.5) from ``uv`` (Sec. 3.1, with the
+    1/255 skip of 3DGS), i.e. ``q <= 2 ln(255 o~)``.  ``shrink`` < 1 scales
+    that level down, leaving out centres within rounding of the boundary.
+    Brute force over every pixel; small images only."""
+    uv = np.asarray(uv, np.float64).reshape(-1, 2)
+    conic = np.asarray(conic, np.float64).reshape(-1, 3)
+    ot = np.asarray(ot, np.float64).reshape(-1)
+    tiles_x = (width + tile_w - 1) // tile_w
+    py, px = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
+    tile = (py // tile_h) * tiles_x + px // tile_w
+    cx, cy = px + 0.5, py + 0.5
+    out = []
+    for k in range(uv.shape[0]):
+        if not ot[k] > 1.0 / 255.0:
+            out.append(set())
+            continue
+        level = shrink * 2.0 * np.log(255.0 * ot[k])
+        dx, dy = cx - uv[k, 0], cy - uv[k, 1]
+        q = conic[k, 0] * dx * dx + 2.0 * conic[k, 1] * dx * dy + conic[k, 2] * dy * dy
+        out.append(set(np.unique(tile[q <= level]).tolist()))
+    return out

@@ -8,7 +8,8 @@
 //   k_finalize       (stage a, pass 2) for every visible item, in item
 //                    order: the same projection plus the SH colour; writes
 //                    the 48-byte compositing record, the tile rectangle and
-//                    the tile count at the item's depth position m.
+//                    the count of its tiles that the footprint ellipse
+//                    meets, at the item's depth position m.
 //
 // Both passes compute the projection with the same inline function and
 // this file is compiled with --fmad=false, so pass 1 and pass 2 agree bit
@@ -84,7 +85,15 @@ __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
         P.rec[3 * (size_t)m + 1] = make_float4(F.cc, F.ot, z, F.hx);
         P.rec[3 * (size_t)m + 2] = make_float4(fmaxf(rgb[0], 0.0f), fmaxf(rgb[1], 0.0f), fmaxf(rgb[2], 0.0f), F.hy);
         P.rect[m] = make_uint2(F.tx0 | (F.ty0 << 16), F.tx1 | (F.ty1 << 16));
-        P.vis_cnt[m] = F.count;
+        // tiles of the rectangle that the footprint ellipse meets
+        const FootprintEllipse E = footprint_ellipse(F.u, F.v, F.ca, F.cb, F.cc, F.ot);
+        store_ellipse(P.ell, m, E);
+        uint32_t cnt = 0;
+        for (uint32_t ty = F.ty0; ty < F.ty1; ty++) {
+            const uint2 c = footprint_cols(E, ty, P.tile_w, P.tile_h, F.tx0, F.tx1);
+            cnt += c.y - c.x;
+        }
+        P.vis_cnt[m] = cnt;
     }
 }
 

@@ -95,14 +95,6 @@ __device__ __forceinline__ void store_floats(float *dst, const float (&src)[NF],
 
 __device__ __forceinline__ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Kahan's difference of products a*b - c*d, accurate to a few ulp.
-__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
-    const float w = __fmul_rn(c, d);
-    const float e = __fmaf_rn(-c, d, w);
-    const float f = __fmaf_rn(a, b, -w);
-    return __fadd_rn(f, e);
-}
-
 // Steps 1-3 + footprint for item (view V, index i).  Returns false if the
 // item is culled (behind the near plane, o~ < 1/255, degenerate
 // covariance, non-finite values or no tile covered).

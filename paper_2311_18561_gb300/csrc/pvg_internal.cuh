@@ -8,7 +8,9 @@
 //     rec[m]    3 x float4 record read by the compositor:
 //               (u, v, conic a, conic b) (conic c, o~, z, hx) (r, g, b, hy)
 //               hx, hy: guarded half extents of the footprint box in pixels
+//     ell[m]    2 x float4: the footprint ellipse in tile-row form
 //     rect[m]   tile rectangle, packed (tx0 | ty0 << 16, tx1 | ty1 << 16)
+//     vis_cnt[m] tiles of the rectangle that the footprint ellipse meets
 //   pairs     (tile, m) pairs sorted by (tile, depth, gid)             [K]
 //   ranges    [start, end) into the pairs per global tile             [tiles]
 //   pixels    final transmittance and last blended list position      [sum HW]
@@ -84,6 +86,7 @@ struct Params {
     uint32_t *inv;           // [NV] depth position of each item, 0xffffffff if not visible
     uint32_t *szkey;         // [M]
     float4 *rec;             // [M*3]
+    float4 *ell;             // [M*2] footprint ellipses (store_ellipse)
     uint2 *rect;             // [M]
     uint32_t *vis_cnt;       // [M] tiles per visible item
     uint32_t *vis_off;       // [M] first pair position of the item
@@ -140,6 +143,113 @@ __device__ __forceinline__ void record_terms(const float4 *rec, uint32_t m, floa
     s0 = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
     s1 = make_float2(-0.5f * kLog2e * b.x, b.y);
     s2 = make_float4(c.x, c.y, c.z, b.z);
+}
+
+// Kahan's difference of products a*b - c*d, accurate to a few ulp.
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
+// Footprint of a record in one tile row.  The compositor blends a record at
+// a pixel only where o~ G >= 1/255, i.e. where the pixel centre's offset d
+// from (u, v) lies in the ellipse a dx^2 + 2 b dx dy + c dy^2 <= Q with
+// Q = 2 ln(255 o~) (conic a b c).  Of the bounding rectangle's tiles, those
+// of row ty whose pixel centres can reach that ellipse are the columns
+// [c0, c1) returned here, computed for the widened level Q' = 1.01 Q + 1e-4
+// and pixel-centre bands widened by 0.1 px: the widening covers the
+// rounding of the compositor's own evaluation of the quadratic form, which
+// for conics with (a + c)^2 > 1e4 (ac - b^2) (needle footprints, relative
+// error above 0.4 %) is not assured: there the whole rectangle row is kept.
+//   In a band of offsets y in [lo, hi] the left edge of the ellipse,
+// x(y) = (-b y - sqrt(a Q' - D y^2)) / a with D = ac - b^2, is convex with
+// its minimum at y_l = b sqrt(Q' / (c D)) (the right edge is concave with
+// its maximum at -y_l), so the band's span is the edges evaluated at those
+// points clamped into the band.  The tile count of a record (finalize pass)
+// and the pair expansion both call this on the same stored floats, with
+// explicitly rounded or hardware-approximate operations only, so the two
+// agree bit for bit; the approximations' relative errors (a few ulp) are
+// far inside the widening.
+struct FootprintEllipse {
+    float u, v, b, ia, aQ, D, ym, yl;
+    bool exact;  // false: keep whole rectangle rows
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ FootprintEllipse footprint_ellipse(float u, float v, float a, float b, float c,
+                                                              float ot) {
+    // Q' = 1.01 * 2 ln(255 o~) + 1e-4 = 1.01 * 2 ln(2) log2(255 o~) + 1e-4
+    const float Q = fmaxf(__fmul_rn(2.0f * 0.6931471805599453f, lg2_approx(__fmul_rn(255.0f, ot))), 0.0f);
+    const float Qp = __fadd_rn(__fmul_rn(1.01f, Q), 1e-4f);
+    FootprintEllipse E;
+    E.u = u; E.v = v; E.b = b;
+    E.D = diff_of_products(a, c, b, b);
+    const float tr = __fadd_rn(a, c);
+    E.exact = E.D > 0.0f && a > 0.0f && c > 0.0f && __fmul_rn(tr, tr) <= __fmul_rn(1e4f, E.D);
+    const float iD = E.exact ? __frcp_rn(E.D) : 0.0f;
+    E.ia = E.exact ? __frcp_rn(a) : 0.0f;
+    E.exact = E.exact && E.ia > 0.0f;  // the stored form's flag
+    if (!E.exact) E.ia = 0.0f;
+    E.aQ = __fmul_rn(a, Qp);
+    E.ym = sqrt_approx(__fmul_rn(E.aQ, iD));
+    E.yl = __fmul_rn(b, sqrt_approx(__fmul_rn(Qp, __fmul_rn(iD, E.exact ? __frcp_rn(c) : 0.0f))));
+    return E;
+}
+
+// The ellipse as stored per visible item (the finalize pass writes it and
+// counts the tiles with the values it writes; the pair expansion reads it
+// back), !exact encoded as ia = 0.
+__device__ __forceinline__ void store_ellipse(float4 *ell, uint32_t m, const FootprintEllipse &E) {
+    ell[2 * (size_t)m] = make_float4(E.u, E.v, E.b, E.ia);
+    ell[2 * (size_t)m + 1] = make_float4(E.aQ, E.D, E.ym, E.yl);
+}
+
+__device__ __forceinline__ FootprintEllipse load_ellipse(const float4 *ell, uint32_t m) {
+    const float4 p = ell[2 * (size_t)m], q = ell[2 * (size_t)m + 1];
+    FootprintEllipse E;
+    E.u = p.x; E.v = p.y; E.b = p.z; E.ia = p.w;
+    E.aQ = q.x; E.D = q.y; E.ym = q.z; E.yl = q.w;
+    E.exact = p.w > 0.0f;
+    return E;
+}
+
+// Columns [c0, c1) of tile row ty (tiles TW x TH, TW a power of two) within
+// [tx0, tx1).
+__device__ __forceinline__ uint2 footprint_cols(const FootprintEllipse &E, uint32_t ty, int TW, int TH,
+                                                uint32_t tx0, uint32_t tx1) {
+    if (!E.exact) return make_uint2(tx0, tx1);
+    constexpr float kPad = 0.1f;
+    // offsets of the row's pixel centres, py + 0.5 - v for py in [ty TH, (ty + 1) TH)
+    const float lo = fmaxf(__fsub_rn((float)(ty * TH) + (0.5f - kPad), E.v), -E.ym);
+    const float hi = fminf(__fsub_rn((float)((ty + 1) * TH) - (0.5f - kPad), E.v), E.ym);
+    if (!(lo <= hi)) return make_uint2(tx0, tx0);
+    const float yl = fminf(fmaxf(E.yl, lo), hi);
+    const float yr = fminf(fmaxf(-E.yl, lo), hi);
+    const float wl = sqrt_approx(fmaxf(__fsub_rn(E.aQ, __fmul_rn(E.D, __fmul_rn(yl, yl))), 0.0f));
+    const float wr = sqrt_approx(fmaxf(__fsub_rn(E.aQ, __fmul_rn(E.D, __fmul_rn(yr, yr))), 0.0f));
+    const float xl = __fmul_rn(__fsub_rn(__fmul_rn(-E.b, yl), wl), E.ia);
+    const float xr = __fmul_rn(__fadd_rn(__fmul_rn(-E.b, yr), wr), E.ia);
+    // pixel columns px with px + 0.5 - u in [xl - pad, xr + pad]
+    const float p0 = ceilf(__fadd_rn(__fsub_rn(E.u, 0.5f + kPad), xl));
+    const float p1 = floorf(__fadd_rn(__fadd_rn(E.u, kPad - 0.5f), xr));
+    const float inv_w = __frcp_rn((float)TW);  // exact for a power of two
+    const float c0 = fmaxf(floorf(__fmul_rn(p0, inv_w)), (float)tx0);
+    const float c1 = fminf(__fadd_rn(floorf(__fmul_rn(p1, inv_w)), 1.0f), (float)tx1);
+    if (!(c0 < c1)) return make_uint2(tx0, tx0);
+    return make_uint2((uint32_t)c0, (uint32_t)c1);
 }
 
 // 1/x on the SFU (PTX rcp.approx.ftz.f32, within 1 ulp); the adjoints use it

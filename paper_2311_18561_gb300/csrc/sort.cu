@@ -9,7 +9,8 @@
 //      their camera depth (4 digit passes over M items; the items start in
 //      gid order and the sort is stable, so equal depths keep gid order);
 //   2. each item, in that depth order, emits one (tile id, depth position)
-//      pair per covered tile, and the K pairs are sorted stably by tile id
+//      pair per tile its footprint ellipse meets, and the K pairs are
+//      sorted stably by tile id
 //      alone (ceil(log2 tiles) bits, 2-3 passes).
 // The result is ordered by (tile, depth, gid) -- the per-tile front-to-back
 // lists -- while the wide K-sized sort only moves the tile bits.
@@ -38,6 +39,9 @@ constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
 
 constexpr uint32_t kEmitChunk = 2048;  // pair outputs per expansion chunk
 constexpr int kEmitThreads = 256;
+static_assert(kEmitChunk % kEmitThreads == 0, "whole warps per expansion pass");
+constexpr uint32_t kWalkRows = 3;  // items with more tile rows: warp-cooperative row search
+constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -226,11 +230,14 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, uint32_t *t
 // Expansion of the sorted visible items into (tile id, depth position)
 // pairs: one thread per output pair, chunks of kEmitChunk outputs; the
 // item of output j is the last m with vis_off[m] <= j, searched among the
-// chunk's items staged in shared memory.
+// chunk's items staged in shared memory.  Its r-th pair is the r-th tile,
+// row by row, of the rectangle tiles that its footprint ellipse meets (the
+// rows the finalize pass counted, recomputed from the ellipse it stored).
 __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *__restrict__ vis_off,
                                                               const uint32_t *__restrict__ chunk_start,
                                                               const uint2 *__restrict__ rect,
-                                                              const uint32_t *__restrict__ sgid,
+                                                              const float4 *__restrict__ ell, int tile_w,
+                                                              int tile_h, const uint32_t *__restrict__ sgid,
                                                               const ViewDesc *views, int nv, const uint32_t *d_m,
                                                               const uint32_t *d_k, uint32_t capacity,
                                                               uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
@@ -248,25 +255,103 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
         if (staged)
             for (uint32_t q = threadIdx.x; q < span; q += kEmitThreads) s_off[q] = vis_off[m_lo + q];
         __syncthreads();
+        // whole warps iterate together (kEmitChunk is a multiple of the
+        // block), so the warp-wide steps below see all 32 lanes
         for (uint32_t q = threadIdx.x; q < kEmitChunk; q += kEmitThreads) {
             const uint32_t j = j0 + q;
-            if (j >= K) break;
-            // last m in [m_lo, m_hi] with vis_off[m] <= j
-            uint32_t lo = 0, hi = span - 1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                const uint32_t o = staged ? s_off[mid] : vis_off[m_lo + mid];
-                if (o <= j) lo = mid; else hi = mid - 1;
+            const bool valid = j < K;
+            if (!__any_sync(kFull, valid)) break;
+            uint32_t m = m_lo, r = 0;
+            if (valid) {
+                // last m in [m_lo, m_hi] with vis_off[m] <= j
+                uint32_t lo = 0, hi = span - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    const uint32_t o = staged ? s_off[mid] : vis_off[m_lo + mid];
+                    if (o <= j) lo = mid; else hi = mid - 1;
+                }
+                m = m_lo + lo;
+                r = j - (staged ? s_off[lo] : vis_off[m]);
             }
-            const uint32_t m = m_lo + lo;
-            const uint32_t r = j - (staged ? s_off[lo] : vis_off[m]);
             const uint2 rc = rect[m];
-            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu;
-            const uint32_t w = tx1 - tx0;
-            const uint32_t ty = ty0 + r / w, tx = tx0 + r % w;
-            const int view = nv == 1 ? 0 : view_of_item(views, nv, sgid[m]);
-            keys[j] = views[view].tile_base + ty * (uint32_t)views[view].tiles_x + tx;
-            vals[j] = m;
+            const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu, ty1 = rc.y >> 16;
+            const FootprintEllipse E = load_ellipse(ell, m);
+            // the row holding pair r (the rows sum to the item's count, so
+            // the search ends inside the rectangle; its first tile otherwise)
+            uint32_t tx = tx0, ty = ty0;
+            const bool coop = valid && ty1 - ty0 > kWalkRows;
+            if (valid && !coop) {  // short items: each lane walks its rows
+                for (uint32_t row = ty0; row < ty1; row++) {
+                    const uint2 c = footprint_cols(E, row, tile_w, tile_h, tx0, tx1);
+                    if (r < c.y - c.x) {
+                        tx = c.x + r;
+                        ty = row;
+                        break;
+                    }
+                    r -= c.y - c.x;
+                }
+            }
+            // tall items, one at a time: the warp evaluates 32 rows at once,
+            // scans their spans and each of the item's lanes finds its row
+            // by binary search over the inclusive sums
+            uint32_t pending = __ballot_sync(kFull, coop);
+            while (pending) {
+                const int L = __ffs(pending) - 1;
+                // every lane takes part in every shuffle (none sits behind
+                // a short-circuit or a branch)
+                const uint32_t mL = __shfl_sync(kFull, m, L);
+                const bool mine = coop && m == mL;
+                FootprintEllipse EL;
+                EL.u = __shfl_sync(kFull, E.u, L);
+                EL.v = __shfl_sync(kFull, E.v, L);
+                EL.b = __shfl_sync(kFull, E.b, L);
+                EL.ia = __shfl_sync(kFull, E.ia, L);
+                EL.aQ = __shfl_sync(kFull, E.aQ, L);
+                EL.D = __shfl_sync(kFull, E.D, L);
+                EL.ym = __shfl_sync(kFull, E.ym, L);
+                EL.yl = __shfl_sync(kFull, E.yl, L);
+                EL.exact = __shfl_sync(kFull, (int)E.exact, L) != 0;
+                const uint32_t ltx0 = __shfl_sync(kFull, tx0, L), ltx1 = __shfl_sync(kFull, tx1, L);
+                const uint32_t lty0 = __shfl_sync(kFull, ty0, L), lty1 = __shfl_sync(kFull, ty1, L);
+                bool todo = mine;
+                uint32_t base = 0;
+                for (uint32_t row0 = lty0; row0 < lty1; row0 += 32) {
+                    const uint32_t row = row0 + (threadIdx.x & 31);
+                    uint32_t cx = 0, sp = 0;
+                    if (row < lty1) {
+                        const uint2 c = footprint_cols(EL, row, tile_w, tile_h, ltx0, ltx1);
+                        cx = c.x;
+                        sp = c.y - c.x;
+                    }
+                    uint32_t inc = sp;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+                        if ((int)(threadIdx.x & 31) >= o) inc += t;
+                    }
+                    const uint32_t total = __shfl_sync(kFull, inc, 31);
+                    const uint32_t rr = r - base;  // used only while todo (then r >= base)
+                    uint32_t k = 0;  // first lane whose inclusive sum exceeds rr
+#pragma unroll
+                    for (int step = 16; step; step >>= 1)
+                        if (__shfl_sync(kFull, inc, k + step - 1) <= rr) k += step;
+                    const uint32_t inc_k = __shfl_sync(kFull, inc, k), sp_k = __shfl_sync(kFull, sp, k);
+                    const uint32_t cx_k = __shfl_sync(kFull, cx, k);
+                    if (todo && rr < total) {
+                        ty = row0 + k;
+                        tx = cx_k + rr - (inc_k - sp_k);
+                        todo = false;
+                    }
+                    base += total;
+                    if (!__any_sync(kFull, todo)) break;
+                }
+                pending &= ~__ballot_sync(kFull, mine);
+            }
+            if (valid) {
+                const int view = nv == 1 ? 0 : view_of_item(views, nv, sgid[m]);
+                keys[j] = views[view].tile_base + ty * (uint32_t)views[view].tiles_x + tx;
+                vals[j] = m;
+            }
         }
     }
 }
@@ -450,7 +535,8 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     if (grid < 1) grid = 1;
     if (grid > 152 * 8) grid = 152 * 8;
     note_launch();
-    k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.chunk_start, p.rect, p.sgid, p.views, p.n_views,
+    k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.chunk_start, p.rect, p.ell, p.tile_w, p.tile_h,
+                                                 p.sgid, p.views, p.n_views,
                                                  &p.counters[0], &p.counters[1], p.pair_capacity, p.pair_keys,
                                                  p.pair_vals);
 }

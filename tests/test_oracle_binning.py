@@ -49,3 +49,39 @@ def test_pairs_are_a_permutation_and_sorted():
         keys = [(zb[int(g)], int(g)) for g in values[s:e]]
         assert keys == sorted(keys)
     assert ranges[-1, 1] == values.size
+
+
+def test_contributing_tiles_of_a_disc():
+    """A circular Gaussian (conic I / s^2) is blended inside the disc of
+    radius s sqrt(2 ln(255 o~)) (closed form); its tiles are those holding a
+    pixel centre within that radius, found here by a plain loop."""
+    s, o = 3.0, 0.6
+    r = s * np.sqrt(2.0 * np.log(255.0 * o))
+    W, H, tw, th = 37, 29, 8, 4
+    for (u, v) in [(10.3, 12.7), (0.0, 0.0), (36.9, 3.2), (20.0, 28.5)]:
+        want = set()
+        for py in range(H):
+            for px in range(W):
+                if (px + 0.5 - u) ** 2 + (py + 0.5 - v) ** 2 <= r * r * (1 - 1e-12):
+                    want.add((py // th) * ((W + tw - 1) // tw) + px // tw)
+        got = binning.contributing_tiles([[u, v]], [[1 / s**2, 0.0, 1 / s**2]], [o], W, H, tw, th)[0]
+        assert got == want, (u, v)
+    # below the skip threshold nothing is blended
+    assert binning.contributing_tiles([[5, 5]], [[1, 0, 1]], [1 / 255.0], 16, 16, 8, 8)[0] == set()
+
+
+def test_contributing_tiles_of_a_sheared_ellipse():
+    """An anisotropic conic: a pixel centre is in the footprint iff its
+    offset's quadratic form is under the level, checked per pixel."""
+    a, b, c, o = 0.05, 0.04, 0.08, 0.9
+    level = 2 * np.log(255 * o)
+    W, H, tw, th = 40, 30, 16, 8
+    u, v = 17.2, 14.9
+    want = set()
+    for py in range(H):
+        for px in range(W):
+            dx, dy = px + 0.5 - u, py + 0.5 - v
+            if a * dx * dx + 2 * b * dx * dy + c * dy * dy <= level:
+                want.add((py // th) * 3 + px // tw)
+    got = binning.contributing_tiles([[u, v]], [[a, b, c]], [o], W, H, tw, th)[0]
+    assert got == want and len(want) < 3 * 4
