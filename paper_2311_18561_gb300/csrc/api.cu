@@ -162,6 +162,7 @@ struct pvg_frame {
     DevBuf inv;                 // [NV] depth position per item
     DevBuf rec;                 // [NV * 3] float4
     DevBuf ell;                 // [NV * 2] float4 footprint ellipses
+    DevBuf rowtab;              // [NV] uint4 packed tile rows
     DevBuf rect, vis_cnt;       // [NV]
     DevBuf pair_vals;           // [K]
     DevBuf ranges;              // [tiles]
@@ -265,7 +266,7 @@ extern "C" pvg_status_t pvg_frame_create(pvg_frame_t **frame) {
 extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
-    for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->ell, &f->rect, &f->vis_cnt, &f->pair_vals,
+    for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->ell, &f->rowtab, &f->rect, &f->vis_cnt, &f->pair_vals,
                       &f->ranges, &f->tile_order, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d, &f->gfeat})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
@@ -517,6 +518,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     PVG_TRY(ensure_c(f->szkey, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(f->rec, sizeof(float4) * 3 * (size_t)NV, capturing));
     PVG_TRY(ensure_c(f->ell, sizeof(float4) * 2 * (size_t)NV, capturing));
+    PVG_TRY(ensure_c(f->rowtab, sizeof(uint4) * (size_t)NV, capturing));
     PVG_TRY(ensure_c(f->rect, sizeof(uint2) * NV, capturing));
     PVG_TRY(ensure_c(f->vis_cnt, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(f->ranges, sizeof(uint2) * tiles, capturing));
@@ -574,6 +576,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     p.szkey = ptr<uint32_t>(f->szkey);
     p.rec = ptr<float4>(f->rec);
     p.ell = ptr<float4>(f->ell);
+    p.rowtab = ptr<uint4>(f->rowtab);
     p.rect = ptr<uint2>(f->rect);
     p.vis_cnt = ptr<uint32_t>(f->vis_cnt);
     p.ranges = ptr<uint2>(f->ranges);

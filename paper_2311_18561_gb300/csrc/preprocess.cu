@@ -87,12 +87,20 @@ __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
         P.rect[m] = make_uint2(F.tx0 | (F.ty0 << 16), F.tx1 | (F.ty1 << 16));
         // tiles of the rectangle that the footprint ellipse meets
         const FootprintEllipse E = footprint_ellipse(F.u, F.v, F.ca, F.cb, F.cc, F.ot);
-        store_ellipse(P.ell, m, E);
-        uint32_t cnt = 0;
+        const bool tab = has_row_table(F.tx0, F.ty0, F.tx1, F.ty1);
+        if (!tab) store_ellipse(P.ell, m, E);  // the expansion recomputes these rows
+        uint32_t cnt = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0;
         for (uint32_t ty = F.ty0; ty < F.ty1; ty++) {
             const uint2 c = footprint_cols(E, ty, P.tile_w, P.tile_h, F.tx0, F.tx1);
             cnt += c.y - c.x;
+            const uint32_t i = ty - F.ty0;
+            const uint32_t v = ((c.x - F.tx0) | ((c.y - c.x) << 8)) << (16 * (i & 1));
+            w0 |= i >> 1 == 0 ? v : 0u;
+            w1 |= i >> 1 == 1 ? v : 0u;
+            w2 |= i >> 1 == 2 ? v : 0u;
+            w3 |= i >> 1 == 3 ? v : 0u;
         }
+        if (tab) P.rowtab[m] = make_uint4(w0, w1, w2, w3);
         P.vis_cnt[m] = cnt;
     }
 }

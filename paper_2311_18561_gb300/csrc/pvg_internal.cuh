@@ -8,7 +8,10 @@
 //     rec[m]    3 x float4 record read by the compositor:
 //               (u, v, conic a, conic b) (conic c, o~, z, hx) (r, g, b, hy)
 //               hx, hy: guarded half extents of the footprint box in pixels
-//     ell[m]    2 x float4: the footprint ellipse in tile-row form
+//     rowtab[m] tiles of the footprint ellipse row by row, packed (items
+//               of <= 8 rows x 255 columns)
+//     ell[m]    2 x float4: the footprint ellipse in tile-row form (the
+//               other items)
 //     rect[m]   tile rectangle, packed (tx0 | ty0 << 16, tx1 | ty1 << 16)
 //     vis_cnt[m] tiles of the rectangle that the footprint ellipse meets
 //   pairs     (tile, m) pairs sorted by (tile, depth, gid)             [K]
@@ -87,6 +90,7 @@ struct Params {
     uint32_t *szkey;         // [M]
     float4 *rec;             // [M*3]
     float4 *ell;             // [M*2] footprint ellipses (store_ellipse)
+    uint4 *rowtab;           // [M] packed tile-row spans (has_row_table)
     uint2 *rect;             // [M]
     uint32_t *vis_cnt;       // [M] tiles per visible item
     uint32_t *vis_off;       // [M] first pair position of the item
@@ -209,9 +213,9 @@ __device__ __forceinline__ FootprintEllipse footprint_ellipse(float u, float v, 
     return E;
 }
 
-// The ellipse as stored per visible item (the finalize pass writes it and
-// counts the tiles with the values it writes; the pair expansion reads it
-// back), !exact encoded as ia = 0.
+// The ellipse as stored per visible item without a row table (the finalize
+// pass writes it and counts the tiles with the values it writes; the pair
+// expansion reads it back), !exact encoded as ia = 0.
 __device__ __forceinline__ void store_ellipse(float4 *ell, uint32_t m, const FootprintEllipse &E) {
     ell[2 * (size_t)m] = make_float4(E.u, E.v, E.b, E.ia);
     ell[2 * (size_t)m + 1] = make_float4(E.aQ, E.D, E.ym, E.yl);
@@ -224,6 +228,15 @@ __device__ __forceinline__ FootprintEllipse load_ellipse(const float4 *ell, uint
     E.aQ = q.x; E.D = q.y; E.ym = q.z; E.yl = q.w;
     E.exact = p.w > 0.0f;
     return E;
+}
+
+// Row table of an item whose rectangle has at most kTabRows rows and 255
+// columns: row i's (c0 - tx0) | (c1 - c0) << 8 in bits [16 (i & 1), +16) of
+// word i >> 1.
+constexpr uint32_t kTabRows = 8;
+
+__device__ __forceinline__ bool has_row_table(uint32_t tx0, uint32_t ty0, uint32_t tx1, uint32_t ty1) {
+    return ty1 - ty0 <= kTabRows && tx1 - tx0 <= 255u;
 }
 
 // Columns [c0, c1) of tile row ty (tiles TW x TH, TW a power of two) within

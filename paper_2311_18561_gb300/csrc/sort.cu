@@ -40,7 +40,6 @@ constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
 constexpr uint32_t kEmitChunk = 2048;  // pair outputs per expansion chunk
 constexpr int kEmitThreads = 256;
 static_assert(kEmitChunk % kEmitThreads == 0, "whole warps per expansion pass");
-constexpr uint32_t kWalkRows = 3;  // items with more tile rows: warp-cooperative row search
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -228,20 +227,28 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, uint32_t *t
 }
 
 // Expansion of the sorted visible items into (tile id, depth position)
-// pairs: one thread per output pair, chunks of kEmitChunk outputs; the
-// item of output j is the last m with vis_off[m] <= j, searched among the
-// chunk's items staged in shared memory.  Its r-th pair is the r-th tile,
-// row by row, of the rectangle tiles that its footprint ellipse meets (the
-// rows the finalize pass counted, recomputed from the ellipse it stored).
+// pairs, one chunk of kEmitChunk outputs at a time.  The item of every
+// output comes from a block max-scan of start markers (each item whose
+// first output falls in the chunk marks that slot with its m; the scan
+// carries the last mark forward).  Its r-th pair is the r-th tile, row by
+// row, of the rectangle tiles that its footprint ellipse meets: read from
+// the item's packed row table when it has one (at most kTabRows rows),
+// else recomputed from the stored ellipse, 32 rows at a time by the whole
+// warp, for one such item after another.
 __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *__restrict__ vis_off,
+                                                              const uint32_t *__restrict__ vis_cnt,
                                                               const uint32_t *__restrict__ chunk_start,
                                                               const uint2 *__restrict__ rect,
+                                                              const uint4 *__restrict__ rowtab,
                                                               const float4 *__restrict__ ell, int tile_w,
                                                               int tile_h, const uint32_t *__restrict__ sgid,
                                                               const ViewDesc *views, int nv, const uint32_t *d_m,
                                                               const uint32_t *d_k, uint32_t capacity,
                                                               uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    __shared__ uint32_t s_off[kEmitChunk + 1];
+    constexpr int kPer = kEmitChunk / kEmitThreads;  // slots per thread in the scan
+    __shared__ uint32_t s_item[kEmitChunk];
+    __shared__ uint32_t s_warp[kEmitThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t M = *d_m;
     const uint32_t K = min(*d_k, capacity);
     const uint32_t nchunks = (K + kEmitChunk - 1) / kEmitChunk;
@@ -249,11 +256,40 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
         const uint32_t j0 = c * kEmitChunk;
         const uint32_t m_lo = chunk_start[c];
         const uint32_t m_hi = (c + 1 < nchunks) ? chunk_start[c + 1] : M - 1;
-        const uint32_t span = m_hi - m_lo + 1;
-        const bool staged = span <= kEmitChunk + 1;
         __syncthreads();
-        if (staged)
-            for (uint32_t q = threadIdx.x; q < span; q += kEmitThreads) s_off[q] = vis_off[m_lo + q];
+        for (int q = threadIdx.x; q < (int)kEmitChunk; q += kEmitThreads) s_item[q] = 0u;
+        __syncthreads();
+        // marks: slot 0 holds the item containing j0 (chunk_start); a
+        // non-empty item starting inside the chunk marks its first slot
+        // (distinct slots: non-empty items start at distinct offsets)
+        if (threadIdx.x == 0) s_item[0] = m_lo;
+        for (uint32_t m = m_lo + threadIdx.x; m <= m_hi; m += kEmitThreads) {
+            const uint32_t o = vis_off[m];
+            if (o >= j0 && o - j0 < kEmitChunk && vis_cnt[m] > 0u) s_item[o - j0] = m;
+        }
+        __syncthreads();
+        // inclusive max-scan of the marks: kPer consecutive slots per
+        // thread, then across the warp, then across the warps
+        uint32_t loc[kPer];
+        uint32_t run = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; i++) {
+            run = max(run, s_item[threadIdx.x * kPer + i]);
+            loc[i] = run;
+        }
+        uint32_t wrun = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, wrun, o);
+            if (lane >= o) wrun = max(wrun, y);
+        }
+        if (lane == 31) s_warp[warp] = wrun;
+        uint32_t before = __shfl_up_sync(kFull, wrun, 1);
+        if (lane == 0) before = 0;
+        __syncthreads();
+        for (int w = 0; w < warp; w++) before = max(before, s_warp[w]);
+#pragma unroll
+        for (int i = 0; i < kPer; i++) s_item[threadIdx.x * kPer + i] = max(loc[i], before);
         __syncthreads();
         // whole warps iterate together (kEmitChunk is a multiple of the
         // block), so the warp-wide steps below see all 32 lanes
@@ -261,80 +297,61 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
             const uint32_t j = j0 + q;
             const bool valid = j < K;
             if (!__any_sync(kFull, valid)) break;
-            uint32_t m = m_lo, r = 0;
-            if (valid) {
-                // last m in [m_lo, m_hi] with vis_off[m] <= j
-                uint32_t lo = 0, hi = span - 1;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    const uint32_t o = staged ? s_off[mid] : vis_off[m_lo + mid];
-                    if (o <= j) lo = mid; else hi = mid - 1;
-                }
-                m = m_lo + lo;
-                r = j - (staged ? s_off[lo] : vis_off[m]);
-            }
+            const uint32_t m = valid ? s_item[q] : m_lo;
+            uint32_t r = valid ? j - vis_off[m] : 0u;
             const uint2 rc = rect[m];
             const uint32_t tx0 = rc.x & 0xffffu, ty0 = rc.x >> 16, tx1 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-            const FootprintEllipse E = load_ellipse(ell, m);
-            // the row holding pair r (the rows sum to the item's count, so
-            // the search ends inside the rectangle; its first tile otherwise)
-            uint32_t tx = tx0, ty = ty0;
-            const bool coop = valid && ty1 - ty0 > kWalkRows;
-            if (valid && !coop) {  // short items: each lane walks its rows
-                for (uint32_t row = ty0; row < ty1; row++) {
-                    const uint2 c = footprint_cols(E, row, tile_w, tile_h, tx0, tx1);
-                    if (r < c.y - c.x) {
-                        tx = c.x + r;
-                        ty = row;
+            uint32_t tx = tx0, ty = ty0;  // the rows sum to the item's count; first tile otherwise
+            const bool tab = has_row_table(tx0, ty0, tx1, ty1);
+            if (valid && tab) {
+                const uint4 t = rowtab[m];
+                const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int i = 0; i < (int)kTabRows; i++) {
+                    if (ty0 + i >= ty1) break;
+                    const uint32_t v = (w[i >> 1] >> (16 * (i & 1))) & 0xffffu;
+                    const uint32_t sp = v >> 8;
+                    if (r < sp) {
+                        tx = tx0 + (v & 0xffu) + r;
+                        ty = ty0 + i;
                         break;
                     }
-                    r -= c.y - c.x;
+                    r -= sp;
                 }
             }
-            // tall items, one at a time: the warp evaluates 32 rows at once,
-            // scans their spans and each of the item's lanes finds its row
-            // by binary search over the inclusive sums
+            // items without a table, one at a time: the warp evaluates 32
+            // rows at once, scans their spans and each of the item's lanes
+            // finds its row by binary search over the inclusive sums.  Every
+            // lane takes part in every shuffle (none sits behind a branch or
+            // a short-circuit).
+            const bool coop = valid && !tab;
             uint32_t pending = __ballot_sync(kFull, coop);
             while (pending) {
                 const int L = __ffs(pending) - 1;
-                // every lane takes part in every shuffle (none sits behind
-                // a short-circuit or a branch)
                 const uint32_t mL = __shfl_sync(kFull, m, L);
                 const bool mine = coop && m == mL;
-                FootprintEllipse EL;
-                EL.u = __shfl_sync(kFull, E.u, L);
-                EL.v = __shfl_sync(kFull, E.v, L);
-                EL.b = __shfl_sync(kFull, E.b, L);
-                EL.ia = __shfl_sync(kFull, E.ia, L);
-                EL.aQ = __shfl_sync(kFull, E.aQ, L);
-                EL.D = __shfl_sync(kFull, E.D, L);
-                EL.ym = __shfl_sync(kFull, E.ym, L);
-                EL.yl = __shfl_sync(kFull, E.yl, L);
-                EL.exact = __shfl_sync(kFull, (int)E.exact, L) != 0;
-                const uint32_t ltx0 = __shfl_sync(kFull, tx0, L), ltx1 = __shfl_sync(kFull, tx1, L);
-                const uint32_t lty0 = __shfl_sync(kFull, ty0, L), lty1 = __shfl_sync(kFull, ty1, L);
+                const FootprintEllipse EL = load_ellipse(ell, mL);
+                const uint2 rl = rect[mL];
+                const uint32_t ltx0 = rl.x & 0xffffu, lty0 = rl.x >> 16, ltx1 = rl.y & 0xffffu, lty1 = rl.y >> 16;
                 bool todo = mine;
                 uint32_t base = 0;
                 for (uint32_t row0 = lty0; row0 < lty1; row0 += 32) {
-                    const uint32_t row = row0 + (threadIdx.x & 31);
+                    const uint32_t row = row0 + lane;
                     uint32_t cx = 0, sp = 0;
                     if (row < lty1) {
-                        const uint2 c = footprint_cols(EL, row, tile_w, tile_h, ltx0, ltx1);
-                        cx = c.x;
-                        sp = c.y - c.x;
+                        const uint2 cc = footprint_cols(EL, row, tile_w, tile_h, ltx0, ltx1);
+                        cx = cc.x;
+                        sp = cc.y - cc.x;
                     }
-                    uint32_t inc = sp;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                        if ((int)(threadIdx.x & 31) >= o) inc += t;
-                    }
+                    const uint32_t inc = warp_incl_scan(sp);
                     const uint32_t total = __shfl_sync(kFull, inc, 31);
                     const uint32_t rr = r - base;  // used only while todo (then r >= base)
                     uint32_t k = 0;  // first lane whose inclusive sum exceeds rr
 #pragma unroll
-                    for (int step = 16; step; step >>= 1)
-                        if (__shfl_sync(kFull, inc, k + step - 1) <= rr) k += step;
+                    for (int step = 16; step; step >>= 1) {
+                        const uint32_t v = __shfl_sync(kFull, inc, k + step - 1);
+                        if (v <= rr) k += step;
+                    }
                     const uint32_t inc_k = __shfl_sync(kFull, inc, k), sp_k = __shfl_sync(kFull, sp, k);
                     const uint32_t cx_k = __shfl_sync(kFull, cx, k);
                     if (todo && rr < total) {
@@ -535,7 +552,8 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     if (grid < 1) grid = 1;
     if (grid > 152 * 8) grid = 152 * 8;
     note_launch();
-    k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.chunk_start, p.rect, p.ell, p.tile_w, p.tile_h,
+    k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.vis_cnt, p.chunk_start, p.rect, p.rowtab, p.ell,
+                                                 p.tile_w, p.tile_h,
                                                  p.sgid, p.views, p.n_views,
                                                  &p.counters[0], &p.counters[1], p.pair_capacity, p.pair_keys,
                                                  p.pair_vals);
