@@ -768,6 +768,7 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.pix_T = ptr<float>(f->pix_T);
     p.pix_last = ptr<uint32_t>(f->pix_last);
     p.g2d = ptr<float>(f->g2d);
+    for (const ViewDesc &d : views) p.aux |= (d.dl_depth || d.dl_alpha || d.sky) ? 1 : 0;
     if (feat_bwd) {
         p.feat_mask = f->feat_mask;
         p.n_feat = f->n_feat;

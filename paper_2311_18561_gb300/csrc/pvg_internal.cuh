@@ -106,6 +106,7 @@ struct Params {
     // backward
     float *g2d;              // [M*10] image-space gradients by depth position (u, v, conic a b c,
                              // o~, colour with the forward's clamp applied, z)
+    int32_t aux;             // backward: some view has depth / opacity-map gradients or a sky map
     // extra channels
     int32_t feat_mask;       // kFeat* bits (0: none)
     int32_t n_feat;          // F

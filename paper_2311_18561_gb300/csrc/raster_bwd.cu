@@ -10,8 +10,8 @@
 // so one scalar per pixel carries what the colour, depth and opacity
 // suffix sums would.  The 10 image-space gradient terms of an entry
 // (moments of dL/dpower for u, v, conic a b c; o~; r g b; z) are summed
-// over a thread's PX pixels, then over the warp by two transposing
-// butterflies (12 shuffles; afterwards lane s holds term s), added to
+// over a thread's PX pixels, then over the warp by transposing butterflies
+// (afterwards lane s holds term s), added to
 // per-CTA shared accumulators by 10 lanes at once, and reach global memory with one
 // atomic per (Gaussian, tile, term).  Alpha is the forward's expression
 // (explicit roundings), so the blend decisions are the forward's; the rest
@@ -21,13 +21,17 @@
 namespace pvg {
 namespace {
 
-// Sum of v[0..9] over the warp, as two transposing butterflies: terms 0..7
-// within groups of 8 lanes (4 + 2 + 1 exchanges, then two folds across the
-// groups) and terms 8, 9 between lane pairs (1 exchange, four folds).  On
-// return lane L holds in .x the total of term L & 7 and in .y that of term
-// 8 + (L & 1); lanes 0..9 therefore hold term L in .x (L < 8) or .y.
-// 12 shuffles and 44 instructions instead of one 16-slot butterfly's 62.
-__device__ __forceinline__ float2 warp_sum10(const float (&v)[10]) {
+// Sum of v[0..NT-1] (NT = 9 or 10) over the warp, as transposing
+// butterflies: terms 0..7 within groups of 8 lanes (4 + 2 + 1 exchanges,
+// then two folds across the groups); for NT = 10 terms 8, 9 between lane
+// pairs (1 exchange, four folds), for NT = 9 term 8 by a plain butterfly.
+// On return lane L holds in .x the total of term L & 7 and in .y that of
+// term 8 + (L & 1) (NT = 10) or term 8 (NT = 9); lanes 0..NT-1 therefore
+// hold term L in .x (L < 8) or .y.  12 shuffles and 44 instructions for
+// NT = 10 instead of one 16-slot butterfly's 62.
+template <int NT>
+__device__ __forceinline__ float2 warp_sum_terms(const float (&v)[10]) {
+    static_assert(NT == 9 || NT == 10, "9 or 10 terms");
     const int lane = threadIdx.x & 31;
     bool hi = lane & 4;
     float b[4];
@@ -47,9 +51,16 @@ __device__ __forceinline__ float2 warp_sum10(const float (&v)[10]) {
     float d = (hi ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, hi ? c[0] : c[1], 1);
     d += __shfl_xor_sync(0xffffffffu, d, 8);
     d += __shfl_xor_sync(0xffffffffu, d, 16);
-    float e = (hi ? v[9] : v[8]) + __shfl_xor_sync(0xffffffffu, hi ? v[8] : v[9], 1);
+    float e;
+    if constexpr (NT == 10) {
+        e = (hi ? v[9] : v[8]) + __shfl_xor_sync(0xffffffffu, hi ? v[8] : v[9], 1);
 #pragma unroll
-    for (int o = 2; o < 32; o <<= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        for (int o = 2; o < 32; o <<= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    } else {
+        e = v[8];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
     return make_float2(d, e);
 }
 
@@ -127,10 +138,14 @@ __device__ __forceinline__ void flush_entry(float *dst, const float *a, float ap
         if (gt[c] != 0.f) atomicAdd(dst + c, gt[c]);
 }
 
-template <int TW, int TH, int PX>
+// kAux: the call has depth or opacity-map gradients or a sky map (dL/dO
+// and the depth term of X can be non-zero); without them X = gC.c and the
+// depth term is not reduced (9 terms).
+template <int TW, int TH, int PX, bool kAux>
 __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
     constexpr int BLOCK = TW * TH / PX;
-    constexpr int NG = 10;
+    constexpr int NG = 10;               // shared accumulator stride
+    constexpr int NT = kAux ? 10 : 9;    // terms reduced
     __shared__ float4 s0[BLOCK];
     __shared__ float2 s1[BLOCK];
     __shared__ float4 s2[BLOCK];
@@ -173,9 +188,14 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
         __syncthreads();
         for (int k = cnt - 1; k >= 0; k--) {
             const uint32_t pos = start + k - r.x;  // list position
+            // gv: the entry's 10 terms over this thread's pixels.  All of
+            // them share dx, so the conic moments are kept as sum gpow
+            // (A0), sum gpow dy (gv[1]) and sum gpow dy^2 (gv[4]) and
+            // expanded once: m_x = dx A0, m_xx = dx^2 A0, m_xy = dx m_y.
             float gv[NG];
 #pragma unroll
             for (int c = 0; c < NG; c++) gv[c] = 0.f;
+            float A0 = 0.f;
             bool contrib = false;
             const float4 g = s0[k];
             const float2 q = s1[k];
@@ -194,30 +214,32 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
                 const float inv = rcp_approx(1.0f - alpha);
                 const float Ti = T[p] * inv;
                 const float w = alpha * Ti;
-                const float X = gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z + gD[p] * col.w + gO[p];
+                float X = gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z;
+                if constexpr (kAux) X += gD[p] * col.w + gO[p];
                 const float ga = Ti * X - inv * S[p];
                 gv[6] += gC0[p] * w;
                 gv[7] += gC1[p] * w;
                 gv[8] += gC2[p] * w;
-                gv[9] += gD[p] * w;
+                if constexpr (kAux) gv[9] += gD[p] * w;
                 if (raw <= kAlphaCap) {
                     // moments of gpow = dL/dpower (d alpha / d power = alpha);
                     // the conic is applied once per Gaussian in the flush
                     gv[5] += ga * G;
                     const float gpow = ga * alpha;
-                    const float mx = gpow * dx, my = gpow * dy;
-                    gv[0] += mx;
+                    const float my = gpow * dy;
+                    A0 += gpow;
                     gv[1] += my;
-                    gv[2] += mx * dx;
-                    gv[3] += mx * dy;
                     gv[4] += my * dy;
                 }
                 S[p] += X * w;
                 T[p] = Ti;
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float2 tot = warp_sum10(gv);
-                if (lane < NG) atomicAdd(&s_acc[k * NG + lane], lane < 8 ? tot.x : tot.y);
+                gv[0] = dx * A0;
+                gv[2] = dx * gv[0];
+                gv[3] = dx * gv[1];
+                const float2 tot = warp_sum_terms<NT>(gv);
+                if (lane < NT) atomicAdd(&s_acc[k * NG + lane], lane < 8 ? tot.x : tot.y);
             }
         }
         __syncthreads();
@@ -231,7 +253,10 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
 template <int TW, int TH, int PX>
 void launch_bwd_t(const Params &p, cudaStream_t s) {
     note_launch();
-    k_composite_bwd<TW, TH, PX><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+    if (p.aux)
+        k_composite_bwd<TW, TH, PX, true><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+    else
+        k_composite_bwd<TW, TH, PX, false><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
 }
 
 }  // namespace

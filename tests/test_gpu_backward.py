@@ -151,3 +151,23 @@ def test_backward_with_sky_cube_map():
     _compare_grads(grads, ref)
     g = grads["sky"].cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - ref["sky"]) <= 1e-3 * np.linalg.norm(ref["sky"])
+
+
+@pytest.mark.parametrize("cfg", [(16, 16, 1), (16, 32, 4), (32, 16, 2)])
+def test_backward_colour_only(cfg):
+    """Only dL/drgb given (no depth or opacity-map gradient, no sky): the
+    compositor adjoint's reduced form, against the oracle with zero depth
+    and opacity weights."""
+    scene = synth.make_fd_scene(seed=11, n=500, sh_degree=3)
+    cam = synth.fd_camera(64, 48, t=0.55)
+    cam["bg"] = np.array([0.3, 0.1, 0.6], np.float32)
+    H, W = cam["height"], cam["width"]
+    w_rgb, _, _ = _weights(H, W, 9)
+    r = R.Renderer(tile=cfg[:2], pixels_per_thread=cfg[2])
+    fr = R.Frame()
+    st = R.scene_to_device(scene)
+    r.forward(st, [cam], frame=fr)
+    grads = r.backward(st, [cam], fr, [dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"))])
+    torch.cuda.synchronize()
+    ref = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), np.zeros((H, W)), np.zeros((H, W)))
+    _compare_grads(grads, ref)
