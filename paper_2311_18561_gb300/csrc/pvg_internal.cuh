@@ -240,16 +240,16 @@ __device__ __forceinline__ bool has_row_table(uint32_t tx0, uint32_t ty0, uint32
     return ty1 - ty0 <= kTabRows && tx1 - tx0 <= 255u;
 }
 
-// Columns [c0, c1) of tile row ty (tiles TW x TH, TW a power of two) within
-// [tx0, tx1).
-__device__ __forceinline__ uint2 footprint_cols(const FootprintEllipse &E, uint32_t ty, int TW, int TH,
-                                                uint32_t tx0, uint32_t tx1) {
-    if (!E.exact) return make_uint2(tx0, tx1);
+// Pixel-centre columns [p0, p1] that the ellipse (widened by kPad) reaches
+// within the pixel rows [ylo, yhi) (integer-valued floats); false when the
+// rows miss it.  Only for E.exact.
+__device__ __forceinline__ bool footprint_span(const FootprintEllipse &E, float ylo, float yhi, float &p0,
+                                               float &p1) {
     constexpr float kPad = 0.1f;
-    // offsets of the row's pixel centres, py + 0.5 - v for py in [ty TH, (ty + 1) TH)
-    const float lo = fmaxf(__fsub_rn((float)(ty * TH) + (0.5f - kPad), E.v), -E.ym);
-    const float hi = fminf(__fsub_rn((float)((ty + 1) * TH) - (0.5f - kPad), E.v), E.ym);
-    if (!(lo <= hi)) return make_uint2(tx0, tx0);
+    // offsets of the rows' pixel centres, py + 0.5 - v for py in [ylo, yhi)
+    const float lo = fmaxf(__fsub_rn(ylo + (0.5f - kPad), E.v), -E.ym);
+    const float hi = fminf(__fsub_rn(yhi - (0.5f - kPad), E.v), E.ym);
+    if (!(lo <= hi)) return false;
     const float yl = fminf(fmaxf(E.yl, lo), hi);
     const float yr = fminf(fmaxf(-E.yl, lo), hi);
     const float wl = sqrt_approx(fmaxf(__fsub_rn(E.aQ, __fmul_rn(E.D, __fmul_rn(yl, yl))), 0.0f));
@@ -257,8 +257,18 @@ __device__ __forceinline__ uint2 footprint_cols(const FootprintEllipse &E, uint3
     const float xl = __fmul_rn(__fsub_rn(__fmul_rn(-E.b, yl), wl), E.ia);
     const float xr = __fmul_rn(__fadd_rn(__fmul_rn(-E.b, yr), wr), E.ia);
     // pixel columns px with px + 0.5 - u in [xl - pad, xr + pad]
-    const float p0 = ceilf(__fadd_rn(__fsub_rn(E.u, 0.5f + kPad), xl));
-    const float p1 = floorf(__fadd_rn(__fadd_rn(E.u, kPad - 0.5f), xr));
+    p0 = ceilf(__fadd_rn(__fsub_rn(E.u, 0.5f + kPad), xl));
+    p1 = floorf(__fadd_rn(__fadd_rn(E.u, kPad - 0.5f), xr));
+    return true;
+}
+
+// Columns [c0, c1) of tile row ty (tiles TW x TH, TW a power of two) within
+// [tx0, tx1).
+__device__ __forceinline__ uint2 footprint_cols(const FootprintEllipse &E, uint32_t ty, int TW, int TH,
+                                                uint32_t tx0, uint32_t tx1) {
+    if (!E.exact) return make_uint2(tx0, tx1);
+    float p0, p1;
+    if (!footprint_span(E, (float)(ty * TH), (float)((ty + 1) * TH), p0, p1)) return make_uint2(tx0, tx0);
     const float inv_w = __frcp_rn((float)TW);  // exact for a power of two
     const float c0 = fmaxf(floorf(__fmul_rn(p0, inv_w)), (float)tx0);
     const float c1 = fminf(__fadd_rn(floorf(__fmul_rn(p1, inv_w)), 1.0f), (float)tx1);
