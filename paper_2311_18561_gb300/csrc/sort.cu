@@ -32,7 +32,7 @@ constexpr int kMaxScanBlocks = 1024;
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 8;
+constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 constexpr int kRadix = 256;
 constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
@@ -417,7 +417,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
 #pragma unroll
         for (int j = 0; j < kSortItems; j++) {
             const uint32_t d = (key[j] >> shift) & mask;
-            const uint32_t peers = __match_any_sync(0xffffffffu, valid[j] ? d : 0xffffffffu);
+            uint32_t peers = __ballot_sync(0xffffffffu, valid[j]);
+#pragma unroll
+            for (int bit = 0; bit < 8; bit++) {
+                const bool on = (d >> bit) & 1u;
+                const uint32_t b = __ballot_sync(0xffffffffu, on);
+                peers &= on ? b : ~b;
+            }
             uint32_t before = 0;
             if (valid[j]) before = S.warp_hist[warp][d];
             __syncwarp();
@@ -463,13 +469,34 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
     }
 }
 
-__global__ void k_ranges(const uint32_t *keys, const uint32_t *d_k, uint32_t capacity, uint2 *ranges) {
-    uint32_t K = *d_k;
-    if (K > capacity) K = capacity;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
-        const uint32_t t = keys[j];
-        if (j == 0 || keys[j - 1] != t) ranges[t].x = j;
-        if (j == K - 1 || keys[j + 1] != t) ranges[t].y = j + 1;
+// [start, end) of every tile's run in the sorted keys.  Eight keys per
+// thread per sweep (two 16-byte loads and the two neighbours), so that
+// few dependent sweeps remain.
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_k,
+                                                uint32_t capacity, uint2 *__restrict__ ranges) {
+    constexpr uint32_t kNone = 0xffffffffu;  // no tile has this id
+    const uint32_t K = min(*d_k, capacity);
+    const uint32_t stride = gridDim.x * blockDim.x * 8u;
+    for (uint32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) * 8u; j0 < K; j0 += stride) {
+        uint32_t k[10];  // keys[j0 - 1 .. j0 + 8]
+        k[0] = j0 > 0 ? keys[j0 - 1] : kNone;
+        if (j0 + 8 <= K) {
+            const uint4 a = reinterpret_cast<const uint4 *>(keys + j0)[0];
+            const uint4 b = reinterpret_cast<const uint4 *>(keys + j0)[1];
+            k[1] = a.x; k[2] = a.y; k[3] = a.z; k[4] = a.w;
+            k[5] = b.x; k[6] = b.y; k[7] = b.z; k[8] = b.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; i++) k[1 + i] = j0 + i < K ? keys[j0 + i] : kNone;
+        }
+        k[9] = j0 + 8 < K ? keys[j0 + 8] : kNone;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint32_t t = k[1 + i];
+            if (t == kNone) break;
+            if (k[i] != t) ranges[t].x = j0 + i;
+            if (k[2 + i] != t) ranges[t].y = j0 + i + 1;
+        }
     }
 }
 
