@@ -5,7 +5,7 @@
 //                    EWA projection (Sec. 3.1, Eq. 2) and the tile
 //                    footprint; writes the tile count and depth bits of
 //                    every item.
-//   k_finalize       (stage a, pass 2) for every visible item, in item
+//   k_finalize       (stage a, pass 2) for every visible item, in gid
 //                    order: the same projection plus the SH colour; writes
 //                    the 48-byte compositing record, the tile rectangle and
 //                    the count of its tiles that the footprint ellipse
@@ -47,13 +47,15 @@ __global__ void __launch_bounds__(256) k_scatter_inv(Params P) {
         P.inv[P.sgid[m]] = m;
 }
 
-// Records in depth order, computed in item order (coalesced parameter
-// reads; the 48-byte record goes to its depth position m = inv[g]).
+// Records in depth order, computed over the visible items in gid order
+// (the compacted list: every lane has an item, parameter reads stay in gid
+// order; the 48-byte record goes to its depth position m = inv[g]).
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
     constexpr int K = (D + 1) * (D + 1);
-    const uint32_t n = P.n_items;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    const uint32_t M = P.counters[0];
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        const uint32_t g = P.vis_items[j];
         const uint32_t m = P.inv[g];
         if (m == 0xffffffffu) continue;
         const int view = view_of_item(P.views, P.n_views, g);
