@@ -21,29 +21,6 @@ __device__ __forceinline__ void put(float *dst, size_t k, float v, bool atomic) 
     else dst[k] = v;
 }
 
-// Writes zero gradients for item g of view V (single-view calls, where
-// this kernel writes every gradient entry instead of a separate memset).
-template <int K>
-__device__ __forceinline__ void zero_grads(const ViewDesc &V, uint32_t i) {
-    if (V.g_mu) for (int k = 0; k < 3; k++) V.g_mu[3 * (size_t)i + k] = 0.f;
-    if (V.g_vel) for (int k = 0; k < 3; k++) V.g_vel[3 * (size_t)i + k] = 0.f;
-    if (V.g_scale) for (int k = 0; k < 3; k++) V.g_scale[3 * (size_t)i + k] = 0.f;
-    if (V.g_quat) {
-        const float z4[4] = {0.f, 0.f, 0.f, 0.f};
-        store_floats<4>(V.g_quat + 4 * (size_t)i, z4, aligned16(V.g_quat));
-    }
-    if (V.g_tau) V.g_tau[i] = 0.f;
-    if (V.g_beta) V.g_beta[i] = 0.f;
-    if (V.g_period) V.g_period[i] = 0.f;
-    if (V.g_opac) V.g_opac[i] = 0.f;
-    if (V.g_sh) {
-        float z[3 * K];
-#pragma unroll
-        for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
-        store_floats<3 * K>(V.g_sh + (size_t)i * 3 * K, z, aligned16(V.g_sh));
-    }
-}
-
 // dL/dsh[k][c] = gcol[c] Y_k(d), written (or accumulated) in groups of four
 // basis functions (three float4) when the rows allow it
 template <int D>
@@ -111,163 +88,297 @@ __device__ __forceinline__ void sh_dir_adjoint(float x, float y, float z, const 
     }
 }
 
-// Adjoint of the projection and colour, in item order: item g reads the
-// image-space gradients of its depth position m = inv[g].  With `atomic`
-// (several views share the gradients) the gradients were zeroed before and
-// are accumulated; otherwise every entry of item g is written, zeros for
-// invisible items.
+// The per-item gradients other than the SH coefficients' (17 floats).
+struct SmallGrads {
+    float mu[3], vel[3], scale[3], quat[4], tau, beta, period, opac;
+};
+constexpr int kSmall = 17;
+
+// Adjoint of the projection and colour of visible item i of view V, from
+// the image-space gradients of its depth position m.  The SH coefficients'
+// gradients go to V.g_sh directly (written, or accumulated with `atomic`);
+// the others are returned.  False if the projection culls the item (then
+// nothing is written).
 template <int D>
-__global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
+__device__ __forceinline__ bool item_adjoint(const Params &P, const ViewDesc &V, uint32_t i, uint32_t m,
+                                             bool atomic, SmallGrads &out) {
     constexpr int K = (D + 1) * (D + 1);
+    Fwd F;
+    if (!project(V, i, P.dilation, P.tile_w, P.tile_h, F)) return false;
+    const float *G2 = P.g2d + 10 * (size_t)m;
+    const float gu = G2[0], gv = G2[1], ga = G2[2], gb = G2[3], gc = G2[4];
+    const float got = G2[5], gz = G2[9];
+    float gmut[3] = {0.f, 0.f, 0.f};
+    float gp[3] = {0.f, 0.f, 0.f};
+    // ---- conic = inverse(cov2): dL/dcov2 = -Q Ghat Q
+    const float a = F.ca, b = F.cb, c = F.cc;
+    const float gA = -(a * a * ga + a * b * gb + b * b * gc);
+    const float gB = -(a * b * ga + 0.5f * (a * c + b * b) * gb + b * c * gc);  // symmetric entry
+    const float gC = -(b * b * ga + b * c * gb + c * c * gc);
+    // ---- cov2 = Tm Sigma Tm^T: G_Sigma = Tm^T G2 Tm, G_Tm = 2 G2 Tm Sigma
+    const float *Tm = F.Tm, *S = F.Sig;
+    float GS[6];  // xx xy xz yy yz zz of the symmetric gradient
+    {
+        float U[6];  // G2 Tm (2x3)
+        for (int k = 0; k < 3; k++) {
+            U[k] = gA * Tm[k] + gB * Tm[3 + k];
+            U[3 + k] = gB * Tm[k] + gC * Tm[3 + k];
+        }
+        GS[0] = Tm[0] * U[0] + Tm[3] * U[3];
+        GS[1] = Tm[0] * U[1] + Tm[3] * U[4];
+        GS[2] = Tm[0] * U[2] + Tm[3] * U[5];
+        GS[3] = Tm[1] * U[1] + Tm[4] * U[4];
+        GS[4] = Tm[1] * U[2] + Tm[4] * U[5];
+        GS[5] = Tm[2] * U[2] + Tm[5] * U[5];
+        // G_Tm = 2 U Sigma
+        float GT[6];
+        for (int r = 0; r < 2; r++) {
+            const float *u = U + 3 * r;
+            GT[3 * r + 0] = 2.f * (u[0] * S[0] + u[1] * S[1] + u[2] * S[2]);
+            GT[3 * r + 1] = 2.f * (u[0] * S[1] + u[1] * S[3] + u[2] * S[4]);
+            GT[3 * r + 2] = 2.f * (u[0] * S[2] + u[1] * S[4] + u[2] * S[5]);
+        }
+        // Tm = J W: dL/dJ = G_Tm W^T (only J00, J02, J11, J12 are free)
+        const float *R = V.R;
+        const float gJ00 = GT[0] * R[0] + GT[1] * R[1] + GT[2] * R[2];
+        const float gJ02 = GT[0] * R[6] + GT[1] * R[7] + GT[2] * R[8];
+        const float gJ11 = GT[3] * R[3] + GT[4] * R[4] + GT[5] * R[5];
+        const float gJ12 = GT[3] * R[6] + GT[4] * R[7] + GT[5] * R[8];
+        const float z = F.p.z, iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+        gp[2] += gJ00 * (-V.fx * iz2) + gJ11 * (-V.fy * iz2);
+        if (F.clampx == 0) {
+            gp[0] += gJ02 * (-V.fx * iz2);
+            gp[2] += gJ02 * (2.f * V.fx * F.p.x * iz3);
+        } else {
+            gp[2] += gJ02 * (V.fx * F.clampx * V.limx * iz2);
+        }
+        if (F.clampy == 0) {
+            gp[1] += gJ12 * (-V.fy * iz2);
+            gp[2] += gJ12 * (2.f * V.fy * F.p.y * iz3);
+        } else {
+            gp[2] += gJ12 * (V.fy * F.clampy * V.limy * iz2);
+        }
+        // projected mean and depth
+        gp[0] += gu * V.fx * iz;
+        gp[1] += gv * V.fy * iz;
+        gp[2] += -(gu * V.fx * F.p.x + gv * V.fy * F.p.y) * iz2 + gz;
+    }
+    // ---- Sigma = M M^T, M = Rq diag(s): G_M = 2 G_Sigma M
+    {
+        float M[9];
+        for (int r = 0; r < 3; r++)
+            for (int k = 0; k < 3; k++) M[3 * r + k] = F.Rq[3 * r + k] * F.s[k];
+        const float Gs[9] = {GS[0], GS[1], GS[2], GS[1], GS[3], GS[4], GS[2], GS[4], GS[5]};
+        float GM[9];
+        for (int r = 0; r < 3; r++)
+            for (int k = 0; k < 3; k++)
+                GM[3 * r + k] = 2.f * (Gs[3 * r] * M[k] + Gs[3 * r + 1] * M[3 + k] + Gs[3 * r + 2] * M[6 + k]);
+        float gsc[3], GR[9];
+        for (int k = 0; k < 3; k++) gsc[k] = GM[k] * F.Rq[k] + GM[3 + k] * F.Rq[3 + k] + GM[6 + k] * F.Rq[6 + k];
+        for (int r = 0; r < 3; r++)
+            for (int k = 0; k < 3; k++) GR[3 * r + k] = GM[3 * r + k] * F.s[k];
+        const float w = F.qn[0], x = F.qn[1], y = F.qn[2], zq = F.qn[3];
+        // dR/dw, dR/dx, dR/dy, dR/dz contracted with GR
+        const float gw = 2.f * (-zq * GR[1] + y * GR[2] + zq * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+        const float gx = 2.f * (y * GR[1] + zq * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + zq * GR[6] +
+                                w * GR[7] - 2.f * x * GR[8]);
+        const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + zq * GR[5] - w * GR[6] +
+                                zq * GR[7] - 2.f * y * GR[8]);
+        const float gzq = 2.f * (-2.f * zq * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * zq * GR[4] +
+                                 y * GR[5] + x * GR[6] + y * GR[7]);
+        const float dot = F.qn[0] * gw + F.qn[1] * gx + F.qn[2] * gy + F.qn[3] * gzq;
+        out.quat[0] = (gw - F.qn[0] * dot) * F.qinv;
+        out.quat[1] = (gx - F.qn[1] * dot) * F.qinv;
+        out.quat[2] = (gy - F.qn[2] * dot) * F.qinv;
+        out.quat[3] = (gzq - F.qn[3] * dot) * F.qinv;
+        for (int k = 0; k < 3; k++) out.scale[k] = gsc[k];
+    }
+    // ---- p = W mu~ + T
+    {
+        const float *R = V.R;
+        for (int k = 0; k < 3; k++) gmut[k] += R[k] * gp[0] + R[3 + k] * gp[1] + R[6 + k] * gp[2];
+    }
+    // ---- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5).  The compositor's
+    // adjoint already zeroed the colour terms where the forward clamped;
+    // two streaming passes over the coefficients (dL/dsh from Y, then
+    // dL/ddir from dY) keep few values live at a time.
+    {
+        const float gcol[3] = {G2[6], G2[7], G2[8]};
+        float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
+        const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float inv = 1.0f / dist;
+        dx *= inv; dy *= inv; dz *= inv;
+        const float *shp = V.sh + (size_t)i * K * 3;
+        const bool vec = aligned16(V.sh) && (!V.g_sh || aligned16(V.g_sh));
+        if (V.g_sh) sh_coef_adjoint<D>(dx, dy, dz, gcol, V.g_sh + (size_t)i * K * 3, vec, atomic);
+        float gd[3];
+        sh_dir_adjoint<D>(dx, dy, dz, gcol, shp, vec, gd);
+        const float dot = dx * gd[0] + dy * gd[1] + dz * gd[2];
+        gmut[0] += (gd[0] - dx * dot) * inv;
+        gmut[1] += (gd[1] - dy * dot) * inv;
+        gmut[2] += (gd[2] - dz * dot) * inv;
+    }
+    // ---- time evaluation (Eq. 6 / Eq. 7)
+    {
+        const float3 vel = ld3(V.vel, i);
+        const float l = V.period[i], beta = V.beta[i];
+        const float gvd = gmut[0] * vel.x + gmut[1] * vel.y + gmut[2] * vel.z;
+        for (int k = 0; k < 3; k++) {
+            out.mu[k] = gmut[k];
+            out.vel[k] = gmut[k] * F.amp;
+        }
+        const float ib2 = 1.0f / (beta * beta);
+        out.tau = -F.cs * gvd + got * F.ot * F.delta * ib2;
+        // flow shift dt v exp(-beta / (2 l)): its beta and l terms
+        const float gsh = gvd * V.dt * F.vbw;
+        out.period = gvd * (F.sn * kInv2Pi - F.delta / l * F.cs) + gsh * (0.5f * beta / (l * l));
+        out.opac = got * F.egate;
+        out.beta = got * F.ot * F.delta * F.delta * ib2 / beta - gsh * (0.5f / l);
+    }
+    return true;
+}
+
+// exclusive scan over the block (blockDim.x = 256) of one value per
+// thread; *total gets the sum.  smem: 33 words.
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *smem, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nw ? smem[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) smem[lane] = wi - w;
+        if (lane == 31) smem[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = smem[warp] + x - v;
+    *total = smem[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void put_small(const ViewDesc &V, uint32_t i, const SmallGrads &q) {
+    if (V.g_mu) for (int k = 0; k < 3; k++) atomicAdd(V.g_mu + 3 * (size_t)i + k, q.mu[k]);
+    if (V.g_vel) for (int k = 0; k < 3; k++) atomicAdd(V.g_vel + 3 * (size_t)i + k, q.vel[k]);
+    if (V.g_scale) for (int k = 0; k < 3; k++) atomicAdd(V.g_scale + 3 * (size_t)i + k, q.scale[k]);
+    if (V.g_quat) for (int k = 0; k < 4; k++) atomicAdd(V.g_quat + 4 * (size_t)i + k, q.quat[k]);
+    if (V.g_tau) atomicAdd(V.g_tau + i, q.tau);
+    if (V.g_beta) atomicAdd(V.g_beta + i, q.beta);
+    if (V.g_period) atomicAdd(V.g_period + i, q.period);
+    if (V.g_opac) atomicAdd(V.g_opac + i, q.opac);
+}
+
+// Several views (`atomic`): the gradients were zeroed before; every view's
+// visible items accumulate theirs, one thread per item.
+template <int D>
+__global__ void __launch_bounds__(256) k_preprocess_bwd_atomic(Params P) {
     const uint32_t n = P.n_items;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const uint32_t m = P.inv[g];
+        if (m == 0xffffffffu) continue;
         const int view = view_of_item(P.views, P.n_views, g);
         const ViewDesc &V = P.views[view];
-        const uint32_t i = g - V.item_base;
-        const uint32_t m = P.inv[g];
-        Fwd F;
-        if (m == 0xffffffffu || !project(V, i, P.dilation, P.tile_w, P.tile_h, F)) {
-            if (!atomic) zero_grads<K>(V, i);
-            continue;
-        }
-        const float *G2 = P.g2d + 10 * (size_t)m;
-        const float gu = G2[0], gv = G2[1], ga = G2[2], gb = G2[3], gc = G2[4];
-        const float got = G2[5], gz = G2[9];
-        float gmut[3] = {0.f, 0.f, 0.f};
-        float gp[3] = {0.f, 0.f, 0.f};
+        SmallGrads q;
+        if (item_adjoint<D>(P, V, g - V.item_base, m, true, q)) put_small(V, g - V.item_base, q);
+    }
+}
 
-        // ---- conic = inverse(cov2): dL/dcov2 = -Q Ghat Q
-        const float a = F.ca, b = F.cb, c = F.cc;
-        const float gA = -(a * a * ga + a * b * gb + b * b * gc);
-        const float gB = -(a * b * ga + 0.5f * (a * c + b * b) * gb + b * c * gc);  // symmetric entry
-        const float gC = -(b * b * ga + b * c * gb + c * c * gc);
-        // ---- cov2 = Tm Sigma Tm^T: G_Sigma = Tm^T G2 Tm, G_Tm = 2 G2 Tm Sigma
-        const float *Tm = F.Tm, *S = F.Sig;
-        float GS[6];  // xx xy xz yy yz zz of the symmetric gradient
-        {
-            float U[6];  // G2 Tm (2x3)
-            for (int k = 0; k < 3; k++) {
-                U[k] = gA * Tm[k] + gB * Tm[3 + k];
-                U[3 + k] = gB * Tm[k] + gC * Tm[3 + k];
-            }
-            GS[0] = Tm[0] * U[0] + Tm[3] * U[3];
-            GS[1] = Tm[0] * U[1] + Tm[3] * U[4];
-            GS[2] = Tm[0] * U[2] + Tm[3] * U[5];
-            GS[3] = Tm[1] * U[1] + Tm[4] * U[4];
-            GS[4] = Tm[1] * U[2] + Tm[4] * U[5];
-            GS[5] = Tm[2] * U[2] + Tm[5] * U[5];
-            // G_Tm = 2 U Sigma
-            float GT[6];
-            for (int r = 0; r < 2; r++) {
-                const float *u = U + 3 * r;
-                GT[3 * r + 0] = 2.f * (u[0] * S[0] + u[1] * S[1] + u[2] * S[2]);
-                GT[3 * r + 1] = 2.f * (u[0] * S[1] + u[1] * S[3] + u[2] * S[4]);
-                GT[3 * r + 2] = 2.f * (u[0] * S[2] + u[1] * S[4] + u[2] * S[5]);
-            }
-            // Tm = J W: dL/dJ = G_Tm W^T (only J00, J02, J11, J12 are free)
-            const float *R = V.R;
-            const float gJ00 = GT[0] * R[0] + GT[1] * R[1] + GT[2] * R[2];
-            const float gJ02 = GT[0] * R[6] + GT[1] * R[7] + GT[2] * R[8];
-            const float gJ11 = GT[3] * R[3] + GT[4] * R[4] + GT[5] * R[5];
-            const float gJ12 = GT[3] * R[6] + GT[4] * R[7] + GT[5] * R[8];
-            const float z = F.p.z, iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
-            gp[2] += gJ00 * (-V.fx * iz2) + gJ11 * (-V.fy * iz2);
-            if (F.clampx == 0) {
-                gp[0] += gJ02 * (-V.fx * iz2);
-                gp[2] += gJ02 * (2.f * V.fx * F.p.x * iz3);
-            } else {
-                gp[2] += gJ02 * (V.fx * F.clampx * V.limx * iz2);
-            }
-            if (F.clampy == 0) {
-                gp[1] += gJ12 * (-V.fy * iz2);
-                gp[2] += gJ12 * (2.f * V.fy * F.p.y * iz3);
-            } else {
-                gp[2] += gJ12 * (V.fy * F.clampy * V.limy * iz2);
-            }
-            // projected mean and depth
-            gp[0] += gu * V.fx * iz;
-            gp[1] += gv * V.fy * iz;
-            gp[2] += -(gu * V.fx * F.p.x + gv * V.fy * F.p.y) * iz2 + gz;
+// One view: every gradient entry is written once.  A block takes chunks
+// of kChunk consecutive items; their visible items are compacted onto the
+// block's threads (so every lane of the heavy path has an item), the 19
+// small gradients of the chunk are staged in shared memory (zeros for the
+// invisible items) and written out coalesced, field by field, so that each
+// 32-byte sector is written whole by one instruction.  SH-coefficient rows
+// (192 bytes at degree 3) are written by the item's thread, zeros for the
+// invisible items.
+template <int D>
+__global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
+    constexpr int K = (D + 1) * (D + 1);
+    constexpr int kChunk = 512, kPer = kChunk / 256;
+    __shared__ float s_g[kSmall][kChunk];
+    __shared__ uint16_t s_list[kChunk];
+    __shared__ uint32_t s_scan[33];
+    const ViewDesc &V = P.views[0];  // one view: item g is Gaussian g (item_base 0)
+    const uint32_t n = P.n_items;
+    const int tid = threadIdx.x;
+    for (uint32_t base = blockIdx.x * kChunk; base < n; base += gridDim.x * kChunk) {
+        // visibility of the chunk's items (kPer consecutive ones per thread)
+        uint32_t mv[kPer];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const uint32_t g = base + tid * kPer + q;
+            mv[q] = g < n ? P.inv[g] : 0xffffffffu;
+            cnt += mv[q] != 0xffffffffu ? 1u : 0u;
         }
-        // ---- Sigma = M M^T, M = Rq diag(s): G_M = 2 G_Sigma M
-        {
-            float M[9];
-            for (int r = 0; r < 3; r++)
-                for (int k = 0; k < 3; k++) M[3 * r + k] = F.Rq[3 * r + k] * F.s[k];
-            const float Gs[9] = {GS[0], GS[1], GS[2], GS[1], GS[3], GS[4], GS[2], GS[4], GS[5]};
-            float GM[9];
-            for (int r = 0; r < 3; r++)
-                for (int k = 0; k < 3; k++)
-                    GM[3 * r + k] = 2.f * (Gs[3 * r] * M[k] + Gs[3 * r + 1] * M[3 + k] + Gs[3 * r + 2] * M[6 + k]);
-            float gsc[3], GR[9];
-            for (int k = 0; k < 3; k++) gsc[k] = GM[k] * F.Rq[k] + GM[3 + k] * F.Rq[3 + k] + GM[6 + k] * F.Rq[6 + k];
-            for (int r = 0; r < 3; r++)
-                for (int k = 0; k < 3; k++) GR[3 * r + k] = GM[3 * r + k] * F.s[k];
-            const float w = F.qn[0], x = F.qn[1], y = F.qn[2], zq = F.qn[3];
-            // dR/dw, dR/dx, dR/dy, dR/dz contracted with GR
-            const float gw = 2.f * (-zq * GR[1] + y * GR[2] + zq * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
-            const float gx = 2.f * (y * GR[1] + zq * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + zq * GR[6] +
-                                    w * GR[7] - 2.f * x * GR[8]);
-            const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + zq * GR[5] - w * GR[6] +
-                                    zq * GR[7] - 2.f * y * GR[8]);
-            const float gzq = 2.f * (-2.f * zq * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * zq * GR[4] +
-                                     y * GR[5] + x * GR[6] + y * GR[7]);
-            const float dot = F.qn[0] * gw + F.qn[1] * gx + F.qn[2] * gy + F.qn[3] * gzq;
-            if (V.g_quat) {
-                const float gq[4] = {(gw - F.qn[0] * dot) * F.qinv, (gx - F.qn[1] * dot) * F.qinv,
-                                     (gy - F.qn[2] * dot) * F.qinv, (gzq - F.qn[3] * dot) * F.qinv};
-                if (atomic) {
-                    for (int k = 0; k < 4; k++) atomicAdd(V.g_quat + 4 * (size_t)i + k, gq[k]);
-                } else {
-                    store_floats<4>(V.g_quat + 4 * (size_t)i, gq, aligned16(V.g_quat));
+        uint32_t nvis;
+        uint32_t pos = block_excl_scan_u32(cnt, s_scan, &nvis);
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const int idx = tid * kPer + q;
+            if (mv[q] != 0xffffffffu) {
+                s_list[pos++] = (uint16_t)idx;
+            } else if (base + idx < n) {
+#pragma unroll
+                for (int f = 0; f < kSmall; f++) s_g[f][idx] = 0.f;
+                if (V.g_sh) {
+                    float z[3 * K];
+#pragma unroll
+                    for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
+                    store_floats<3 * K>(V.g_sh + (size_t)(base + idx) * 3 * K, z, aligned16(V.g_sh));
                 }
             }
-            if (V.g_scale)
-                for (int k = 0; k < 3; k++) put(V.g_scale, 3 * (size_t)i + k, gsc[k], atomic);
         }
-        // ---- p = W mu~ + T
-        {
-            const float *R = V.R;
-            for (int k = 0; k < 3; k++) gmut[k] += R[k] * gp[0] + R[3 + k] * gp[1] + R[6 + k] * gp[2];
+        __syncthreads();
+        // the visible items, compacted
+        for (uint32_t k = tid; k < nvis; k += 256) {
+            const int idx = s_list[k];
+            const uint32_t i = base + idx;
+            SmallGrads q;
+            if (!item_adjoint<D>(P, V, i, P.inv[i], false, q)) {  // culled after all: zeros
+                q = SmallGrads{};
+                if (V.g_sh) {
+                    float z[3 * K];
+#pragma unroll
+                    for (int c = 0; c < 3 * K; c++) z[c] = 0.f;
+                    store_floats<3 * K>(V.g_sh + (size_t)i * 3 * K, z, aligned16(V.g_sh));
+                }
+            }
+            const float v[kSmall] = {q.mu[0], q.mu[1], q.mu[2], q.vel[0], q.vel[1], q.vel[2],
+                                     q.scale[0], q.scale[1], q.scale[2], q.quat[0], q.quat[1], q.quat[2], q.quat[3],
+                                     q.tau, q.beta, q.period, q.opac};
+#pragma unroll
+            for (int f = 0; f < kSmall; f++) s_g[f][idx] = v[f];
         }
-        // ---- colour: rgb = max(0, sum_k sh_k Y_k(d) + 0.5).  The compositor's
-        // adjoint already zeroed the colour terms where the forward clamped;
-        // two streaming passes over the coefficients (dL/dsh from Y, then
-        // dL/ddir from dY) keep few values live at a time.
-        {
-            const float gcol[3] = {G2[6], G2[7], G2[8]};
-            float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
-            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float inv = 1.0f / dist;
-            dx *= inv; dy *= inv; dz *= inv;
-            const float *shp = V.sh + (size_t)i * K * 3;
-            const bool vec = aligned16(V.sh) && (!V.g_sh || aligned16(V.g_sh));
-            if (V.g_sh) sh_coef_adjoint<D>(dx, dy, dz, gcol, V.g_sh + (size_t)i * K * 3, vec, atomic);
-            float gd[3];
-            sh_dir_adjoint<D>(dx, dy, dz, gcol, shp, vec, gd);
-            const float dot = dx * gd[0] + dy * gd[1] + dz * gd[2];
-            gmut[0] += (gd[0] - dx * dot) * inv;
-            gmut[1] += (gd[1] - dy * dot) * inv;
-            gmut[2] += (gd[2] - dz * dot) * inv;
-        }
-        // ---- time evaluation (Eq. 6 / Eq. 7)
-        {
-            const float3 vel = ld3(V.vel, i);
-            const float l = V.period[i], beta = V.beta[i];
-            const float gvd = gmut[0] * vel.x + gmut[1] * vel.y + gmut[2] * vel.z;
-            if (V.g_mu)
-                for (int k = 0; k < 3; k++) put(V.g_mu, 3 * (size_t)i + k, gmut[k], atomic);
-            if (V.g_vel)
-                for (int k = 0; k < 3; k++) put(V.g_vel, 3 * (size_t)i + k, gmut[k] * F.amp, atomic);
-            const float ib2 = 1.0f / (beta * beta);
-            if (V.g_tau) put(V.g_tau, i, -F.cs * gvd + got * F.ot * F.delta * ib2, atomic);
-            // flow shift dt v exp(-beta / (2 l)): its beta and l terms
-            const float gsh = gvd * V.dt * F.vbw;
-            if (V.g_period)
-                put(V.g_period, i, gvd * (F.sn * kInv2Pi - F.delta / l * F.cs) + gsh * (0.5f * beta / (l * l)), atomic);
-            if (V.g_opac) put(V.g_opac, i, got * F.egate, atomic);
-            if (V.g_beta) put(V.g_beta, i, got * F.ot * F.delta * F.delta * ib2 / beta - gsh * (0.5f / l), atomic);
-        }
+        __syncthreads();
+        // coalesced write-out of the chunk's small gradients
+        const uint32_t cn = min((uint32_t)kChunk, n - base);
+        auto out3 = [&](float *dst, int f0) {
+            if (!dst) return;
+            for (uint32_t e = tid; e < 3 * cn; e += 256) dst[3 * (size_t)base + e] = s_g[f0 + e % 3][e / 3];
+        };
+        out3(V.g_mu, 0);
+        out3(V.g_vel, 3);
+        out3(V.g_scale, 6);
+        if (V.g_quat)
+            for (uint32_t e = tid; e < 4 * cn; e += 256) V.g_quat[4 * (size_t)base + e] = s_g[9 + (e & 3)][e >> 2];
+        float *const one[4] = {V.g_tau, V.g_beta, V.g_period, V.g_opac};
+#pragma unroll
+        for (int f = 0; f < 4; f++)
+            if (one[f])
+                for (uint32_t e = tid; e < cn; e += 256) one[f][base + e] = s_g[13 + f][e];
+        __syncthreads();
     }
 }
 
@@ -275,11 +386,21 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(Params P, bool atomic) {
 
 void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s) {
     note_launch();
+    if (accumulate_atomic) {
+        switch (p.sh_degree) {
+            case 0: k_preprocess_bwd_atomic<0><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+            case 1: k_preprocess_bwd_atomic<1><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+            case 2: k_preprocess_bwd_atomic<2><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+            default: k_preprocess_bwd_atomic<3><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+        }
+        return;
+    }
+    const int grid = grid_for((p.n_items + 1) / 2);
     switch (p.sh_degree) {
-        case 0: k_preprocess_bwd<0><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
-        case 1: k_preprocess_bwd<1><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
-        case 2: k_preprocess_bwd<2><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
-        default: k_preprocess_bwd<3><<<grid_for(p.n_items), 256, 0, s>>>(p, accumulate_atomic); break;
+        case 0: k_preprocess_bwd<0><<<grid, 256, 0, s>>>(p); break;
+        case 1: k_preprocess_bwd<1><<<grid, 256, 0, s>>>(p); break;
+        case 2: k_preprocess_bwd<2><<<grid, 256, 0, s>>>(p); break;
+        default: k_preprocess_bwd<3><<<grid, 256, 0, s>>>(p); break;
     }
 }
 
