@@ -175,6 +175,15 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
     if (maxlast) atomicMax(&s_maxlast, maxlast);
     __syncthreads();
     const uint32_t n = s_maxlast;
+    // gv: an entry's 10 terms over this thread's pixels, zero between
+    // entries (reset after each warp reduction).  The pixels share dx, so
+    // the conic moments are kept as sum gpow (A0), sum gpow dy (gv[1]) and
+    // sum gpow dy^2 (gv[4]) and expanded once: m_x = dx A0, m_xx = dx^2 A0,
+    // m_xy = dx m_y.
+    float gv[NG];
+#pragma unroll
+    for (int c = 0; c < NG; c++) gv[c] = 0.f;
+    float A0 = 0.f;
     for (uint32_t end = r.x + n; end > r.x;) {
         const uint32_t start = end - r.x > (uint32_t)BLOCK ? end - BLOCK : r.x;
         const int cnt = (int)(end - start);
@@ -188,58 +197,57 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
         __syncthreads();
         for (int k = cnt - 1; k >= 0; k--) {
             const uint32_t pos = start + k - r.x;  // list position
-            // gv: the entry's 10 terms over this thread's pixels.  All of
-            // them share dx, so the conic moments are kept as sum gpow
-            // (A0), sum gpow dy (gv[1]) and sum gpow dy^2 (gv[4]) and
-            // expanded once: m_x = dx A0, m_xx = dx^2 A0, m_xy = dx m_y.
-            float gv[NG];
-#pragma unroll
-            for (int c = 0; c < NG; c++) gv[c] = 0.f;
-            float A0 = 0.f;
             bool contrib = false;
-            const float4 g = s0[k];
-            const float2 q = s1[k];
-            const float4 col = s2[k];
-            const float dx = __fsub_rn(fx, g.x);
+            if (pos < maxlast) {  // before the last blend of one of this thread's pixels
+                const float4 g = s0[k];
+                const float2 q = s1[k];
+                const float4 col = s2[k];
+                const float dx = __fsub_rn(fx, g.x);
 #pragma unroll
-            for (int p = 0; p < PX; p++) {
-                if (pos >= last[p]) continue;
-                const float dy = __fsub_rn(fy[p], g.y);
-                const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
-                const float G = ex2_approx(e);
-                const float raw = __fmul_rn(q.y, G);
-                const float alpha = fminf(kAlphaCap, raw);
-                if (alpha < kAlphaMin) continue;
-                contrib = true;
-                const float inv = rcp_approx(1.0f - alpha);
-                const float Ti = T[p] * inv;
-                const float w = alpha * Ti;
-                float X = gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z;
-                if constexpr (kAux) X += gD[p] * col.w + gO[p];
-                const float ga = Ti * X - inv * S[p];
-                gv[6] += gC0[p] * w;
-                gv[7] += gC1[p] * w;
-                gv[8] += gC2[p] * w;
-                if constexpr (kAux) gv[9] += gD[p] * w;
-                if (raw <= kAlphaCap) {
-                    // moments of gpow = dL/dpower (d alpha / d power = alpha);
-                    // the conic is applied once per Gaussian in the flush
-                    gv[5] += ga * G;
-                    const float gpow = ga * alpha;
-                    const float my = gpow * dy;
-                    A0 += gpow;
-                    gv[1] += my;
-                    gv[4] += my * dy;
+                for (int p = 0; p < PX; p++) {
+                    if (pos >= last[p]) continue;
+                    const float dy = __fsub_rn(fy[p], g.y);
+                    const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
+                    const float G = ex2_approx(e);
+                    const float raw = __fmul_rn(q.y, G);
+                    const float alpha = fminf(kAlphaCap, raw);
+                    if (alpha < kAlphaMin) continue;
+                    contrib = true;
+                    const float inv = rcp_approx(1.0f - alpha);
+                    const float Ti = T[p] * inv;
+                    const float w = alpha * Ti;
+                    float X = gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z;
+                    if constexpr (kAux) X += gD[p] * col.w + gO[p];
+                    const float ga = Ti * X - inv * S[p];
+                    gv[6] += gC0[p] * w;
+                    gv[7] += gC1[p] * w;
+                    gv[8] += gC2[p] * w;
+                    if constexpr (kAux) gv[9] += gD[p] * w;
+                    if (raw <= kAlphaCap) {
+                        // moments of gpow = dL/dpower (d alpha / d power = alpha);
+                        // the conic is applied once per Gaussian in the flush
+                        gv[5] += ga * G;
+                        const float gpow = ga * alpha;
+                        const float my = gpow * dy;
+                        A0 += gpow;
+                        gv[1] += my;
+                        gv[4] += my * dy;
+                    }
+                    S[p] += X * w;
+                    T[p] = Ti;
                 }
-                S[p] += X * w;
-                T[p] = Ti;
+                if (contrib) {
+                    gv[0] = dx * A0;
+                    gv[2] = dx * gv[0];
+                    gv[3] = dx * gv[1];
+                }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                gv[0] = dx * A0;
-                gv[2] = dx * gv[0];
-                gv[3] = dx * gv[1];
                 const float2 tot = warp_sum_terms<NT>(gv);
                 if (lane < NT) atomicAdd(&s_acc[k * NG + lane], lane < 8 ? tot.x : tot.y);
+#pragma unroll
+                for (int c = 0; c < NG; c++) gv[c] = 0.f;
+                A0 = 0.f;
             }
         }
         __syncthreads();
