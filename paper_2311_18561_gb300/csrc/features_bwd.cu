@@ -97,6 +97,13 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
         if (maxlast) atomicMax(&s_maxlast, maxlast);
         __syncthreads();
         const uint32_t n = s_maxlast;
+        // gv: an entry's terms over this thread's pixels, zero between
+        // entries (reset after each warp reduction); the conic moments as
+        // in the colour adjoint (sum gpow in A0, expanded with the shared dx)
+        float gv[NT];
+#pragma unroll
+        for (int c = 0; c < NT; c++) gv[c] = 0.f;
+        float A0 = 0.f;
         for (uint32_t end = Q.r.x + n; end > Q.r.x;) {
             const uint32_t start = end - Q.r.x > (uint32_t)kFB ? end - kFB : Q.r.x;
             const int cnt = (int)(end - start);
@@ -115,9 +122,6 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
             __syncthreads();
             for (int k = cnt - 1; k >= 0; k--) {
                 const uint32_t pos = start + k - Q.r.x;
-                float gv[NT];
-#pragma unroll
-                for (int c = 0; c < NT; c++) gv[c] = 0.f;
                 bool contrib = false;
                 const float4 g = s0[k];
                 const float2 q = s1[k];
@@ -151,20 +155,24 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
                         const float ga = Ti * X - inv * S[p];
                         gv[5] += ga * G;
                         const float gpow = ga * alpha;
-                        const float mx = gpow * dx, my = gpow * dy;
-                        gv[0] += mx;
+                        const float my = gpow * dy;
+                        A0 += gpow;
                         gv[1] += my;
-                        gv[2] += mx * dx;
-                        gv[3] += mx * dy;
                         gv[4] += my * dy;
                     }
                     S[p] += X * w;
                     T[p] = Ti;
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
+                    gv[0] = dx * A0;
+                    gv[2] = dx * gv[0];
+                    gv[3] = dx * gv[1];
                     constexpr int N0 = NT >= 32 ? 32 : pow2_at_least(NT);
                     reduce_chunk<NT, 0, N0>(gv, s_acc, k);
                     if constexpr (NT > 32) reduce_chunk<NT, 32, pow2_at_least(NT - 32)>(gv, s_acc, k);
+#pragma unroll
+                    for (int c = 0; c < NT; c++) gv[c] = 0.f;
+                    A0 = 0.f;
                 }
             }
             __syncthreads();
