@@ -3,6 +3,9 @@ and compare with the FP64 oracle."""
 import numpy as np
 import torch
 
+import oracle
+from oracle import binning
+
 # Image tolerance: max-abs 1e-3 per channel in [0, 1] (rgb, alpha) on
 # pixels the oracle does not flag; flagged pixels (a gate within 1e-5
 # relative of its threshold, or two blended depths within 1e-6 relative:
@@ -41,3 +44,36 @@ def gpu_render(renderer, scene_t, cams, frame=None):
     outs = renderer.forward(scene_t, cams, frame=frame)
     torch.cuda.synchronize()
     return outs
+
+
+def check_tile_lists(ex, scene, cam, tile, tiles_x, tiles_y):
+    """The GPU's per-tile lists (exported frame `ex`) against what is fixed:
+    each list is an ordered subset of the bounding-rectangle list (plain
+    definition over the GPU's own rectangles and depth keys), it holds
+    every tile where the FP64 oracle blends the Gaussian (level shrunk by
+    1e-3 against rounding), and the ranges partition the pairs in tile
+    order.  Returns (pairs kept, pairs of the rectangle lists)."""
+    gid, zk, rect = ex["sorted_gid"], ex["depth_key"], ex["rect"]
+    z = zk.view(np.float32)
+    values, ranges = binning.tile_lists(gid, z, rect[:, [0, 1, 2, 3]], tiles_x, tiles_y)
+    got_vals = gid[ex["pair_vals"]].astype(np.int64)
+    got_r = ex["ranges"].astype(np.int64)
+    lens = got_r[:, 1] - got_r[:, 0]
+    assert np.all(lens >= 0) and lens.sum() == got_vals.size
+    nonempty = lens > 0
+    np.testing.assert_array_equal(got_r[nonempty, 0], np.concatenate([[0], np.cumsum(lens[nonempty])[:-1]]))
+    pp = oracle.preprocess(scene, cam)
+    need = binning.contributing_tiles(pp["uv"][gid], pp["conic"][gid], pp["ot"][gid], cam["width"],
+                                      cam["height"], tile[0], tile[1], shrink=1 - 1e-3)
+    kept = {}
+    for t in range(tiles_x * tiles_y):
+        full = values[ranges[t, 0]:ranges[t, 1]]
+        got = got_vals[got_r[t, 0]:got_r[t, 1]]
+        pos = {int(g): i for i, g in enumerate(full)}
+        idx = np.array([pos.get(int(g), -1) for g in got])
+        assert np.all(idx >= 0) and np.all(np.diff(idx) > 0), t
+        for g in got:
+            kept.setdefault(int(g), set()).add(t)
+    for k, g in enumerate(gid):
+        assert need[k] <= kept.get(int(g), set()), int(g)
+    return got_vals.size, values.size

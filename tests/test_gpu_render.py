@@ -11,7 +11,7 @@ from oracle import binning
 from paper_2311_18561_gb300 import render as R
 from paper_2311_18561_gb300 import synth
 
-from .gpu_util import compare_to_oracle, gpu_render, to_numpy_images
+from .gpu_util import check_tile_lists, compare_to_oracle, gpu_render, to_numpy_images
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
@@ -111,34 +111,8 @@ def test_depth_order_tile_lists_and_ranges_bit_exact(tile):
     assert np.all(z > 0)
     # depth order: the GPU's order equals (z bits, gid) order of its own keys
     np.testing.assert_array_equal(binning.depth_order(np.sort(gid), z[np.argsort(gid)]), gid)
-    # per-tile lists: the bounding-rectangle lists (plain definition over
-    # the GPU's own rectangles), of which the GPU keeps the tiles that the
-    # footprint ellipse meets.  Several lists are correct, so check what is
-    # fixed: every kept entry is in the rectangle list and in its order,
-    # every tile where the Gaussian is blended (FP64, level shrunk by 1e-3
-    # against rounding) is kept, and the ranges partition the pairs.
-    values, ranges = binning.tile_lists(gid, z, rect[:, [0, 1, 2, 3]], tx, ty)
-    got_vals = gid[ex["pair_vals"]].astype(np.int64)
-    got_r = ex["ranges"].astype(np.int64)
-    lens = got_r[:, 1] - got_r[:, 0]
-    assert np.all(lens >= 0) and lens.sum() == got_vals.size
-    nonempty = lens > 0
-    np.testing.assert_array_equal(got_r[nonempty, 0], np.concatenate([[0], np.cumsum(lens[nonempty])[:-1]]))
-    pp = oracle.preprocess(scene, cam)
-    need = binning.contributing_tiles(pp["uv"][gid], pp["conic"][gid], pp["ot"][gid], cam["width"],
-                                      cam["height"], tile[0], tile[1], shrink=1 - 1e-3)
-    kept = {}
-    for t in range(tx * ty):
-        full = values[ranges[t, 0]:ranges[t, 1]]
-        got = got_vals[got_r[t, 0]:got_r[t, 1]]
-        pos = {int(g): i for i, g in enumerate(full)}
-        idx = np.array([pos.get(int(g), -1) for g in got])
-        assert np.all(idx >= 0) and np.all(np.diff(idx) > 0), t
-        for g in got:
-            kept.setdefault(int(g), set()).add(t)
-    for k, g in enumerate(gid):
-        assert need[k] <= kept.get(int(g), set()), int(g)
-    assert got_vals.size < values.size  # the ellipse test leaves tiles out
+    kept, full = check_tile_lists(ex, scene, cam, tile, tx, ty)
+    assert kept < full  # the ellipse test leaves tiles out
     r.close()
     fr.close()
 
