@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
                     if (done & (1u << p)) continue;
                     const float dy = __fsub_rn(fy[p], g.y);
                     const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
-                    const float alpha = fminf(kAlphaCap, __fmul_rn(q.y, ex2_approx(e)));
-                    if (alpha < kAlphaMin) continue;
+                    const float raw = __fmul_rn(q.y, ex2_approx(e));
+                    if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
+                    const float alpha = fminf(kAlphaCap, raw);
                     const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
                     if (Tn < kTStop) {
                         done |= 1u << p;

@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
                     const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
                     const float G = ex2_approx(e);
                     const float raw = __fmul_rn(q.y, G);
+                    if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
                     const float alpha = fminf(kAlphaCap, raw);
-                    if (alpha < kAlphaMin) continue;
                     contrib = true;
                     const float inv = rcp_approx(1.0f - alpha);
                     const float Ti = T[p] * inv;

@@ -26,6 +26,7 @@ namespace pvg {
 constexpr float kAlphaMin = 1.0f / 255.0f;  // skip gate
 constexpr float kAlphaCap = 0.99f;          // alpha cap
 constexpr float kTStop = 1e-4f;             // transmittance stop
+constexpr float kFarRow = 1e30f;            // row coordinate of a pixel that is done (packed compositor)
 constexpr float kLog2e = 1.4426950408889634f;  // log2(e): e^x = 2^(x log2 e)
 constexpr int kMaxViewsPerCall = 4096;
 

@@ -118,8 +118,9 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
                     if (fabsf(dx) <= h.x && fabsf(dy) <= h.y) neval[p]++;
                 }
                 const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
-                const float alpha = fminf(kAlphaCap, __fmul_rn(q.y, ex2_approx(e)));
-                if (alpha < kAlphaMin) continue;
+                const float raw = __fmul_rn(q.y, ex2_approx(e));
+                if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
+                const float alpha = fminf(kAlphaCap, raw);
                 if constexpr (kStats) nblend[p]++;
                 const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
                 if (Tn < kTStop) {
@@ -191,6 +192,15 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
         last[p] = 0;
         if (!(G.px < V.W && G.py0 + p < V.H)) done |= 1u << p;
     }
+    // A pixel that is done (stopped, or outside the image) gets a row
+    // coordinate far away: its falloff exponent is then -inf or NaN, its
+    // alpha 0 or NaN, and the alpha test (false for NaN) never passes
+    // again, so the loop needs no per-pixel done test.
+#pragma unroll
+    for (int q = 0; q < NP; q++) {
+        if (done & (1u << (2 * q))) fy[q].x = kFarRow;
+        if (done & (2u << (2 * q))) fy[q].y = kFarRow;
+    }
     for (uint32_t base = r.x; base < r.y; base += BLOCK) {
         if (__syncthreads_count(done != ALL) == 0) break;
         const uint32_t j = base + tid;
@@ -218,18 +228,28 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
             const float2 g2 = make_float2(Dq.x, Dq.y), b2 = make_float2(Dq.z, Dq.w);
 #pragma unroll
             for (int q = 0; q < NP; q++) {
-                const uint32_t bits = (done >> (2 * q)) & 3u;
-                if (bits == 3u) continue;
                 const float2 dy = sub2(fy[q], v2);
                 const float2 e = falloff_exp2_x2(adx2, bp2, cp2, dx2, dy);
                 const float2 a = mul2(o2, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-                const float ax = fminf(kAlphaCap, a.x), ay = fminf(kAlphaCap, a.y);
-                bool bx = !(bits & 1u) && ax >= kAlphaMin, by = !(bits & 2u) && ay >= kAlphaMin;
+                // min(cap, a) >= 1/255 iff a >= 1/255 (cap > 1/255): the cap
+                // is applied to blending pixels only
+                bool bx = a.x >= kAlphaMin, by = a.y >= kAlphaMin;
                 if (!(bx || by)) continue;
+                // a done pixel passes only for a degenerate conic (c = 0,
+                // falloff independent of the row): the done bits decide
+                const uint32_t bits = (done >> (2 * q)) & 3u;
+                bx = bx && !(bits & 1u);
+                by = by && !(bits & 2u);
+                if (!(bx || by)) continue;
+                const float ax = fminf(kAlphaCap, a.x), ay = fminf(kAlphaCap, a.y);
                 const float2 al = make_float2(ax, ay);
                 const float2 Tn = mul2(T[q], sub2(one2, al));
                 const bool sx = bx && Tn.x < kTStop, sy = by && Tn.y < kTStop;
-                done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
+                if (sx || sy) {
+                    done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
+                    if (sx) fy[q].x = kFarRow;
+                    if (sy) fy[q].y = kFarRow;
+                }
                 bx = bx && !sx;
                 by = by && !sy;
                 // a pixel that does not blend takes alpha 0: w = +0 and T * (1 - 0) = T,
