@@ -20,8 +20,13 @@ from . import tune as T
 
 
 class BatchGraph:
+    """``host_targets``: optional pinned host tensors, one per view; the
+    graph then copies them into the device targets on a side stream that
+    runs beside the forward pass and joins before the loss, so a training
+    loop writes each step's targets into those host buffers and replays."""
+
     def __init__(self, scene_t, cams, targets=None, backward=True, config=None, autotune=True,
-                 headroom=1.25, stream=None, tune_configs=T.CONFIGS):
+                 headroom=1.25, stream=None, tune_configs=T.CONFIGS, host_targets=None):
         self.scene_t = scene_t
         self.cams = list(cams)
         self.backward = backward
@@ -48,6 +53,15 @@ class BatchGraph:
             self.dls = [torch.empty_like(o["rgb"]) for o in self.outs]
             self.losses = torch.zeros(len(self.cams), device=dev)
             self.grads = {k: torch.empty_like(scene_t[k]) for k in R.PARAM_NAMES}
+        self.host_targets = None
+        if host_targets is not None:
+            if not backward or len(host_targets) != len(self.cams):
+                raise ValueError("host_targets: one pinned host tensor per view, with backward=True")
+            for h, t in zip(host_targets, self.targets):
+                if h.device.type != "cpu" or not h.is_pinned() or h.shape != t.shape or h.dtype != t.dtype:
+                    raise ValueError("host_targets must be pinned CPU tensors shaped like the targets")
+            self.host_targets = list(host_targets)
+            self.copy_stream = torch.cuda.Stream(device=dev)
         self.stream = stream or torch.cuda.Stream(device=dev)
         self.graph = None
         # uncaptured run: allocates every buffer at its final size
@@ -60,7 +74,15 @@ class BatchGraph:
         torch.cuda.synchronize()
 
     def _enqueue(self):
+        if self.host_targets is not None:  # target copies beside the forward pass
+            cur = torch.cuda.current_stream()
+            self.copy_stream.wait_stream(cur)
+            with torch.cuda.stream(self.copy_stream):
+                for t, h in zip(self.targets, self.host_targets):
+                    t.copy_(h, non_blocking=True)
         self.r.forward(self.scene_t, self.cams, outs=self.outs, frame=self.frame)
+        if self.host_targets is not None:
+            torch.cuda.current_stream().wait_stream(self.copy_stream)
         if self.backward:
             for v, o in enumerate(self.outs):
                 R.l1_loss(o["rgb"], self.targets[v], dl=self.dls[v], loss=self.losses[v:v + 1])

@@ -62,6 +62,30 @@ def test_graph_replays_are_repeatable():
         assert torch.equal(a, o["rgb"])
 
 
+def test_graph_copies_host_targets_each_replay():
+    """With pinned host targets the graph copies them in on every replay
+    (beside the forward pass): new host values give the loss of those
+    values, equal to the loss against device copies of them."""
+    scene = synth.make_urban_scene(40_000, seed=6)
+    st = R.scene_to_device(scene)
+    cams = _cams()[:2]
+    hosts = [torch.empty(3, int(c["height"]), int(c["width"])).pin_memory() for c in cams]
+    g = B.BatchGraph(st, cams, autotune=False, config=(16, 16, 1), host_targets=hosts)
+    for trial in range(2):
+        gen = torch.Generator().manual_seed(10 + trial)
+        for h in hosts:
+            h.copy_(torch.rand(h.shape, generator=gen))
+        g.replay()
+        torch.cuda.synchronize()
+        for v, h in enumerate(hosts):
+            assert torch.equal(g.targets[v].cpu(), h)
+            loss, _ = R.l1_loss(g.outs[v]["rgb"], h.cuda())
+            torch.cuda.synchronize()
+            assert abs(float(loss[0]) - float(g.losses[v])) <= 1e-6 * max(1.0, abs(float(loss[0]))), (trial, v)
+    with pytest.raises(ValueError):
+        B.BatchGraph(st, cams, autotune=False, config=(16, 16, 1), host_targets=[hosts[0]])
+
+
 def test_uneven_views_in_one_call_equal_single_calls():
     scene = synth.make_urban_scene(50_000, seed=5)
     st = R.scene_to_device(scene)
