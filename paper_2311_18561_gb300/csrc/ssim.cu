@@ -31,16 +31,20 @@ constexpr int kX = kT + 4 * kR;      // staged input region (52)
 constexpr int kThreads = 384;  // one round of the largest pass (364 strips)
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
-// shared layout, in floats
+// shared layout, in floats.  The staged inputs are dead after the first
+// row pass, so a, b, c take their place (the gradient pass reads x and y
+// of its own pixels from global memory again, where they are L2 hits):
+// 65 KB per CTA, three CTAs per SM.
 constexpr int kOffX = 0, kOffY = kX * kX;
+constexpr int kOffABC = 0;                         // [3][kA][kA] over the inputs
+static_assert(3 * kA * kA <= 2 * kX * kX, "a, b, c fit where the inputs were");
 constexpr int kOffH = 2 * kX * kX;                 // 5 row-filtered moments [5][kX][kA]
-constexpr int kOffABC = kOffH + 5 * kX * kA;       // [3][kA][kA]
 constexpr int kOffH2 = kOffH;                      // row-filtered a, b, c [3][kA][kT] (reuses the moments)
-constexpr int kOffG = kOffABC + 3 * kA * kA;       // 11 window taps
+constexpr int kOffG = kOffH + 5 * kX * kA;         // 11 window taps
 constexpr int kOffRed = kOffG + 12;                // 2 x 16 warp partials
 constexpr int kSmemFloats = kOffRed + 32;
 
-__global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__ pred,
+__global__ void __launch_bounds__(kThreads, 3) k_rgb_loss(const float *__restrict__ pred,
                                                        const float *__restrict__ tgt, int H, int W,
                                                        float lambda_r, float inv_n, float *__restrict__ dl,
                                                        float2 *__restrict__ partial) {
@@ -103,7 +107,9 @@ __global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__
     }
     __syncthreads();
     // column pass -> S and its moment derivatives a, b, c on the tile + R
-    // halo: every column, strips of 6 rows (7 per column)
+    // halo: every column, strips of 6 rows (7 per column).  The row pass
+    // was the inputs' last reader (barrier above), so a, b, c are written
+    // over them.
     float ssum = 0.f, l1sum = 0.f;
     for (int k = tid; k < kA * 7; k += kThreads) {
         const int c = k % kA, r0 = (k / kA) * 6;
@@ -141,11 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__
                 a = fmaf(-2.f * mx, dvx, fmaf(-my, dcxy, dmu));
                 b = dvx;
                 cc = dcxy;
-                if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {
-                    ssum += S;
-                    const int s_idx = (r + kR) * kX + (c + kR);
-                    l1sum += fabsf(sx[s_idx] - sy[s_idx]);
-                }
+                if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) ssum += S;
             }
             abc[0 * kA * kA + r * kA + c] = a;
             abc[1 * kA * kA + r * kA + c] = b;
@@ -172,35 +174,40 @@ __global__ void __launch_bounds__(kThreads) k_rgb_loss(const float *__restrict__
         }
     }
     __syncthreads();
-    // column pass and the gradient of the tile's pixels: strips of 4 rows
-    if (dl) {
+    // column pass and the gradient of the tile's pixels (strips of 4 rows),
+    // and the L1 term of those pixels (x, y again from global memory)
+    {
         const float kl1 = (1.0f - lambda_r) * inv_n, kss = lambda_r * inv_n;
-        float *D = dl + blockIdx.z * plane;
+        float *D = dl ? dl + blockIdx.z * plane : nullptr;
         for (int k = tid; k < kT * 8; k += kThreads) {
             const int c = k % kT, r0 = (k / kT) * 4, gx = tx0 + c;
             float q[3][4];
+            if (D) {
 #pragma unroll
-            for (int t = 0; t < 3; t++) {
-                float v[14];
+                for (int t = 0; t < 3; t++) {
+                    float v[14];
 #pragma unroll
-                for (int i = 0; i < 14; i++) v[i] = h2[t * kA * kT + (r0 + i) * kT + c];
+                    for (int i = 0; i < 14; i++) v[i] = h2[t * kA * kT + (r0 + i) * kT + c];
 #pragma unroll
-                for (int o = 0; o < 4; o++) {
-                    float acc = 0.f;
+                    for (int o = 0; o < 4; o++) {
+                        float acc = 0.f;
 #pragma unroll
-                    for (int i = 0; i < 11; i++) acc = fmaf(gw[i], v[o + i], acc);
-                    q[t][o] = acc;
+                        for (int i = 0; i < 11; i++) acc = fmaf(gw[i], v[o + i], acc);
+                        q[t][o] = acc;
+                    }
                 }
             }
 #pragma unroll
             for (int o = 0; o < 4; o++) {
                 const int r = r0 + o, gy = ty0 + r;
                 if (gx >= W || gy >= H) continue;
-                const int s_idx = (r + 2 * kR) * kX + (c + 2 * kR);
-                const float x = sx[s_idx], y = sy[s_idx], d = x - y;
-                const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-                const float dssim = q[0][o] + 2.f * x * q[1][o] + y * q[2][o];
-                D[(size_t)gy * W + gx] = kl1 * sgn - kss * dssim;
+                const float x = X[(size_t)gy * W + gx], y = Y[(size_t)gy * W + gx], d = x - y;
+                l1sum += fabsf(d);
+                if (D) {
+                    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                    const float dssim = q[0][o] + 2.f * x * q[1][o] + y * q[2][o];
+                    D[(size_t)gy * W + gx] = kl1 * sgn - kss * dssim;
+                }
             }
         }
     }
