@@ -32,8 +32,12 @@ constexpr int kMaxScanBlocks = 1024;
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
+// keys per thread of the radix passes: 16 for large sorts (fewer tiles,
+// fewer barriers per key), 4 when the capacity is at most
+// kSmallSort (a block's chain of dependent steps is shorter)
 constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+constexpr int kSmallItems = 4;
+constexpr uint32_t kSmallSort = 4u << 20;
 constexpr int kRadix = 256;
 constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
 
@@ -192,8 +196,8 @@ int scan_blocks(uint32_t capacity) {
     return (int)g;
 }
 
-int sort_blocks(uint32_t capacity) {
-    uint32_t g = (capacity + kSortTile - 1) / kSortTile;
+int sort_blocks(uint32_t capacity, int tile) {
+    uint32_t g = (capacity + tile - 1) / tile;
     if (g < 1) g = 1;
     if (g > kMaxSortBlocks) g = kMaxSortBlocks;
     return (int)g;
@@ -201,6 +205,7 @@ int sort_blocks(uint32_t capacity) {
 
 // ---------------------------------------------------------------- radix
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *keys, const uint32_t *d_n,
                                                                 uint32_t cap, int shift, uint32_t mask,
                                                                 uint32_t *hist) {
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) sh[d] = 0;
     __syncthreads();
     uint32_t b0, b1;
-    segment_of(min(*d_n, cap), gridDim.x, kSortTile, &b0, &b1);
+    segment_of(min(*d_n, cap), gridDim.x, kSortThreads * ITEMS, &b0, &b1);
     for (uint32_t i = b0 + threadIdx.x; i < b1; i += kSortThreads) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * gridDim.x + blockIdx.x] = sh[d];
@@ -377,15 +382,17 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
 
 static_assert(kSortThreads == kRadix, "one thread per digit in the downsweep");
 
+template <int TILE>
 struct SortSmem {
     uint32_t base[kRadix];                // running global offset per digit
     uint32_t warp_hist[kSortWarps][kRadix];
     uint32_t tile_start[kRadix];
-    uint32_t keys[kSortTile];
-    uint32_t vals[kSortTile];
+    uint32_t keys[TILE];
+    uint32_t vals[TILE];
     uint32_t scan[33];
 };
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
                                                                   const uint32_t *__restrict__ vals_in,
                                                                   uint32_t *__restrict__ keys_out,
@@ -393,7 +400,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
                                                                   const uint32_t *d_n, uint32_t cap, int shift,
                                                                   uint32_t mask, const uint32_t *hist,
                                                                   const uint32_t *totals) {
-    __shared__ SortSmem S;
+    constexpr int kSortTile = kSortThreads * ITEMS;
+    __shared__ SortSmem<kSortTile> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         // digit bases: exclusive prefix of the per-digit totals (one thread per digit)
@@ -407,17 +415,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
     for (uint32_t t0 = b0; t0 < b1; t0 += kSortTile) {
         for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&S.warp_hist[0][0])[k] = 0;
         __syncthreads();
-        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-        bool valid[kSortItems];
+        uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+        bool valid[ITEMS];
 #pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
-            const uint32_t pos = t0 + warp * (32 * kSortItems) + j * 32 + lane;
+        for (int j = 0; j < ITEMS; j++) {
+            const uint32_t pos = t0 + warp * (32 * ITEMS) + j * 32 + lane;
             valid[j] = pos < b1;
             key[j] = valid[j] ? keys_in[pos] : 0u;
             val[j] = valid[j] ? vals_in[pos] : 0u;
         }
 #pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             const uint32_t d = (key[j] >> shift) & mask;
             uint32_t peers = __ballot_sync(0xffffffffu, valid[j]);
 #pragma unroll
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kSortItems; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             if (!valid[j]) continue;
             const uint32_t d = (key[j] >> shift) & mask;
             const uint32_t p = S.tile_start[d] + S.warp_hist[warp][d] + rank[j];
@@ -532,11 +540,26 @@ void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, vo
     k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
 }
 
+template <int ITEMS>
+void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_count,
+                  uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt);
+
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
                       cudaStream_t s, bool *result_in_alt) {
+    if (capacity <= kSmallSort)
+        radix_passes<kSmallItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
+                                  result_in_alt);
+    else
+        radix_passes<kSortItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
+                                 result_in_alt);
+}
+
+template <int ITEMS>
+void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_count,
+                  uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt) {
     TempLayout t = temp_layout(temp);
-    const int G = sort_blocks(capacity);
+    const int G = sort_blocks(capacity, kSortThreads * ITEMS);
     bool alt = false;
     for (int b = begin_bit; b < end_bit;) {
         const int nb = (end_bit - b) >= 8 ? 8 : (end_bit - b);
@@ -546,11 +569,12 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
         note_launch();
-        k_radix_upsweep<<<G, kSortThreads, 0, s>>>(ki, d_count, capacity, b, mask, t.hist);
+        k_radix_upsweep<ITEMS><<<G, kSortThreads, 0, s>>>(ki, d_count, capacity, b, mask, t.hist);
         note_launch();
         k_radix_scan<<<kRadix, 1024, 0, s>>>(t.hist, t.totals, G);
         note_launch();
-        k_radix_downsweep<<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist, t.totals);
+        k_radix_downsweep<ITEMS><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist,
+                                                           t.totals);
         alt = !alt;
         b += nb;
     }
