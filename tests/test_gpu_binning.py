@@ -106,3 +106,51 @@ def test_backward_matches_oracle():
         nr = np.linalg.norm(rr)
         assert nr > 0, k
         assert np.linalg.norm(g - rr) / nr <= 1e-2, k
+
+
+def _strip_scene(axis, seed=31):
+    """2,000 Gaussians in a thin slab around the image's long axis (world
+    axis `axis` spans it), a few of them huge (footprints wider than 255
+    tiles of 8 pixels: no row table)."""
+    scene = synth.make_plain_scene(seed=seed, n=2000)
+    rng = np.random.default_rng(seed)
+    other = 1 - axis
+    scene["mu"][:, other] = rng.uniform(-0.002, 0.002, 2000).astype(np.float32)
+    scene["vel"][:, other] = 0.0
+    scene["scale"][:8] = rng.uniform(1.5, 3.0, size=(8, 3)).astype(np.float32)
+    scene["opacity"][:8] = 0.2
+    return scene
+
+
+@pytest.mark.parametrize("shape", [(16384, 24), (24, 16384)])
+def test_maximum_image_size(shape):
+    """The largest accepted image side (16384 pixels) renders like the
+    oracle at sampled pixels, with 8x8 tiles (2048 tiles along the long
+    side); one pixel more is rejected."""
+    W, H = shape
+    scene = _strip_scene(0 if W > H else 1)
+    vm = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0))
+    cam = synth.make_camera(vm, W, H, 4000.0, t=0.5, bg=(0.05, 0.1, 0.15))
+    r = R.Renderer(tile=(8, 8), pixels_per_thread=1)
+    fr = R.Frame()
+    out = gpu_render(r, R.scene_to_device(scene), [cam], frame=fr)[0]
+    tx, ty = R.tiles_of(cam, (8, 8))
+    rect = fr.export(tx * ty)["rect"]
+    assert np.any(rect[:, 2] - rect[:, 0] > 255) or np.any(rect[:, 3] - rect[:, 1] > 255)
+    rng = np.random.default_rng(1)
+    long_ = max(W, H)
+    a = np.concatenate([rng.integers(0, long_, 600), rng.integers(long_ // 2 - 1500, long_ // 2 + 1500, 600)])
+    b = rng.integers(0, min(W, H), a.size)
+    pix = np.stack([a, b], 1) if W > H else np.stack([b, a], 1)
+    ref = oracle.render(scene, cam, mode="culled", pixels=pix)
+    img = to_numpy_images(out)
+    got = {k: img[k][pix[:, 1], pix[:, 0]] for k in ("rgb", "depth", "alpha")}
+    compare_to_oracle(got, ref, pixels=pix)
+    assert float(img["alpha"].max()) > 0.5  # the strip is not empty
+    r.close()
+    fr.close()
+    too_big = synth.make_camera(vm, W + (W > H), H + (H > W), 4000.0)
+    r2 = R.Renderer()
+    with pytest.raises(Exception):
+        r2.forward(R.scene_to_device(scene), [too_big])
+    r2.close()
