@@ -190,6 +190,7 @@ struct pvg_ctx {
     pvg_config_t cfg;
     DevBuf views;
     DevBuf item_cnt, item_zkey;  // [NV]
+    DevBuf proj;                 // [NV * 4] float4: projections from pass 1 to pass 2
     DevBuf alt_keys, alt_vals;   // [NV] depth sort ping-pong
     DevBuf pair_keys, pair_keys2, pair_vals2;  // [K]
     DevBuf vis_off;              // [NV]
@@ -306,7 +307,7 @@ extern "C" pvg_status_t pvg_create(pvg_ctx_t **ctx, const pvg_config_t *cfg) {
 extern "C" void pvg_destroy(pvg_ctx_t *x) {
     if (!x) return;
     cudaDeviceSynchronize();
-    for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->alt_keys, &x->alt_vals, &x->pair_keys,
+    for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->proj, &x->alt_keys, &x->alt_vals, &x->pair_keys,
                       &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n, &x->vis_off, &x->chunk_start,
                       &x->loss_partials})
         release(*b);
@@ -511,6 +512,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     // workspace
     PVG_TRY(ensure_c(x->item_cnt, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(x->item_zkey, sizeof(uint32_t) * NV, capturing));
+    PVG_TRY(ensure_c(x->proj, sizeof(float4) * 4 * (size_t)NV, capturing));
     PVG_TRY(ensure_c(x->alt_keys, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(x->alt_vals, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(x->vis_off, sizeof(uint32_t) * NV, capturing));
@@ -573,6 +575,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     p.counters = ptr<uint32_t>(f->counters);
     p.item_cnt = ptr<uint32_t>(x->item_cnt);
     p.item_zkey = ptr<uint32_t>(x->item_zkey);
+    p.proj = ptr<float4>(x->proj);
     p.sgid = ptr<uint32_t>(f->sgid);
     p.inv = ptr<uint32_t>(f->inv);
     p.szkey = ptr<uint32_t>(f->szkey);

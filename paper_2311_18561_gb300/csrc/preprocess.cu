@@ -6,14 +6,13 @@
 //                    footprint; writes the tile count and depth bits of
 //                    every item.
 //   k_finalize       (stage a, pass 2) for every visible item, in gid
-//                    order: the same projection plus the SH colour; writes
+//                    order: pass 1's stored projection plus the SH colour; writes
 //                    the 48-byte compositing record, the tile rectangle and
 //                    the count of its tiles that the footprint ellipse
 //                    meets, at the item's depth position m.
 //
-// Both passes compute the projection with the same inline function and
-// this file is compiled with --fmad=false, so pass 1 and pass 2 agree bit
-// for bit (their tile counts must match).  Every kernel is HBM-bound: one
+// Pass 1 stores each visible item's projection (64 bytes, item order) and
+// pass 2 reads it back, so both use the same bits.  Every kernel is HBM-bound: one
 // thread per item, grid-stride.  The adjoint is in preprocess_bwd.cu.
 #include "preprocess_common.cuh"
 
@@ -36,7 +35,16 @@ __global__ void __launch_bounds__(256) k_project_count(Params P) {
         Fwd F;
         const bool vis = project(V, g - V.item_base, P.dilation, P.tile_w, P.tile_h, F);
         P.item_cnt[g] = vis ? F.count : 0u;
-        if (vis) P.item_zkey[g] = __float_as_uint(F.p.z);
+        if (vis) {
+            P.item_zkey[g] = __float_as_uint(F.p.z);
+            // what the finalize pass needs of the projection, so that it
+            // reads 64 bytes instead of the item's parameters again
+            float4 *q = P.proj + 4 * (size_t)g;
+            q[0] = make_float4(F.u, F.v, F.ca, F.cb);
+            q[1] = make_float4(F.cc, F.ot, F.hx, F.hy);
+            q[2] = make_float4(F.mut.x, F.mut.y, F.mut.z, __uint_as_float(F.tx0 | (F.ty0 << 16)));
+            q[3] = make_float4(__uint_as_float(F.tx1 | (F.ty1 << 16)), 0.f, 0.f, 0.f);
+        }
     }
 }
 
@@ -61,13 +69,15 @@ __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
         const int view = view_of_item(P.views, P.n_views, g);
         const ViewDesc &V = P.views[view];
         const uint32_t i = g - V.item_base;
+        // the projection as pass 1 computed and stored it
+        const float4 *pq = P.proj + 4 * (size_t)g;
+        const float4 q0 = pq[0], q1 = pq[1], q2 = pq[2], q3 = pq[3];
         Fwd F;
-        const bool vis = project(V, i, P.dilation, P.tile_w, P.tile_h, F);
-        if (!vis) {  // cannot happen (same arithmetic as pass 1); stay safe
-            P.vis_cnt[m] = 0u;
-            P.rect[m] = make_uint2(0u, 0u);
-            continue;
-        }
+        F.u = q0.x; F.v = q0.y; F.ca = q0.z; F.cb = q0.w;
+        F.cc = q1.x; F.ot = q1.y; F.hx = q1.z; F.hy = q1.w;
+        F.mut = make_float3(q2.x, q2.y, q2.z);
+        const uint32_t r0 = __float_as_uint(q2.w), r1 = __float_as_uint(q3.x);
+        F.tx0 = r0 & 0xffffu; F.ty0 = r0 >> 16; F.tx1 = r1 & 0xffffu; F.ty1 = r1 >> 16;
         float dx = F.mut.x - V.campos[0], dy = F.mut.y - V.campos[1], dz = F.mut.z - V.campos[2];
         const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
         dx *= inv; dy *= inv; dz *= inv;

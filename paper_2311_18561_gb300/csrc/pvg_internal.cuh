@@ -85,6 +85,7 @@ struct Params {
     // per-item scratch
     uint32_t *item_cnt;      // [NV] tiles touched (0 = invisible)
     uint32_t *item_zkey;     // [NV] depth bits (valid where item_cnt > 0)
+    float4 *proj;            // [NV * 4] projection of each visible item (pass 1 -> pass 2)
     // visible
     uint32_t *sgid;          // [M]
     uint32_t *inv;           // [NV] depth position of each item, 0xffffffff if not visible
