@@ -392,7 +392,8 @@ struct SortSmem {
     uint32_t scan[33];
 };
 
-template <int ITEMS>
+// NB: ballots per key in the ranking (the pass's digit width, or 8)
+template <int ITEMS, int NB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
                                                                   const uint32_t *__restrict__ vals_in,
                                                                   uint32_t *__restrict__ keys_out,
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
             const uint32_t d = (key[j] >> shift) & mask;
             uint32_t peers = __ballot_sync(0xffffffffu, valid[j]);
 #pragma unroll
-            for (int bit = 0; bit < 8; bit++) {
+            for (int bit = 0; bit < NB; bit++) {
                 const bool on = (d >> bit) & 1u;
                 const uint32_t b = __ballot_sync(0xffffffffu, on);
                 peers &= on ? b : ~b;
@@ -573,8 +574,16 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
         note_launch();
         k_radix_scan<<<kRadix, 1024, 0, s>>>(t.hist, t.totals, G);
         note_launch();
-        k_radix_downsweep<ITEMS><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, t.hist,
-                                                           t.totals);
+        switch (nb) {  // the digit widths of the depth sort (31 bits) and tile sorts of up to 2^16 tiles
+            case 3: k_radix_downsweep<ITEMS, 3><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
+                                                                           t.hist, t.totals); break;
+            case 5: k_radix_downsweep<ITEMS, 5><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
+                                                                           t.hist, t.totals); break;
+            case 7: k_radix_downsweep<ITEMS, 7><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
+                                                                           t.hist, t.totals); break;
+            default: k_radix_downsweep<ITEMS, 8><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
+                                                                             t.hist, t.totals); break;
+        }
         alt = !alt;
         b += nb;
     }
