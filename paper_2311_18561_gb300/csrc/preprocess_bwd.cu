@@ -1,6 +1,7 @@
 // preprocess_bwd.cu -- adjoint of the per-item projection and colour
-// (stage d2): in item order, from the image-space gradients of record
-// m = inv[g] to dL/d{mu, v, tau, beta, l, s, q, o, sh} (Sec. 3.1, Eq. 2-4;
+// (stage d2): for the visible items in gid order, from the image-space
+// gradients of record m = inv[g] to dL/d{mu, v, tau, beta, l, s, q, o, sh}
+// (Sec. 3.1, Eq. 2-4;
 // Sec. 3.2, Eq. 6-8; the flow shift of Sec. 3.4).  Visibility comes from
 // inv[]; the projection is recomputed for its intermediate terms only, so
 // this file may contract a*b+c into fused multiply-adds.
