@@ -3,9 +3,10 @@
 //
 // Forward pass on one stream (no host round trip except the optional pair
 // count read-back that sizes the pair buffers):
-//   a  k_project_count      items -> tile count, depth bits
+//   a  k_project_count      items -> tile count, depth bits, projection
 //      compact_visible      visible items in gid order -> (zbits, gid), M
-//   b  radix sort           by depth bits (4 passes of <= 8 bits)
+//   b  radix sort           by depth bits (4 passes of <= 8 bits); the last
+//                           pass also writes inv[gid] = depth position
 //   a  k_finalize           records, rects, counts in depth order
 //   b  scan + emit          (tile, m) pairs in depth order, K
 //      radix sort           by tile id (ceil(log2 tiles) bits)
@@ -605,8 +606,11 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
         tm.begin(PVG_STAGE_DEPTH_SORT, s);
         compact_visible(p, p.szkey, p.sgid, x->temp.p, s);
         bool in_alt = false;
+        // the sort's last pass also writes the inverse map inv[gid] = depth
+        // position (0xffffffff stays for the invisible items)
+        PVG_CUDA(cudaMemsetAsync(p.inv, 0xff, sizeof(uint32_t) * NV, s));
         radix_sort_pairs(p.szkey, p.sgid, ptr<uint32_t>(x->alt_keys), ptr<uint32_t>(x->alt_vals), &p.counters[0], NV,
-                         0, 31, x->temp.p, s, &in_alt);
+                         0, 31, x->temp.p, s, &in_alt, p.inv);
         if (in_alt) {  // 31 bits = 4 passes: never taken, kept for safety
             PVG_CUDA(cudaMemcpyAsync(p.szkey, x->alt_keys.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
             PVG_CUDA(cudaMemcpyAsync(p.sgid, x->alt_vals.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
@@ -614,8 +618,6 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
         tm.end(PVG_STAGE_DEPTH_SORT, s);
         // (a) records in depth order, (b) pair count
         tm.begin(PVG_STAGE_FINALIZE, s);
-        PVG_CUDA(cudaMemsetAsync(p.inv, 0xff, sizeof(uint32_t) * NV, s));
-        launch_scatter_inv(p, s);
         launch_finalize(p, s);
         tm.end(PVG_STAGE_FINALIZE, s);
         tm.begin(PVG_STAGE_PAIRS, s);

@@ -48,13 +48,6 @@ __global__ void __launch_bounds__(256) k_project_count(Params P) {
     }
 }
 
-// inverse of the depth order: inv[sgid[m]] = m (inv is 0xffffffff elsewhere)
-__global__ void __launch_bounds__(256) k_scatter_inv(Params P) {
-    const uint32_t M = P.counters[0];
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x)
-        P.inv[P.sgid[m]] = m;
-}
-
 // Records in depth order, computed over the visible items in gid order
 // (the compacted list: every lane has an item, parameter reads stay in gid
 // order; the 48-byte record goes to its depth position m = inv[g]).
@@ -122,11 +115,6 @@ __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
 void launch_project_count(const Params &p, cudaStream_t s) {
     note_launch();
     k_project_count<<<grid_for(p.n_items), 256, 0, s>>>(p);
-}
-
-void launch_scatter_inv(const Params &p, cudaStream_t s) {
-    note_launch();
-    k_scatter_inv<<<grid_for(p.n_items), 256, 0, s>>>(p);
 }
 
 void launch_finalize(const Params &p, cudaStream_t s) {

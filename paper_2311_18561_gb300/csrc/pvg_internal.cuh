@@ -386,15 +386,16 @@ void note_launch();
 cudaError_t set_sh_constants();      // both copies of the SH constants
 cudaError_t set_sh_constants_bwd();  // the adjoint's copy
 void launch_project_count(const Params &p, cudaStream_t s);
-void launch_scatter_inv(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);
 void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s);
 // sort / scan
 size_t sort_temp_bytes(uint32_t capacity);
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);
+// inv_out (optional): the last pass also writes inv_out[value] = the
+// value's final position
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                      cudaStream_t s, bool *result_in_alt);
+                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out = nullptr);
 void scan_count_pairs(const Params &p, void *temp, cudaStream_t s);
 void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
 size_t emit_chunks(uint32_t capacity);

@@ -400,7 +400,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
                                                                   uint32_t *__restrict__ vals_out,
                                                                   const uint32_t *d_n, uint32_t cap, int shift,
                                                                   uint32_t mask, const uint32_t *hist,
-                                                                  const uint32_t *totals) {
+                                                                  const uint32_t *totals,
+                                                                  uint32_t *__restrict__ inv_out) {
     constexpr int kSortTile = kSortThreads * ITEMS;
     __shared__ SortSmem<kSortTile> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -473,6 +474,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
             const uint32_t dst = S.base[d] + (p - S.tile_start[d]);
             keys_out[dst] = k;
             vals_out[dst] = S.vals[p];
+            if (inv_out) inv_out[S.vals[p]] = dst;
         }
         __syncthreads();
         S.base[tid] += tile_cnt;
@@ -543,22 +545,24 @@ void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, vo
 
 template <int ITEMS>
 void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_count,
-                  uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt);
+                  uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt,
+                  uint32_t *inv_out);
 
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                      cudaStream_t s, bool *result_in_alt) {
+                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out) {
     if (capacity <= kSmallSort)
         radix_passes<kSmallItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
-                                  result_in_alt);
+                                  result_in_alt, inv_out);
     else
         radix_passes<kSortItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
-                                 result_in_alt);
+                                 result_in_alt, inv_out);
 }
 
 template <int ITEMS>
 void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_count,
-                  uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt) {
+                  uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt,
+                  uint32_t *inv_out) {
     TempLayout t = temp_layout(temp);
     const int G = sort_blocks(capacity, kSortThreads * ITEMS);
     bool alt = false;
@@ -574,15 +578,16 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
         note_launch();
         k_radix_scan<<<kRadix, 1024, 0, s>>>(t.hist, t.totals, G);
         note_launch();
+        uint32_t *inv_pass = b + nb >= end_bit ? inv_out : nullptr;  // the last pass only
         switch (nb) {  // the digit widths of the depth sort (31 bits) and tile sorts of up to 2^16 tiles
             case 3: k_radix_downsweep<ITEMS, 3><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                           t.hist, t.totals); break;
+                                                                           t.hist, t.totals, inv_pass); break;
             case 5: k_radix_downsweep<ITEMS, 5><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                           t.hist, t.totals); break;
+                                                                           t.hist, t.totals, inv_pass); break;
             case 7: k_radix_downsweep<ITEMS, 7><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                           t.hist, t.totals); break;
+                                                                           t.hist, t.totals, inv_pass); break;
             default: k_radix_downsweep<ITEMS, 8><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                             t.hist, t.totals); break;
+                                                                             t.hist, t.totals, inv_pass); break;
         }
         alt = !alt;
         b += nb;
