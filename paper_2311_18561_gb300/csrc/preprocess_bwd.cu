@@ -310,7 +310,14 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     __shared__ float s_g[kSmall][kChunk];
     __shared__ uint16_t s_list[kChunk];
     __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_vis[kChunk / 32];  // visible items of the chunk (bits)
+
     const ViewDesc &V = P.views[0];  // one view: item g is Gaussian g (item_base 0)
+    // SH rows of invisible items are zeroed by the whole block as
+    // consecutive float4 (whole sectors per instruction) when the rows are
+    // whole float4 and aligned; else by each item's thread
+    constexpr bool kRows4 = (3 * K) % 4 == 0;
+    const bool rows4 = kRows4 && V.g_sh && aligned16(V.g_sh);
     const uint32_t n = P.n_items;
     const int tid = threadIdx.x;
     for (uint32_t base = blockIdx.x * kChunk; base < n; base += gridDim.x * kChunk) {
@@ -323,17 +330,19 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
             mv[q] = g < n ? P.inv[g] : 0xffffffffu;
             cnt += mv[q] != 0xffffffffu ? 1u : 0u;
         }
+        if (tid < kChunk / 32) s_vis[tid] = 0u;
         uint32_t nvis;
-        uint32_t pos = block_excl_scan_u32(cnt, s_scan, &nvis);
+        uint32_t pos = block_excl_scan_u32(cnt, s_scan, &nvis);  // (its barriers order s_vis)
 #pragma unroll
         for (int q = 0; q < kPer; q++) {
             const int idx = tid * kPer + q;
             if (mv[q] != 0xffffffffu) {
                 s_list[pos++] = (uint16_t)idx;
+                atomicOr(&s_vis[idx >> 5], 1u << (idx & 31));
             } else if (base + idx < n) {
 #pragma unroll
                 for (int f = 0; f < kSmall; f++) s_g[f][idx] = 0.f;
-                if (V.g_sh) {
+                if (V.g_sh && !rows4) {
                     float z[3 * K];
 #pragma unroll
                     for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
@@ -342,6 +351,17 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
             }
         }
         __syncthreads();
+        if constexpr (kRows4) {
+            if (rows4) {  // zero SH rows of the invisible items, block-wide
+                constexpr int R4 = 3 * K / 4;
+                float4 *sh4 = reinterpret_cast<float4 *>(V.g_sh + (size_t)base * 3 * K);
+                const uint32_t cn4 = min((uint32_t)kChunk, n - base) * R4;
+                for (uint32_t e = tid; e < cn4; e += 256) {
+                    const uint32_t item = e / R4;
+                    if (!((s_vis[item >> 5] >> (item & 31)) & 1u)) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
         // the visible items, compacted
         for (uint32_t k = tid; k < nvis; k += 256) {
             const int idx = s_list[k];
