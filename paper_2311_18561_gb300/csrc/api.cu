@@ -162,7 +162,6 @@ struct pvg_frame {
     DevBuf sgid, szkey;         // [NV]
     DevBuf inv;                 // [NV] depth position per item
     DevBuf rec;                 // [NV * 3] float4
-    DevBuf vis_items;           // [NV] visible gids in gid order
     DevBuf ell;                 // [NV * 2] float4 footprint ellipses
     DevBuf rowtab;              // [NV] uint4 packed tile rows
     DevBuf rect, vis_cnt;       // [NV]
@@ -269,7 +268,7 @@ extern "C" pvg_status_t pvg_frame_create(pvg_frame_t **frame) {
 extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
-    for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->vis_items, &f->ell, &f->rowtab, &f->rect, &f->vis_cnt, &f->pair_vals,
+    for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->ell, &f->rowtab, &f->rect, &f->vis_cnt, &f->pair_vals,
                       &f->ranges, &f->tile_order, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d, &f->gfeat})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
@@ -521,7 +520,6 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     PVG_TRY(ensure_c(f->inv, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(f->szkey, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(f->rec, sizeof(float4) * 3 * (size_t)NV, capturing));
-    PVG_TRY(ensure_c(f->vis_items, sizeof(uint32_t) * (size_t)NV, capturing));
     PVG_TRY(ensure_c(f->ell, sizeof(float4) * 2 * (size_t)NV, capturing));
     PVG_TRY(ensure_c(f->rowtab, sizeof(uint4) * (size_t)NV, capturing));
     PVG_TRY(ensure_c(f->rect, sizeof(uint2) * NV, capturing));
@@ -580,7 +578,6 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     p.sgid = ptr<uint32_t>(f->sgid);
     p.inv = ptr<uint32_t>(f->inv);
     p.szkey = ptr<uint32_t>(f->szkey);
-    p.vis_items = ptr<uint32_t>(f->vis_items);
     p.rec = ptr<float4>(f->rec);
     p.ell = ptr<float4>(f->ell);
     p.rowtab = ptr<uint4>(f->rowtab);
@@ -766,7 +763,6 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     p.counters = ptr<uint32_t>(f->counters);
     p.sgid = ptr<uint32_t>(f->sgid);
     p.inv = ptr<uint32_t>(f->inv);
-    p.vis_items = ptr<uint32_t>(f->vis_items);
     p.szkey = ptr<uint32_t>(f->szkey);
     p.rec = ptr<float4>(f->rec);
     p.rect = ptr<uint2>(f->rect);

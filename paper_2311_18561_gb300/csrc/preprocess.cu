@@ -5,7 +5,7 @@
 //                    EWA projection (Sec. 3.1, Eq. 2) and the tile
 //                    footprint; writes the tile count and depth bits of
 //                    every item.
-//   k_finalize       (stage a, pass 2) for every visible item, in gid
+//   k_finalize       (stage a, pass 2) for every visible item, in depth
 //                    order: pass 1's stored projection plus the SH colour; writes
 //                    the 48-byte compositing record, the tile rectangle and
 //                    the count of its tiles that the footprint ellipse
@@ -48,17 +48,16 @@ __global__ void __launch_bounds__(256) k_project_count(Params P) {
     }
 }
 
-// Records in depth order, computed over the visible items in gid order
-// (the compacted list: every lane has an item, parameter reads stay in gid
-// order; the 48-byte record goes to its depth position m = inv[g]).
+// Records in depth order, one thread per depth position m (item g =
+// sgid[m]): the writes are coalesced, and the reads of g's stored
+// projection (64 bytes) and SH row (192 bytes at degree 3) are whole
+// sectors in any order.
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
     constexpr int K = (D + 1) * (D + 1);
     const uint32_t M = P.counters[0];
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        const uint32_t g = P.vis_items[j];
-        const uint32_t m = P.inv[g];
-        if (m == 0xffffffffu) continue;
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const uint32_t g = P.sgid[m];
         const int view = view_of_item(P.views, P.n_views, g);
         const ViewDesc &V = P.views[view];
         const uint32_t i = g - V.item_base;

@@ -89,7 +89,6 @@ struct Params {
     // visible
     uint32_t *sgid;          // [M]
     uint32_t *inv;           // [NV] depth position of each item, 0xffffffff if not visible
-    uint32_t *vis_items;     // [M] gids of the visible items in gid order
     uint32_t *szkey;         // [M]
     float4 *rec;             // [M*3]
     float4 *ell;             // [M*2] footprint ellipses (store_ellipse)

@@ -101,14 +101,12 @@ struct CompactF {
     const uint32_t *cnt, *zkey;
     uint32_t *keys_out, *vals_out;
     uint32_t n_items;
-    uint32_t *items_out;  // the visible gids in gid order (kept after the sort)
     __device__ uint32_t n() const { return n_items; }
     __device__ uint32_t value(uint32_t i) const { return cnt[i] > 0u ? 1u : 0u; }
     __device__ void apply(uint32_t i, uint32_t off, uint32_t v) const {
         if (v) {
             keys_out[off] = zkey[i];
             vals_out[off] = i;
-            items_out[off] = i;
         }
     }
 };
@@ -533,7 +531,7 @@ size_t sort_temp_bytes(uint32_t) { return sizeof(uint32_t) * ((size_t)kRadix * k
 
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s) {
     TempLayout t = temp_layout(temp);
-    CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, p.n_items, p.vis_items};
+    CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, p.n_items};
     const int G = scan_blocks(p.n_items);
     note_launch();
     k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
