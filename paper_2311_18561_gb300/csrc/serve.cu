@@ -73,10 +73,13 @@ struct pvg_server {
 namespace {
 
 // working-memory estimate of one request: per-Gaussian buffers of its
-// scene, per-pixel state and an allowance of pairs per pixel
+// scene (204 bytes: counts, depth bits, stored projection, sort buffers and
+// offsets in the context; depth order, inverse map, record, footprint
+// ellipse, row table, rectangle and count in the frame), per-pixel state
+// and an allowance of pairs per pixel
 size_t request_bytes(const pvg_scene_t &sc, const pvg_camera_t &cam) {
     const size_t pix = (size_t)cam.width * cam.height;
-    return (size_t)sc.n * 132 + pix * 12 + pix * 6 * 16;
+    return (size_t)sc.n * 204 + pix * 12 + pix * 6 * 16;
 }
 
 void worker_loop(pvg_server *S, Worker *W) {
