@@ -561,11 +561,12 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
     srv = S.Server(max_batch_views=max_batch_views, n_streams=n_streams, memory_budget=24 << 30,
                    tile=config[:2], pixels_per_thread=config[2])
     ids = [srv.add_scene(sc) for sc in scenes]
-    # warm-up: grow every worker's workspace on the largest requests
+    # warm-up: grow every worker's workspace to the worst case, full
+    # batches of the largest scene at the largest resolution
     warm = []
     for k in range(2 * n_streams * max_batch_views):
         cam = synth.street_camera(0.5, 1920, 1280)
-        warm.append(srv.submit(ids[len(ids) - 1 - (k % len(ids))], cam, dict(rgb=buf(cam))))
+        warm.append(srv.submit(ids[-1], cam, dict(rgb=buf(cam))))
     for rid in warm:
         srv.wait(rid, 120.0)
         srv.release(rid)
