@@ -233,8 +233,9 @@ pvg_status_t pvg_set_config(pvg_ctx_t *ctx, const pvg_config_t *cfg);
 pvg_status_t pvg_frame_create(pvg_frame_t **frame);
 void pvg_frame_destroy(pvg_frame_t *frame);
 /* Counters of the last forward into `frame` (synchronises `frame`'s last
- * stream): visible (view, Gaussian) pairs, tile/Gaussian pairs and the
- * overflow status. */
+ * stream): visible (view, Gaussian) pairs, tile/Gaussian pairs (one per
+ * tile of a Gaussian's bounding rectangle that its footprint ellipse
+ * o~ G >= 1/255, slightly widened, reaches) and the overflow status. */
 pvg_status_t pvg_frame_stats(pvg_frame_t *frame, int64_t *n_visible, int64_t *n_pairs,
                              int32_t *overflowed);
 
@@ -432,10 +433,14 @@ pvg_status_t pvg_frame_eval_count(pvg_ctx_t *ctx, pvg_frame_t *frame, int64_t *e
  * caller-owned DEVICE buffers (any may be NULL), for parity testing:
  *   sorted_gid [n_visible]   (view * N + index) in (view-major via tiles, depth, index) order
  *   depth_key  [n_visible]   float32 bits of the camera depth, same order
- *   rect       [n_visible*4] tile rectangle (tx0, ty0, tx1, ty1), half-open, int32
+ *   rect       [n_visible*4] tile rectangle (tx0, ty0, tx1, ty1) of the footprint box,
+ *                            half-open, int32 (a Gaussian's pairs are the tiles of it
+ *                            that its footprint ellipse reaches)
  *   records    [n_visible*12] u, v, conic a, b, c, o~, z, hx, r, g, b, hy (float32;
  *                            hx, hy = footprint half extents in pixels)
- *   pair_vals  [n_pairs]     position in the depth order, sorted by (tile, depth, index)
+ *   pair_vals  [n_pairs]     position in the depth order, sorted by (tile, depth, index);
+ *                            each tile's list is that of the rectangles without the
+ *                            Gaussians whose footprint ellipse misses the tile
  *   ranges     [total_tiles*2] [start, end) per tile, tiles of view 0 first
  * Synchronises the frame's stream. */
 pvg_status_t pvg_frame_export(pvg_frame_t *frame, uint32_t *sorted_gid, uint32_t *depth_key,
