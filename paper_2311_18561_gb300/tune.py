@@ -2,8 +2,8 @@
 
 The compositor's tile shape and pixels per thread change only speed: every
 supported configuration produces bit-identical images (each pixel's
-arithmetic is the same expression; the footprint boxes are conservative
-for the alpha gate).  So the tuner may pick any of them by time alone: it
+arithmetic is the same expression; the tile binning is conservative for
+the alpha gate).  So the tuner may pick any of them by time alone: it
 renders the caller's workload (forward, optionally forward + backward) with
 every candidate, times each with CUDA events, and returns the fastest.
 Results are cached in a JSON file keyed by the workload's shape (Gaussian
