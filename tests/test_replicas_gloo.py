@@ -120,3 +120,4 @@ def test_data_parallel_gradient_sum():
     for _, g in res:
         for j, k in enumerate(R.PARAM_NAMES):
             assert (g[k] == total * (j + 1)).all(), k
+
