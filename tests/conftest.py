@@ -19,3 +19,13 @@ def oracle_lib():
 
     oracle.load()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    from tests import parity_log
+
+    lines = parity_log.summary_lines()
+    if lines:
+        terminalreporter.section("oracle parity: flagged pixels")
+        for line in lines:
+            terminalreporter.write_line(line)

@@ -6,6 +6,8 @@ import torch
 import oracle
 from oracle import binning
 
+from . import parity_log
+
 # Image tolerance: max-abs 1e-3 per channel in [0, 1] (rgb, alpha) on
 # pixels the oracle does not flag; flagged pixels (a gate within 1e-5
 # relative of its threshold, or two blended depths within 1e-6 relative:
@@ -13,6 +15,18 @@ from oracle import binning
 # rare.  Depth (metres, not in [0, 1]) is held to 1e-3 relative.
 TOL = 1e-3
 FLAG_TOL = 1.0 / 255.0 + 1e-3
+# Flagged pixels may be at most 0.1 % of the compared pixels (the 1.5M
+# urban frame at 1920x1280 flags 0.08 % of its sampled pixels).  Nearly all
+# flags are near-ties in depth (two blended Gaussians within 1e-6 relative)
+# and one such pair flags every pixel of its overlap, so scenes dense in
+# such pairs pass DENSE_TIE_FLAG_FRAC (2 %) explicitly: the small synthetic
+# scenes (a few hundred to 2,000 large Gaussians on a few thousand pixels:
+# up to 1.4 %) and the urban distribution at 1242x375 (200k to 1M
+# Gaussians: 0.5 to 1.8 %).  Either cap still holds at least 98 % of the
+# pixels to the 1e-3 bound; the real fractions are printed in the run's
+# terminal summary.
+MAX_FLAG_FRAC = 1e-3
+DENSE_TIE_FLAG_FRAC = 0.02
 
 
 def to_numpy_images(out):
@@ -21,7 +35,7 @@ def to_numpy_images(out):
                 alpha=out["alpha"].cpu().numpy().astype(np.float64))
 
 
-def compare_to_oracle(got, ref, pixels=None, max_flag_frac=0.05):
+def compare_to_oracle(got, ref, pixels=None, max_flag_frac=MAX_FLAG_FRAC):
     """got: dict of numpy arrays [H,W,(3)] or [P,(3)] if pixels given."""
     flag = ref["flag"] != 0
     e_rgb = np.abs(got["rgb"] - ref["rgb"]).max(axis=-1)
@@ -31,7 +45,10 @@ def compare_to_oracle(got, ref, pixels=None, max_flag_frac=0.05):
     ok = ~flag
     report = dict(max_rgb=float(e_rgb[ok].max(initial=0)), max_alpha=float(e_a[ok].max(initial=0)),
                   max_depth_rel=float(e_d[ok].max(initial=0)), flagged=int(flag.sum()),
-                  flagged_max=float(max(e_rgb[flag].max(initial=0), e_a[flag].max(initial=0))))
+                  flagged_max=float(max(e_rgb[flag].max(initial=0), e_a[flag].max(initial=0))),
+                  flagged_frac=float(flag.mean()))
+    parity_log.record("image", flag.size, flag.sum(), rgb=report["max_rgb"], alpha=report["max_alpha"],
+                      depth_rel=report["max_depth_rel"], flagged_max=report["flagged_max"])
     assert report["max_rgb"] <= TOL, report
     assert report["max_alpha"] <= TOL, report
     assert report["max_depth_rel"] <= TOL, report

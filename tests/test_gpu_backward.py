@@ -18,6 +18,9 @@ pytestmark = [pytest.mark.gpu,
 
 NAMES = R.PARAM_NAMES
 
+from .test_oracle_clamp import _camera as clamp_camera  # noqa: E402
+from .test_oracle_clamp import clamped_scene  # noqa: E402
+
 
 def _compare_grads(got, ref, rel=1e-2):
     report = {}
@@ -171,3 +174,33 @@ def test_backward_colour_only(cfg):
     torch.cuda.synchronize()
     ref = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), np.zeros((H, W)), np.zeros((H, W)))
     _compare_grads(grads, ref)
+
+
+@pytest.mark.parametrize("colour_only", [False, True])
+def test_backward_through_the_jacobian_clamp(colour_only):
+    """Gradients of a scene whose large Gaussians sit beyond the EWA
+    Jacobian's clamp limits (both axes, both sides), against the oracle's
+    reverse mode through its clamped branch."""
+    cam = clamp_camera()
+    cam["t"] = 0.45
+    cam["bg"] = np.array([0.2, 0.5, 0.8], np.float32)
+    scene, n_off = clamped_scene(cam, n=150, seed=2)
+    scene = {k: v.astype(np.float32) for k, v in scene.items()}  # the same bytes for both sides
+    H, W = cam["height"], cam["width"]
+    w_rgb, w_d, w_a = _weights(H, W, 21)
+    if colour_only:
+        w_d, w_a = np.zeros((H, W)), np.zeros((H, W))
+    r = R.Renderer()
+    fr = R.Frame()
+    st = R.scene_to_device(scene)
+    r.forward(st, [cam], frame=fr)
+    dl = dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"))
+    if not colour_only:
+        dl["depth"] = torch.tensor(w_d, dtype=torch.float32, device="cuda")
+        dl["alpha"] = torch.tensor(w_a, dtype=torch.float32, device="cuda")
+    grads = r.backward(st, [cam], fr, [dl])
+    torch.cuda.synchronize()
+    ref = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), w_d, w_a)
+    _compare_grads(grads, ref)
+    # the clamped Gaussians carry gradient
+    assert np.count_nonzero(np.abs(ref["mu"][:n_off]).sum(axis=1)) >= n_off - 2
