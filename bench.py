@@ -59,8 +59,7 @@ def workload_camera(frame):
     return synth.street_camera(frame / 49.0, W_PIX, H_PIX, fx=FOCAL)
 
 
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ = 2070.0  # nominal maximum SM clock (MEASURED_PEAKS.json's sm_max_mhz when present)
 # Algorithmic FP32 FMA-pipe lane-instructions of the compositor:
 # every in-footprint evaluation: 2 FADD (dx, dy), 4 FMUL + 2 FFMA (falloff
 # exponent, o~ G) = 8; every blended evaluation in addition, forward:
@@ -135,6 +134,43 @@ def peaks():
         return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=float(d.get("sm_max_mhz", SM_MAX_MHZ)))
     except Exception:
         return dict(hbm_gbs=6800.0, source="fallback", sm_max_mhz=SM_MAX_MHZ)
+
+
+def measure_fp32_peak(dev, seconds=1.2):
+    """FP32 lane-FMA rate of the part, measured with the library's FMA probe
+    (independent fused multiply-add chains, 2048 threads per SM), timed with
+    CUDA events over about `seconds`; the best launch counts.  Returns the
+    rate beside the SM count and the derived figure SMs x 128 lanes x the
+    maximum SM clock."""
+    import torch
+
+    from paper_2311_18561_gb300 import render as R
+
+    sms = R.device_sm_count()
+    props_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * sms
+    dst = torch.empty(blocks * 256, device=dev)
+    iters = 2000
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R.fma_probe(dst, blocks, iters)  # warm-up
+    torch.cuda.synchronize()
+    best, total, launches = 0.0, 0.0, 0
+    while total < seconds * 1e3 or launches < 5:
+        a.record()
+        lanes = R.fma_probe(dst, blocks, iters)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        total += ms
+        launches += 1
+        best = max(best, lanes / (ms * 1e-3))
+        if ms < 40.0:  # grow the launch to about 50 ms
+            iters = int(iters * min(8.0, 50.0 / max(ms, 1e-3)))
+    derived = sms * 128 * peaks()["sm_max_mhz"] * 1e6
+    return {"lane_fma_per_s": best, "sm_count": sms, "sm_count_torch": props_sms, "launches": launches,
+            "derived_lane_per_s": derived, "ratio_to_derived": best / derived,
+            "how": "pvg_fma_probe: %d blocks x 256 threads, 8 independent FMA chains per thread, best of %d "
+                   "launches of about 50 ms (CUDA events)" % (blocks, launches)}
 
 
 class ClockSampler:
@@ -277,7 +313,7 @@ def run_ours(args):
 
     def step():
         r.forward(st, [cam], outs=outs, frame=fr)
-        R.l1_loss(outs[0]["rgb"], target, dl=dl, loss=loss)
+        R.l1_loss(r, outs[0]["rgb"], target, dl=dl, loss=loss)
         r.backward(st, [cam], fr, [dict(rgb=dl)], grads=grads)
         if dp:
             R.allreduce_gradients(grad_flat)
@@ -337,6 +373,8 @@ def run_ours(args):
     launches = launches_per_step * args.steps
     # forward-only rate (same protocol)
     fwd_ms = timed(fwd_graph.replay, args.steps) / args.steps
+    # the FP32 peak of the ALU rooflines, at the clocks sampled here
+    fp32 = measure_fp32_peak(dev)
     clk = clocks.stop()
     # per-stage times from the library's event timer, in eager steps after
     # the timed region (the events add a little time of their own)
@@ -413,11 +451,11 @@ def run_ours(args):
         # separable filtering: 5 moments and 3 derivative maps x 2 passes x 11 taps,
         # 3 products, ~20 for S and its derivatives, 5 for the gradient, 3 for L1
         loss_ops = 3 * W_PIX * H_PIX * OPS_PER_LOSS_PIXEL
-        alu_peak = SM_COUNT * 128 * peaks()["sm_max_mhz"] * 1e6
+        alu_peak = fp32["lane_fma_per_s"]
         paper_loss = {"step_ms": paper_step_ms, "loss_ms": loss_ms,
                       "roofline_loss": {"kernel": "k_rgb_loss", "bound": "alu",
                                         "achieved": loss_ops / (loss_ms * 1e-3) / 1e12, "peak": alu_peak / 1e12,
-                                        "unit": "T FP32-lane-instr/s",
+                                        "unit": "T FP32-lane-instr/s", "peak_kind": "measured (FMA probe)",
                                         "frac": loss_ops / (loss_ms * 1e-3) / alu_peak,
                                         "work": "%d FP32 instructions per pixel and channel" % OPS_PER_LOSS_PIXEL,
                                         "hbm_bytes": 3 * W_PIX * H_PIX * 12,
@@ -436,7 +474,7 @@ def run_ours(args):
 
         def step_features():
             r.forward(st_f, [cam], outs=outs_f, frame=fr, features=fmask)
-            R.l1_loss(outs_f[0]["rgb"], target, dl=dl, loss=loss)
+            R.l1_loss(r, outs_f[0]["rgb"], target, dl=dl, loss=loss)
             r.backward(st_f, [cam], fr, [dict(rgb=dl, feat=dl_feat)], grads=grads_f)
 
         for _ in range(3):
@@ -451,7 +489,7 @@ def run_ours(args):
     dominant = max(stage_ms, key=stage_ms.get)
     pk = peaks()
     roof = None
-    alu_peak = SM_COUNT * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x clock, lane-instr/s
+    alu_peak = fp32["lane_fma_per_s"]  # measured lane-FMA rate (FMA probe)
 
     def alu_roof(stage):
         ops = E * OPS_PER_EVAL + B * OPS_PER_BLEND[stage]
@@ -462,20 +500,22 @@ def run_ours(args):
                 "traffic": ncu_traffic(kern, "%dx%dx%d" % best) if args.workload == "urban" else None,
                 "work": "E=%d in-footprint evaluations x %d + %d blended x %d FP32 instructions"
                         % (E, OPS_PER_EVAL, B, OPS_PER_BLEND[stage]),
-                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (derived)" % pk["sm_max_mhz"]}
+                "peak_kind": "measured (FMA probe)",
+                "peak_source": "FP32 lane-FMA rate of the FMA probe in this run (%d SMs; %.1f T/s derived from "
+                               "%d SMs x 128 lanes x %.0f MHz)" % (fp32["sm_count"], fp32["derived_lane_per_s"] / 1e12,
+                                                                  fp32["sm_count"], pk["sm_max_mhz"])}
 
     if dominant in ("composite", "composite_bwd"):
         roof = alu_roof(dominant)
     else:
-        # HBM-bound stages: algorithmic bytes per launch (see DESIGN.md)
+        # HBM-bound stages: algorithmic bytes per launch
         algo = {"project": N_GAUSS * 68 + N_GAUSS * 8, "finalize": M * (68 + 192 + 48 + 8 + 4),
                 "preprocess_bwd": M * (260 + 40 + 260), "depth_sort": M * 4 * 20,
                 "pairs": M * 12 + K * 8, "tile_sort": K * 40}
         b = algo.get(dominant, 0)
         ach = b / (stage_ms[dominant] * 1e-3) / 1e9
         roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None}
-    roof["peak_kind"] = pk["source"]
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": pk["source"]}
 
     out = {
         "metric": METRIC, "value": job_value(world, mpix, ms_step), "unit": "Mpix/s",
@@ -496,14 +536,19 @@ def run_ours(args):
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "visible": M, "pairs": K, "evals": E, "blended_evals": B, "overflow": ov,
         "roofline_composite_fwd": alu_roof("composite"),
+        "sm_count": fp32["sm_count"],
+        "fp32_peak": {"value": fp32["lane_fma_per_s"] / 1e12, "unit": "T lane-FMA/s", "kind": "measured",
+                      **{k: v for k, v in fp32.items() if k != "lane_fma_per_s"}},
+        "hbm_peak": {"value": pk["hbm_gbs"], "unit": "GB/s", "kind": pk["source"]},
         "wall_s_timed_region": wall,
         "roofline": roof,
         "e2e": {"value": job_value(world, mpix, e2e_s * 1e3), "unit": "Mpix/s",
                 "h2d_bytes_per_step": target_host.numel() * 4,
-                "d2h_bytes_per_step": 4, "api": e2e_api},
+                "d2h_bytes_per_step": 4,
+                "api": e2e_api + "; only the 4-byte loss is read back (images and gradients stay on the device)"},
         "e2e_eager": {"value": job_value(world, mpix, e2e_eager_s * 1e3), "unit": "Mpix/s",
                       "h2d_bytes_per_step": target_host.numel() * 4, "d2h_bytes_per_step": 4,
-                      "api": "Renderer.forward + l1_loss + Renderer.backward"},
+                      "api": "Renderer.forward + l1_loss + Renderer.backward; only the 4-byte loss is read back"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "paper_loss_step": paper_loss,
@@ -693,7 +738,7 @@ def run_batched(args):
         r.forward(scene, cams, outs=outs, frame=fr)
         dls = []
         for v, o in enumerate(outs):
-            dls.append(dict(rgb=R.l1_loss(o["rgb"], g.targets[v])[1]))
+            dls.append(dict(rgb=R.l1_loss(r, o["rgb"], g.targets[v])[1]))
         r.backward(scene, cams, fr, dls, grads=grads)
 
     direct()
@@ -711,7 +756,7 @@ def run_batched(args):
             if key not in o1:
                 o1[key] = r1.alloc_images([cam])
             o = r1.forward(scene, [cam], outs=o1[key], frame=f1)[0]
-            dl = R.l1_loss(o["rgb"], g.targets[v])[1]
+            dl = R.l1_loss(r1, o["rgb"], g.targets[v])[1]
             r1.backward(scene, [cam], f1, [dict(rgb=dl)], grads=grads)
 
     per_view()

@@ -16,8 +16,8 @@
  *     Sigma' = J W Sigma W^T J^T (Sec. 3.1, Eq. 2) with
  *     Sigma = R(q) diag(s)^2 R(q)^T, sorting by camera depth and per-tile
  *     front-to-back alpha blending C = sum_i T_i alpha_i c_i (Sec. 3.1,
- *     Eq. 3), plus the depth and opacity channels of "flexible rendering"
- *     (Sec. 3.1) and O = sum T_i alpha_i (Sec. 3.4, sky refinement);
+ *     Eq. 3), plus the depth and opacity channels that Sec. 3.1
+ *     renders beside colour and O = sum T_i alpha_i (Sec. 3.4, sky refinement);
  *   - optional background from a sky cube map, temporal-smoothing shift
  *     (Sec. 3.4) and extra channels: velocity, staticness and semantic maps
  *     (Sec. 4);
@@ -338,8 +338,8 @@ pvg_status_t pvg_serve_destroy(pvg_server_t *server);
 
 /* Stable LSD radix sort of n (key, value) pairs by bits [begin_bit,
  * end_bit) of the key, in place, on `stream` -- the sort the renderer uses
- * for "sorting the Gaussians according to their depth in camera space"
- * (Sec. 3.1): float32 depth bits of the visible Gaussians, then tile ids
+ * for the depth sort of Sec. 3.1 (camera-space depth order of the
+ * Gaussians): float32 depth bits of the visible Gaussians, then tile ids
  * of the (tile, Gaussian) pairs.  keys / vals: caller-owned device arrays
  * of n uint32 each.  Pairs with equal sort bits keep their input order.
  * Scratch (ping-pong buffers of n pairs, digit histograms) belongs to
@@ -354,7 +354,7 @@ pvg_status_t pvg_sort_pairs(pvg_ctx_t *ctx, uint32_t *keys, uint32_t *vals, int6
  * hosts that forbid allocations outside their own pool).  The paper has no
  * counterpart; this is an interface convenience.  It needs no context and
  * calls no cudaMalloc / cudaFree or allocating routine: its scratch is a
- * set of fixed device arrays inside this library (about 8.6 MiB, held on
+ * set of fixed device arrays inside this library (about 9.1 MiB, held on
  * every GPU that loads the library until the process exits).
  *   - n must be <= 1,048,576 (2^20); larger n returns PVG_ERR_INVALID and
  *     enqueues nothing.  Other arguments as for pvg_sort_pairs.
@@ -376,10 +376,14 @@ pvg_status_t pvg_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, i
  * ...): *loss = scale * sum_i |pred[i] - target[i]| and, if dl is
  * non-NULL, dl[i] = scale * sign(pred[i] - target[i]) (0 where equal).
  * All pointers are device memory of n floats (loss: one float, overwritten).
- * scale = 1/n gives the mean.  The sum is accumulated with float atomics
- * (order not fixed).  PVG_ERR_INVALID for NULL pointers or n < 0. */
-pvg_status_t pvg_l1_loss(const float *pred, const float *target, int64_t n, float scale, float *dl,
-                         float *loss, void *stream);
+ * scale = 1/n gives the mean.  The sum is taken in a fixed order (per-block
+ * partial sums added in block order), so the loss is bit-reproducible for
+ * the same inputs on the same device.  Uses a small scratch array of ctx
+ * (allocated by the first call; calls on one ctx must not overlap);
+ * capturable in a CUDA graph after one uncaptured call.
+ * PVG_ERR_INVALID for NULL pointers or n < 0. */
+pvg_status_t pvg_l1_loss(pvg_ctx_t *ctx, const float *pred, const float *target, int64_t n, float scale,
+                         float *dl, float *loss, void *stream);
 
 /* Photometric loss of the objective (Sec. 3.4):
  *   L = (1 - lambda_r) L1 + lambda_r (1 - SSIM)   (the paper uses 0.2),
@@ -401,6 +405,20 @@ pvg_status_t pvg_rgb_loss(pvg_ctx_t *ctx, const float *pred, const float *target
 
 /* Kernels this library has launched since it was loaded (all contexts). */
 uint64_t pvg_kernel_launches(void);
+
+/* Streaming multiprocessors of the current device, as the library sizes its
+ * grids with them (cudaDevAttrMultiProcessorCount, read once per device). */
+int32_t pvg_device_sm_count(void);
+
+/* FP32 throughput probe, the measured peak of the compositing kernels'
+ * roofline (not part of the rendering path): `blocks` blocks of 256
+ * threads, every thread running `iters` rounds of 128 fused multiply-adds
+ * in 8 independent chains x <- fma(x, a, b), then writing one float into
+ * dst (device, blocks * 256 floats, so nothing is optimised away).  The
+ * caller times the launch on `stream`: lane FMAs = blocks * 256 * iters *
+ * 128.  Choose |a| < 1 so that the chains stay finite.
+ * PVG_ERR_INVALID for dst NULL, blocks < 1 or iters < 1. */
+pvg_status_t pvg_fma_probe(float *dst, int32_t blocks, int64_t iters, float a, float b, void *stream);
 
 /* Stages timed by pvg_profile_* (CUDA events on the call's stream). */
 enum {

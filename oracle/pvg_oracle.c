@@ -13,8 +13,7 @@
  *        mu~(t) = mu + l/(2 pi) sin(2 pi (t - tau)/l) v
  *        o~(t)  = o exp(-(t - tau)^2 / (2 beta^2))
  *   2. View transform p = W mu~ + t_c and the near-plane / opacity culls
- *      (Sec. 3.1, "sorting the Gaussians according to their depth in
- *      camera space").
+ *      (Sec. 3.1: the Gaussians are ordered by camera-space depth).
  *   3. 3D covariance Sigma = R(q) diag(s)^2 R(q)^T (Sec. 3.1, the scaling /
  *      unit-quaternion decomposition) and the EWA projection
  *      Sigma' = J W Sigma W^T J^T (Sec. 3.1, Eq. 2), plus a low-pass
@@ -25,9 +24,8 @@
  *      clamped at 0.
  *   5. Per pixel, front-to-back alpha blending over all surviving Gaussians
  *      ordered by (camera depth, index) (Sec. 3.1, Eq. 3), alpha = o~ G_2D,
- *      with the depth and opacity channels of "flexible rendering"
- *      (Sec. 3.1) and the opacity O = sum T alpha of Sec. 3.4 ("sky
- *      refinement").  Gates (3DGS conventions, options here): alpha capped
+ *      with the depth and opacity channels Sec. 3.1 renders beside
+ *      colour and the opacity O = sum T alpha of the sky step of Sec. 3.4.  Gates (3DGS conventions, options here): alpha capped
  *      at 0.99, alpha < 1/255 skipped, stop before a Gaussian whose blend
  *      would leave T (1 - alpha) < 1e-4.  Finally C += T bg.
  *   6. Culled mode: identical result, but a Gaussian is only considered for
@@ -156,8 +154,8 @@ static void sh_basis(int degree, const double d[3], double *Y, double (*dY)[3])
 /* ------------------------------------------------------------------ */
 /* step 1: time evaluation (Eq. 6, Eq. 7)                             */
 /* ------------------------------------------------------------------ */
-/* With dt != 0 this is the flow-translated state of Sec. 3.4 ("temporal
- * smoothing by intrinsic motion"): the point is queried at t - dt and
+/* With dt != 0 this is the flow-translated state of the temporal
+ * smoothing of Sec. 3.4: the point is queried at t - dt and
  * moved by the average velocity v_bar = v exp(-rho / 2), rho = beta / l
  * (Eq. 10), times dt; its opacity is the one at t - dt. */
 static void time_eval(const scene_t *S, int64_t i, double t, double dt, gauss_t *g)

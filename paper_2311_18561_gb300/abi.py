@@ -108,9 +108,11 @@ _SIGS = {
     "pvg_serve_destroy": (C.c_int, [_P]),
     "pvg_sort_pairs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
     "pvg_sort_pairs_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
-    "pvg_l1_loss": (C.c_int, [_P, _P, C.c_int64, C.c_float, _P, _P, _P]),
+    "pvg_l1_loss": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P, _P]),
     "pvg_rgb_loss": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_float, _P, _P, _P]),
     "pvg_kernel_launches": (C.c_uint64, []),
+    "pvg_device_sm_count": (C.c_int32, []),
+    "pvg_fma_probe": (C.c_int, [_P, C.c_int32, C.c_int64, C.c_float, C.c_float, _P]),
     "pvg_profile_enable": (C.c_int, [_P, C.c_int]),
     "pvg_profile_read": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "pvg_frame_eval_count": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),

@@ -85,7 +85,7 @@ class BatchGraph:
             torch.cuda.current_stream().wait_stream(self.copy_stream)
         if self.backward:
             for v, o in enumerate(self.outs):
-                R.l1_loss(o["rgb"], self.targets[v], dl=self.dls[v], loss=self.losses[v:v + 1])
+                R.l1_loss(self.r, o["rgb"], self.targets[v], dl=self.dls[v], loss=self.losses[v:v + 1])
             self.r.backward(self.scene_t, self.cams, self.frame, [dict(rgb=d) for d in self.dls], grads=self.grads)
 
     def replay(self):

@@ -30,6 +30,26 @@ using namespace pvg;
 namespace pvg {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static constexpr int kMaxSmDevices = 64;
+static std::atomic<int> g_sm_count[kMaxSmDevices];
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxSmDevices) {
+        cudaGetLastError();
+        return 1;
+    }
+    int v = g_sm_count[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
+        }
+        g_sm_count[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
 }  // namespace pvg
 
 namespace {
@@ -198,6 +218,7 @@ struct pvg_ctx {
     DevBuf temp;
     DevBuf sort_n;               // u32: element count of pvg_sort_pairs
     DevBuf loss_partials;        // float2 per CTA of pvg_rgb_loss
+    DevBuf l1_scratch;           // pvg_l1_loss: ticket counter + per-block partial sums
     uint32_t *h_pinned = nullptr;
     pvg_frame *own_frame = nullptr;
     StageTimer timer;
@@ -294,7 +315,7 @@ extern "C" pvg_status_t pvg_create(pvg_ctx_t **ctx, const pvg_config_t *cfg) {
         delete x;
         return PVG_ERR_OOM;
     }
-    if (ensure(x->temp, sort_temp_bytes(0)) != PVG_OK || pvg_frame_create(&x->own_frame) != PVG_OK) {
+    if (ensure(x->temp, sort_temp_bytes()) != PVG_OK || pvg_frame_create(&x->own_frame) != PVG_OK) {
         cudaFreeHost(x->h_pinned);
         release(x->temp);
         delete x;
@@ -309,7 +330,7 @@ extern "C" void pvg_destroy(pvg_ctx_t *x) {
     cudaDeviceSynchronize();
     for (DevBuf *b : {&x->views, &x->item_cnt, &x->item_zkey, &x->proj, &x->alt_keys, &x->alt_vals, &x->pair_keys,
                       &x->pair_keys2, &x->pair_vals2, &x->temp, &x->sort_n, &x->vis_off, &x->chunk_start,
-                      &x->loss_partials})
+                      &x->loss_partials, &x->l1_scratch})
         release(*b);
     if (x->h_pinned) cudaFreeHost(x->h_pinned);
     pvg_frame_destroy(x->own_frame);
@@ -784,11 +805,11 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     if (capturing) tm.on = false;
     tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
     note_launch();
-    k_zero_rows<<<152 * 4, 256, 0, s>>>(p.g2d, &p.counters[0], 10);
+    k_zero_rows<<<device_sm_count() * 4, 256, 0, s>>>(p.g2d, &p.counters[0], 10);
     launch_composite_bwd(p, s);
     if (feat_bwd && f->n_items) {
         note_launch();
-        k_zero_rows<<<152 * 4, 256, 0, s>>>(p.gfeat, &p.counters[0], p.n_feat);
+        k_zero_rows<<<device_sm_count() * 4, 256, 0, s>>>(p.gfeat, &p.counters[0], p.n_feat);
         launch_composite_feat_bwd(p, s);
     }
     tm.end(PVG_STAGE_COMPOSITE_BWD, s);
@@ -813,6 +834,20 @@ extern "C" pvg_status_t pvg_rgb_loss(pvg_ctx_t *x, const float *pred, const floa
     const bool capturing = is_capturing(s);
     PVG_TRY(ensure_c(x->loss_partials, 2 * sizeof(float) * rgb_loss_partials(channels, height, width), capturing));
     PVG_CUDA(launch_rgb_loss(pred, target, channels, height, width, lambda_r, dl, loss, x->loss_partials.p, s));
+    return PVG_OK;
+}
+
+extern "C" pvg_status_t pvg_l1_loss(pvg_ctx_t *x, const float *pred, const float *target, int64_t n, float scale,
+                                    float *dl, float *loss, void *stream) {
+    if (!x || !pred || !target || !loss || n < 0) return PVG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = l1_loss_scratch_bytes();
+    if (x->l1_scratch.bytes < need) {
+        if (is_capturing(s)) return PVG_ERR_INVALID;
+        PVG_TRY(ensure(x->l1_scratch, need));
+        PVG_CUDA(cudaMemsetAsync(x->l1_scratch.p, 0, x->l1_scratch.bytes, s));  // the ticket starts at 0
+    }
+    PVG_CUDA(launch_l1_loss(pred, target, n, scale, dl, loss, x->l1_scratch.p, s));
     return PVG_OK;
 }
 
@@ -859,7 +894,7 @@ extern "C" pvg_status_t pvg_frame_export(pvg_frame_t *f, uint32_t *sorted_gid, u
         PVG_CUDA(cudaMemcpyAsync(ranges, f->ranges.p, 8 * (size_t)f->total_tiles, cudaMemcpyDeviceToDevice, s));
     if (rect && M) {
         note_launch();
-        k_export_rect<<<152, 256, 0, s>>>(ptr<uint2>(f->rect), ptr<uint32_t>(f->counters), rect);
+        k_export_rect<<<device_sm_count(), 256, 0, s>>>(ptr<uint2>(f->rect), ptr<uint32_t>(f->counters), rect);
     }
     PVG_CUDA(cudaGetLastError());
     PVG_CUDA(cudaStreamSynchronize(s));
@@ -929,9 +964,9 @@ extern "C" pvg_status_t pvg_frame_eval_count(pvg_ctx_t *x, pvg_frame_t *f, int64
     unsigned long long *d = ptr<unsigned long long>(x->sort_n);
     PVG_CUDA(cudaMemsetAsync(d, 0, sizeof(h), s));
     note_launch();
-    k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, d);
+    k_sum_u32<<<device_sm_count() * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval), f->total_pix, d);
     note_launch();
-    k_sum_u32<<<152 * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval) + f->total_pix, f->total_pix, d + 1);
+    k_sum_u32<<<device_sm_count() * 4, 256, 0, s>>>(ptr<uint32_t>(f->pix_neval) + f->total_pix, f->total_pix, d + 1);
     PVG_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
     PVG_CUDA(cudaStreamSynchronize(s));
     *evals = (int64_t)h[0];

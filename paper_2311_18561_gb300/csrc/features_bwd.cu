@@ -260,7 +260,7 @@ void launch_composite_feat_bwd(const Params &p, cudaStream_t s) {
 void launch_feat_param_bwd(const Params &p, cudaStream_t s) {
     if (p.n_items == 0 || p.n_feat <= 0) return;
     note_launch();
-    k_feat_param_bwd<<<152 * 4, 256, 0, s>>>(p);
+    k_feat_param_bwd<<<4 * device_sm_count(), 256, 0, s>>>(p);
 }
 
 }  // namespace pvg

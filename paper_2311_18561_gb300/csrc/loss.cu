@@ -2,43 +2,83 @@
 // objective, Sec. 3.4), so that a training step needs no kernel outside
 // this library: loss = scale * sum |pred - target|,
 // dl = scale * sign(pred - target).
+//
+// The sum is taken in a fixed order, so the loss is the same bit for bit
+// on every run with the same inputs on the same device: a fixed grid of
+// blocks (a multiple of the SM count) walks the elements with a fixed
+// stride, each block reduces its threads in a fixed pattern into one
+// partial sum, and the last block to finish adds the partial sums in block
+// order.  Nothing waits on another block.
 #include "../../include/pvg.h"
 #include "pvg_internal.cuh"
 
 namespace pvg {
 namespace {
 
-__global__ void __launch_bounds__(256) k_l1(const float *__restrict__ pred, const float *__restrict__ tgt,
-                                            size_t n, float scale, float *__restrict__ dl, float *loss) {
-    __shared__ float warp_sum[8];
+constexpr int kL1Threads = 256;
+constexpr int kL1BlocksPerSm = 8;
+constexpr size_t kL1PartialsOffset = 16;  // bytes: the ticket counter comes first
+
+__device__ __forceinline__ float block_sum(float v, float *warp_sum) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float b = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kL1Threads / 32; w++) b += warp_sum[w];
+    return b;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kL1Threads) k_l1(const float *__restrict__ pred, const float *__restrict__ tgt,
+                                                   size_t n, float scale, float *__restrict__ dl,
+                                                   unsigned int *ticket, float *partials, float *loss) {
+    __shared__ float warp_sum[kL1Threads / 32];
+    __shared__ bool is_last;
     float acc = 0.f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = blockIdx.x * (size_t)kL1Threads + threadIdx.x; i < n; i += (size_t)gridDim.x * kL1Threads) {
         const float d = pred[i] - tgt[i];
         acc += fabsf(d);
         if (dl) dl[i] = d > 0.f ? scale : (d < 0.f ? -scale : 0.f);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
-    __syncthreads();
+    const float b = block_sum(acc, warp_sum);
     if (threadIdx.x == 0) {
-        float b = 0.f;
-        for (int w = 0; w < 8; w++) b += warp_sum[w];
-        atomicAdd(loss, b * scale);
+        partials[blockIdx.x] = b;
+        __threadfence();
+        is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    // the last block: every other block's partial is visible
+    __threadfence();
+    float s = 0.f;
+    for (unsigned int k = threadIdx.x; k < gridDim.x; k += kL1Threads) s += ((volatile float *)partials)[k];
+    __syncthreads();  // warp_sum is reused
+    const float total = block_sum(s, warp_sum);
+    if (threadIdx.x == 0) {
+        *loss = total * scale;
+        *ticket = 0u;  // ready for the next call
     }
 }
 
-}  // namespace
-}  // namespace pvg
-
-extern "C" pvg_status_t pvg_l1_loss(const float *pred, const float *target, int64_t n, float scale, float *dl,
-                                    float *loss, void *stream) {
-    if (!pred || !target || !loss || n < 0) return PVG_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return PVG_ERR_CUDA;
-    if (n == 0) return PVG_OK;
-    size_t blocks = ((size_t)n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    pvg::note_launch();
-    pvg::k_l1<<<(unsigned)blocks, 256, 0, s>>>(pred, target, (size_t)n, scale, dl, loss);
-    return cudaGetLastError() == cudaSuccess ? PVG_OK : PVG_ERR_CUDA;
+unsigned l1_blocks(int64_t n) {
+    size_t blocks = ((size_t)n + kL1Threads - 1) / kL1Threads;
+    const size_t cap = (size_t)kL1BlocksPerSm * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    return blocks < 1 ? 1u : (unsigned)blocks;
 }
+
+}  // namespace
+
+size_t l1_loss_scratch_bytes() { return kL1PartialsOffset + sizeof(float) * kL1BlocksPerSm * device_sm_count(); }
+
+cudaError_t launch_l1_loss(const float *pred, const float *target, int64_t n, float scale, float *dl, float *loss,
+                           void *scratch, cudaStream_t s) {
+    if (n == 0) return cudaMemsetAsync(loss, 0, sizeof(float), s);
+    unsigned int *ticket = (unsigned int *)scratch;
+    float *partials = (float *)((char *)scratch + kL1PartialsOffset);
+    note_launch();
+    k_l1<<<l1_blocks(n), kL1Threads, 0, s>>>(pred, target, (size_t)n, scale, dl, ticket, partials, loss);
+    return cudaGetLastError();
+}
+
+}  // namespace pvg

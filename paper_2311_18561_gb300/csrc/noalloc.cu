@@ -8,7 +8,9 @@
 // kernels as pvg_sort_pairs but keeps all of its scratch (ping-pong key /
 // value buffers, digit histograms, the element count) in the fixed arrays
 // below, which live in this library's device image.  Every GPU that loads
-// the library holds them (about 8.6 MiB) until the process exits.
+// the library holds them (about 9.1 MiB: two 4 MiB ping-pong buffers and
+// the sort's digit-histogram scratch, sized for up to 1024 sort blocks
+// whatever the SM count) until the process exits.
 //
 // Host code cannot use these array names as device addresses (on the host
 // they name host-side stand-ins), so each device's addresses are looked up
@@ -22,7 +24,7 @@
 namespace {
 
 constexpr uint32_t kNoAllocMaxPairs = 1u << 20;               // 1,048,576 pairs
-constexpr size_t kNoAllocTempBytes = 4u * (256u * 608u + 1024u);  // digit histograms + scan partials
+constexpr size_t kNoAllocTempBytes = pvg::kSortTempBytes;  // digit histograms + scan partials
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_keys[kNoAllocMaxPairs];
@@ -68,7 +70,6 @@ extern "C" pvg_status_t pvg_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, i
         return PVG_ERR_INVALID;
     if (n == 0) return PVG_OK;
     if (!keys || !vals) return PVG_ERR_INVALID;
-    if (pvg::sort_temp_bytes(0) > kNoAllocTempBytes) return PVG_ERR_INVALID;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -266,7 +266,8 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float (&Y)[16
 int grid_for(uint32_t n) {
     uint32_t g = (n + 255) / 256;
     if (g < 1) g = 1;
-    if (g > 152 * 16) g = 152 * 16;
+    const uint32_t cap = 16u * (uint32_t)device_sm_count();
+    if (g > cap) g = cap;
     return (int)g;
 }
 

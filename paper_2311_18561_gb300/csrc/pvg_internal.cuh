@@ -382,13 +382,23 @@ __device__ __forceinline__ void sky_texels(const ViewDesc &V, int px, int py, si
 namespace pvg {
 // counts every kernel launch of the library (reported by pvg_kernel_launches)
 void note_launch();
+// streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device); grids of the grid-stride kernels are multiples of it
+int device_sm_count();
+// radix sort scratch: digit histograms of up to kMaxSortBlocks blocks (4 per
+// SM on parts of up to 256 SMs; larger parts use kMaxSortBlocks blocks) and
+// the scan partials
+constexpr int kMaxSortBlocks = 1024;
+constexpr int kSortRadix = 256;
+constexpr int kMaxScanBlocks = 1024;
+constexpr size_t kSortTempBytes = sizeof(uint32_t) * ((size_t)kSortRadix * kMaxSortBlocks + kMaxScanBlocks);
 cudaError_t set_sh_constants();      // both copies of the SH constants
 cudaError_t set_sh_constants_bwd();  // the adjoint's copy
 void launch_project_count(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);
 void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s);
 // sort / scan
-size_t sort_temp_bytes(uint32_t capacity);
+size_t sort_temp_bytes();  // kSortTempBytes
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);
 // inv_out (optional): the last pass also writes inv_out[value] = the
 // value's final position
@@ -405,6 +415,10 @@ bool composite_supported(int tw, int th, int px);
 void launch_composite(const Params &p, cudaStream_t s);
 void launch_composite_stats(const Params &p, cudaStream_t s);
 void launch_composite_bwd(const Params &p, cudaStream_t s);
+// L1 loss with a fixed-order sum; scratch: l1_loss_scratch_bytes(), zeroed once
+size_t l1_loss_scratch_bytes();
+cudaError_t launch_l1_loss(const float *pred, const float *target, int64_t n, float scale, float *dl, float *loss,
+                           void *scratch, cudaStream_t s);
 // photometric loss (1 - lambda_r) L1 + lambda_r (1 - SSIM)
 size_t rgb_loss_partials(int channels, int height, int width);
 cudaError_t launch_rgb_loss(const float *pred, const float *target, int channels, int height, int width,

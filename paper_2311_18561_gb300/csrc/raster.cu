@@ -1,7 +1,7 @@
 // raster.cu -- per-tile compositing (stage c).
 //
-// Sec. 3.1, Eq. 3 with the depth / opacity channels of "flexible
-// rendering": one CTA per tile of TW x TH pixels, TW x TH/PX threads, each
+// Sec. 3.1, Eq. 3 with the depth and opacity channels Sec. 3.1 renders
+// beside colour: one CTA per tile of TW x TH pixels, TW x TH/PX threads, each
 // thread PX vertically adjacent pixels, each warp an 8 x 4 block of
 // threads.  The tile's sorted list is walked front to back in batches of
 // one record per thread, staged in shared memory as

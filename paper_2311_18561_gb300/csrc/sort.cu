@@ -2,8 +2,8 @@
 // stable LSD radix sort of (u32 key, u32 value) pairs, all with the element
 // count read from device memory so that no host round trip is needed.
 //
-// Role in the method: "sorting the Gaussians according to their depth in
-// camera space" (Sec. 3.1) for every tile of the tile-based rasterizer.
+// Role in the method: the camera-space depth order of the Gaussians
+// (Sec. 3.1) within every tile of the tile-based rasterizer.
 // The sort is done in two stages:
 //   1. the visible (view, Gaussian) items are sorted by the float32 bits of
 //      their camera depth (4 digit passes over M items; the items start in
@@ -20,6 +20,7 @@
 // size, so a block's output for a digit always precedes block b+1's
 // (stability across blocks); inside a block, tiles are taken in order and
 // ranked stably within each warp with __match_any_sync.
+#include <algorithm>
 #include "pvg_internal.cuh"
 
 namespace pvg {
@@ -28,7 +29,6 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;  // 1024
-constexpr int kMaxScanBlocks = 1024;
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -38,8 +38,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSmallItems = 4;
 constexpr uint32_t kSmallSort = 4u << 20;
-constexpr int kRadix = 256;
-constexpr int kMaxSortBlocks = 608;  // 4 per SM on a 152-SM part
+constexpr int kRadix = kSortRadix;
 
 constexpr uint32_t kEmitChunk = 2048;  // pair outputs per expansion chunk
 constexpr int kEmitThreads = 256;
@@ -196,8 +195,9 @@ int scan_blocks(uint32_t capacity) {
 
 int sort_blocks(uint32_t capacity, int tile) {
     uint32_t g = (capacity + tile - 1) / tile;
+    const uint32_t cap = (uint32_t)std::min(kMaxSortBlocks, 4 * device_sm_count());
     if (g < 1) g = 1;
-    if (g > kMaxSortBlocks) g = kMaxSortBlocks;
+    if (g > cap) g = cap;
     return (int)g;
 }
 
@@ -527,7 +527,9 @@ TempLayout temp_layout(void *temp) {
 
 }  // namespace
 
-size_t sort_temp_bytes(uint32_t) { return sizeof(uint32_t) * ((size_t)kRadix * kMaxSortBlocks + kMaxScanBlocks); }
+static_assert(kSortTempBytes >= sizeof(uint32_t) * ((size_t)kRadix * kMaxSortBlocks + kMaxScanBlocks),
+              "sort scratch layout");
+size_t sort_temp_bytes() { return kSortTempBytes; }
 
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s) {
     TempLayout t = temp_layout(temp);
@@ -615,7 +617,7 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
     uint32_t grid = (uint32_t)((p.pair_capacity + kEmitChunk - 1) / kEmitChunk);
     if (grid < 1) grid = 1;
-    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid > (uint32_t)(8 * device_sm_count())) grid = 8 * device_sm_count();
     note_launch();
     k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.vis_cnt, p.chunk_start, p.rect, p.rowtab, p.ell,
                                                  p.tile_w, p.tile_h,
@@ -658,7 +660,7 @@ void launch_tile_order(const Params &p, cudaStream_t s) {
 void launch_ranges(const Params &p, cudaStream_t s) {
     cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * (size_t)p.total_tiles, s);
     note_launch();
-    k_ranges<<<152 * 8, 256, 0, s>>>(p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
+    k_ranges<<<8 * device_sm_count(), 256, 0, s>>>(p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
 }
 
 }  // namespace pvg

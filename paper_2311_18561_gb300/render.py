@@ -308,9 +308,10 @@ def allreduce_gradients(flat, group=None):
     return flat
 
 
-def l1_loss(pred, target, dl=None, loss=None, scale=None, stream=None):
+def l1_loss(renderer, pred, target, dl=None, loss=None, scale=None, stream=None):
     """loss = scale * sum|pred - target| (default scale = 1/numel) and
-    dl = scale * sign(pred - target), computed by ``pvg_l1_loss``."""
+    dl = scale * sign(pred - target), computed by ``pvg_l1_loss`` with the
+    renderer's workspace (fixed-order sum: bit-reproducible)."""
     if pred.shape != target.shape or not pred.is_contiguous() or not target.is_contiguous():
         raise ValueError("pred and target must be contiguous tensors of one shape")
     n = pred.numel()
@@ -319,8 +320,8 @@ def l1_loss(pred, target, dl=None, loss=None, scale=None, stream=None):
     if loss is None:
         loss = torch.empty(1, device=pred.device, dtype=torch.float32)
     s = 1.0 / max(n, 1) if scale is None else float(scale)
-    st = abi.lib().pvg_l1_loss(pred.data_ptr(), target.data_ptr(), n, s, dl.data_ptr(), loss.data_ptr(),
-                              _stream_ptr(stream))
+    st = abi.lib().pvg_l1_loss(renderer.handle, pred.data_ptr(), target.data_ptr(), n, s, dl.data_ptr(),
+                              loss.data_ptr(), _stream_ptr(stream))
     abi.check(st, "pvg_l1_loss")
     return loss, dl
 
@@ -344,6 +345,21 @@ def rgb_loss(renderer, pred, target, lambda_r=0.2, dl=None, loss=None, stream=No
 
 def kernel_launches() -> int:
     return int(abi.lib().pvg_kernel_launches())
+
+
+def device_sm_count() -> int:
+    """SM count of the current device, as the library sizes its grids."""
+    return int(abi.lib().pvg_device_sm_count())
+
+
+def fma_probe(dst, blocks, iters, a=0.9999, b=1e-3, stream=None):
+    """Launches the FP32 throughput probe (``pvg_fma_probe``): blocks x 256
+    threads x iters x 128 lane FMAs; dst holds blocks * 256 floats."""
+    if dst.numel() < blocks * 256 or dst.dtype != torch.float32 or not dst.is_cuda:
+        raise ValueError("dst must be a CUDA float32 tensor of blocks * 256 elements")
+    abi.check(abi.lib().pvg_fma_probe(dst.data_ptr(), int(blocks), int(iters), float(a), float(b),
+                                      _stream_ptr(stream)), "pvg_fma_probe")
+    return int(blocks) * 256 * int(iters) * 128
 
 
 def profile_enable(renderer, on=True):

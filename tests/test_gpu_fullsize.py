@@ -53,15 +53,14 @@ def test_urban_frame_sampled_pixels_match_oracle(urban, cfg):
     out = r.forward(R.scene_to_device(scene), [cam], frame=fr)[0]
     torch.cuda.synchronize()
     m, k, ov = fr.stats()
-    assert ov == 0 and m > 400_000 and k > 4_000_000  # the benchmark's visible and pair counts
+    assert ov == 0 and m > 400_000 and k > 3_000_000  # the benchmark's visible and pair counts
     img = to_numpy_images(out)
     got = {key: img[key][pix[:, 1], pix[:, 0]] for key in ("rgb", "depth", "alpha")}
-    rep = compare_to_oracle(got, ref, pixels=pix)
+    compare_to_oracle(got, ref, pixels=pix)
     assert float(ref["alpha"].mean()) > 0.5  # the sample sees the scene, not the background
     assert int(ref["nblend"].max()) > 100  # deep per-pixel lists are among the sample
     r.close()
     fr.close()
-    return rep
 
 
 @pytest.fixture(scope="module")

@@ -77,3 +77,34 @@ def test_loss_rejects_bad_arguments(renderer):
         R.rgb_loss(renderer, x, x, lambda_r=1.5)
     with pytest.raises(Exception):
         R.rgb_loss(renderer, x, torch.zeros(3, 8, 9, device="cuda"))
+
+
+@pytest.mark.parametrize("n", [1, 255, 257, 3 * 375 * 1242, 3 * 1280 * 1920])
+def test_l1_loss_is_reproducible_and_matches_fp64(renderer, n):
+    """pvg_l1_loss: the fixed-order sum gives the same loss bit for bit on
+    every call (and from a second context), within 1e-6 relative of the FP64
+    sum; the gradient is scale * sign(pred - target) exactly."""
+    rng = np.random.default_rng(n)
+    x = rng.uniform(0, 1, size=n).astype(np.float32)
+    y = rng.uniform(0, 1, size=n).astype(np.float32)
+    y[: n // 7] = x[: n // 7]  # equal entries: sign 0
+    xt, yt = torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda")
+    other = R.Renderer()
+    runs = [R.l1_loss(renderer, xt, yt)[0].clone() for _ in range(3)] + [R.l1_loss(other, xt, yt)[0].clone()]
+    loss, dl = R.l1_loss(renderer, xt, yt)
+    torch.cuda.synchronize()
+    for r in runs:
+        assert torch.equal(r, loss)
+    ref = np.abs(x.astype(np.float64) - y.astype(np.float64)).sum() / n
+    assert float(loss[0]) == pytest.approx(ref, rel=1e-6, abs=1e-9)
+    d = x.astype(np.float64) - y.astype(np.float64)
+    want = np.float32(1.0 / n) * np.sign(d).astype(np.float32)
+    np.testing.assert_array_equal(dl.cpu().numpy(), want)
+    other.close()
+
+
+def test_l1_loss_of_nothing_is_zero(renderer):
+    e = torch.empty(0, device="cuda")
+    loss, _ = R.l1_loss(renderer, e, e)
+    torch.cuda.synchronize()
+    assert float(loss[0]) == 0.0

@@ -1,5 +1,5 @@
-"""Pins of the oracle's compositing (Sec. 3.1, Eq. 3 and "flexible
-rendering") and of its reverse mode (Sec. 3.1 Eq. 4 / Sec. 3.2 Eq. 8:
+"""Pins of the oracle's compositing (Sec. 3.1, Eq. 3 and the depth and
+opacity channels rendered beside colour) and of its reverse mode (Sec. 3.1 Eq. 4 / Sec. 3.2 Eq. 8:
 the render function is differentiable).  No GPU.
 
 * one isotropic Gaussian on the optical axis with h = 0: every pixel equals

@@ -1,4 +1,4 @@
-"""Pins of the oracle's sky cube map (Sec. 3.4, "sky refinement":
+"""Pins of the oracle's sky cube map (the sky step of Sec. 3.4:
 C_f = C + (1 - O) f_sky(d), the sky colour depending only on the ray
 direction d).  No GPU.
 
