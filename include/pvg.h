@@ -381,6 +381,7 @@ pvg_status_t pvg_sort_pairs_noalloc(uint32_t *keys, uint32_t *vals, int64_t n, i
  * the same inputs on the same device.  Uses a small scratch array of ctx
  * (allocated by the first call; calls on one ctx must not overlap);
  * capturable in a CUDA graph after one uncaptured call.
+ * n = 0 writes *loss = 0 (pred, target and dl may then be NULL).
  * PVG_ERR_INVALID for NULL pointers or n < 0. */
 pvg_status_t pvg_l1_loss(pvg_ctx_t *ctx, const float *pred, const float *target, int64_t n, float scale,
                          float *dl, float *loss, void *stream);

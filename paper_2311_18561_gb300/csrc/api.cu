@@ -839,7 +839,7 @@ extern "C" pvg_status_t pvg_rgb_loss(pvg_ctx_t *x, const float *pred, const floa
 
 extern "C" pvg_status_t pvg_l1_loss(pvg_ctx_t *x, const float *pred, const float *target, int64_t n, float scale,
                                     float *dl, float *loss, void *stream) {
-    if (!x || !pred || !target || !loss || n < 0) return PVG_ERR_INVALID;
+    if (!x || !loss || n < 0 || (n > 0 && (!pred || !target))) return PVG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t need = l1_loss_scratch_bytes();
     if (x->l1_scratch.bytes < need) {
