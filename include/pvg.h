@@ -278,34 +278,70 @@ pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_
 /* serving                                                             */
 /* ------------------------------------------------------------------ */
 
-/* A render server: several scenes resident in HBM, requests (scene, camera
- * at time t, destination images) queued on the host and rendered by
- * `n_streams` worker threads, each with its own CUDA stream and workspace.
- * A free worker takes requests from the head of the queue into one batch
- * (up to max_batch_views views, of any scenes with one SH degree and any
- * sizes) as long as their estimated working memory fits in what is left of
- * memory_budget, and renders the batch with one pvg_render_fwd_multi launch
- * sequence; requests that arrive meanwhile join the next batch of the next
- * free worker, so batches overlap on the device (continuous batching).
- * Every request renders bit-identically alone and in a batch.  The server
- * uses the device that is current at creation. */
+/* A render server: several scenes resident in HBM; render requests (scene,
+ * camera at time t, destination images) of any size, time and pose are
+ * batched into shared launch sequences while earlier batches are still on
+ * the GPU (continuous batching).  There is no serving system in the paper
+ * (it reports rendering speed only, Sec. 4 / Tab. 5); the design:
+ *
+ *   - Request ring.  pvg_serve_submit writes the request's view descriptor
+ *     into a slot of a ring in mapped pinned memory, which the GPU reads
+ *     directly, and then publishes the slot with a sequence number.
+ *   - Launch sequences.  Each of `n_streams` workers (a thread, a CUDA
+ *     stream, a workspace) takes queued requests into a batch and enqueues
+ *     one launch sequence for it without waiting for its earlier batches
+ *     (up to pipeline_depth in flight): a gather kernel waits for every
+ *     slot of the batch to be published -- a bounded wait of at most
+ *     gate_timeout_us, after which the slot's request completes with
+ *     PVG_ERR_TIMEOUT and its view renders nothing -- and copies the
+ *     descriptors into the workspace; the forward render of all the batch's
+ *     views follows (one depth sort, one tile sort, one compositing launch
+ *     over every view's tiles); a completion kernel writes each slot's
+ *     status, the batch's pair count and GPU timestamps back into the ring.
+ *     The host learns of completion from those flags; no stream is
+ *     synchronised per batch.
+ *   - Admission by memory.  At creation the server measures the free
+ *     device memory (cudaMemGetInfo) and reserves for every worker an arena
+ *     of min(memory_budget, 90 % of the free memory) / n_streams bytes:
+ *     capacities for Gaussians, pixels, tiles and tile/Gaussian pairs per
+ *     batch.  A batch takes requests from the head of the queue while their
+ *     sum fits the arena; the pairs of a request are estimated from the
+ *     pairs per pixel its scene produced before.  The GPU counts the pairs
+ *     of the batch before emitting them; if the count exceeds the batch's
+ *     reservation the batch's requests go back to the head of the queue
+ *     with the measured count (count, reserve, then continue or requeue).
+ *     The first request of a batch is always taken, so a request larger
+ *     than an arena is rendered alone in a workspace grown for it.
+ *
+ * Every request renders bit-identically alone and in any batch, and equal
+ * to pvg_render_fwd of the same scene and camera.  The server uses the
+ * device that is current at creation. */
 typedef struct pvg_server pvg_server_t;
 
 typedef struct {
-    int32_t max_batch_views; /* views per launch sequence (default 16) */
-    int32_t n_streams;       /* worker streams, 1..16 (default 2) */
-    int64_t memory_budget;   /* bytes of estimated in-flight working memory (default 8 GiB) */
-    int32_t max_pending;     /* queued requests before submit returns PVG_ERR_BUSY (default 4096) */
+    int32_t max_batch_views;  /* views per launch sequence, 1..64 (default 16) */
+    int32_t n_streams;        /* workers, each with its own stream and arena, 1..16 (default 2) */
+    int64_t memory_budget;    /* bytes of the workers' arenas together (default 8 GiB), clamped to
+                               * 90 % of the free device memory at creation */
+    int32_t max_pending;      /* queued requests before submit returns PVG_ERR_BUSY (default 4096) */
     int32_t tile_w, tile_h, pixels_per_thread; /* compositing configuration (16, 16, 1) */
-    int32_t reserved[4];
+    int32_t gate_timeout_us;  /* bound of the gather kernel's wait for a slot (default 1,000,000) */
+    int32_t pipeline_depth;   /* batches a worker keeps in flight, 1..4 (default 2) */
+    int32_t pair_capacity;    /* pairs per batch; 0 (default) = the arena's share */
+    int32_t reserved0;
 } pvg_serve_config_t;
 
-/* Per-request timing in milliseconds since the server was created; start
- * and done are -1 until reached. */
+/* Per-request timing in milliseconds since the server was created (host
+ * clock; start is the launch of the request's batch, done the moment the
+ * host saw its completion flag), -1 until reached; gpu_ms = GPU time from
+ * the gather kernel to the completion kernel of its batch. */
 typedef struct {
     double submit_ms, start_ms, done_ms;
     int32_t batch_views;  /* views in the launch that rendered it */
-    int32_t status;       /* pvg_status_t of that launch */
+    int32_t status;       /* pvg_status_t of the request */
+    double gpu_ms;
+    int32_t attempts;     /* launches it took (> 1 after a requeue) */
+    int32_t reserved0;
 } pvg_req_stats_t;
 
 void pvg_serve_config_default(pvg_serve_config_t *cfg);
@@ -329,6 +365,18 @@ pvg_status_t pvg_serve_release(pvg_server_t *server, uint64_t req_id);
 /* Queue length, launches and views so far, estimated in-flight bytes. */
 pvg_status_t pvg_serve_counters(pvg_server_t *server, int64_t *queued, int64_t *batches, int64_t *views,
                                 int64_t *in_flight_bytes);
+/* Requeues after a pair count above the reservation, and the per-worker
+ * arena capacities: Gaussians, pixels and pairs per batch, and the free
+ * device memory measured at creation. */
+pvg_status_t pvg_serve_arena(pvg_server_t *server, int64_t *requeues, int64_t *items_per_batch,
+                             int64_t *pixels_per_batch, int64_t *pairs_per_batch, int64_t *free_bytes_at_create);
+/* Test hook for the bounded device-side wait: the next n requests
+ * submitted to `server` are queued but their ring slots are never
+ * published, so the gather kernel's wait runs out after gate_timeout_us
+ * and they complete with PVG_ERR_TIMEOUT (their images are not written);
+ * the batches they were in, and the server, go on normally.  n <= 0
+ * clears it. */
+pvg_status_t pvg_serve_debug_withhold(pvg_server_t *server, int32_t n);
 /* Finishes every queued request, stops the workers and frees the server. */
 pvg_status_t pvg_serve_destroy(pvg_server_t *server);
 

@@ -68,12 +68,14 @@ class Config(C.Structure):
 class ServeConfig(C.Structure):
     _fields_ = [("max_batch_views", C.c_int32), ("n_streams", C.c_int32), ("memory_budget", C.c_int64),
                 ("max_pending", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("pixels_per_thread", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("pixels_per_thread", C.c_int32), ("gate_timeout_us", C.c_int32), ("pipeline_depth", C.c_int32),
+                ("pair_capacity", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class ReqStats(C.Structure):
     _fields_ = [("submit_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double),
-                ("batch_views", C.c_int32), ("status", C.c_int32)]
+                ("batch_views", C.c_int32), ("status", C.c_int32), ("gpu_ms", C.c_double),
+                ("attempts", C.c_int32), ("reserved0", C.c_int32)]
 
 
 # every symbol include/pvg.h declares, with (restype, argtypes)
@@ -105,6 +107,8 @@ _SIGS = {
     "pvg_serve_release": (C.c_int, [_P, C.c_uint64]),
     "pvg_serve_counters": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int64)]),
+    "pvg_serve_arena": (C.c_int, [_P] + [C.POINTER(C.c_int64)] * 5),
+    "pvg_serve_debug_withhold": (C.c_int, [_P, C.c_int32]),
     "pvg_serve_destroy": (C.c_int, [_P]),
     "pvg_sort_pairs": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),
     "pvg_sort_pairs_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.c_int32, _P]),

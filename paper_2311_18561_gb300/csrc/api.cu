@@ -499,37 +499,18 @@ static int bits_for(uint32_t n) {
 
 // ------------------------------------------------------------------ forward
 
-static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int scene_stride,
-                                    const pvg_camera_t *cams, int32_t n_views, const pvg_image_t *out,
-                                    pvg_frame_t *frame, void *stream_) {
-    if (!x || !out || !scenes) return PVG_ERR_INVALID;
-    for (int v = 0; v < n_views; v++)
-        if (!out[v].rgb) return PVG_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream_;
-    const bool capturing = is_capturing(s);
-    if (capturing && x->cfg.sync_sizes) return PVG_ERR_INVALID;  // a graph cannot hold the size read-back
-    pvg_frame *f = frame ? frame : x->own_frame;
-    std::vector<ViewDesc> views;
-    uint32_t NV, tiles, pix;
-    PVG_TRY(build_views(x, scenes, scene_stride, cams, n_views, views, &NV, &tiles, &pix));
-    const pvg_scene_t *scene = &scenes[0];
-    // extra channels: one mask for the call, channel values of every scene
-    const int fmask = out[0].feat_mask;
-    if (fmask & ~(kFeatVbar | kFeatRho | kFeatSem)) return PVG_ERR_INVALID;
-    const int nsem = (fmask & kFeatSem) ? scene->n_sem : 0;
-    if ((fmask & kFeatSem) && (nsem < 1 || nsem > kMaxSem)) return PVG_ERR_INVALID;
-    for (int v = 0; v < n_views; v++) {
-        if (out[v].feat_mask != fmask || (fmask && !out[v].feat)) return PVG_ERR_INVALID;
-        if ((fmask & kFeatSem) && ((views[v].n > 0 && !views[v].sem) || views[v].n_sem != nsem))
-            return PVG_ERR_INVALID;
-    }
+// The forward launch sequence for views whose host copies are `views`
+// (sizes and bases set).  dev_views: NULL stages the host copies into the
+// frame (pinned staging, one copy); otherwise the descriptors were already
+// written to dev_views on stream s (the render server's gather kernel).
+// no_alloc: every buffer must already be large enough (graph capture, or a
+// workspace reserved in advance); PVG_ERR_INVALID otherwise.
+static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<ViewDesc> &views,
+                                    const ViewDesc *dev_views, uint32_t NV, uint32_t tiles, uint32_t pix, int fmask,
+                                    int nsem, bool keep_state, bool no_alloc, cudaStream_t s) {
+    const bool capturing = no_alloc;
+    const int n_views = (int)views.size();
     const int n_feat = fmask ? feat_count(fmask, nsem) : 0;
-    for (int v = 0; v < n_views; v++) {
-        views[v].out_rgb = out[v].rgb;
-        views[v].out_depth = out[v].depth;
-        views[v].out_alpha = out[v].alpha;
-        views[v].out_feat = fmask ? out[v].feat : nullptr;
-    }
     // workspace
     PVG_TRY(ensure_c(x->item_cnt, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(x->item_zkey, sizeof(uint32_t) * NV, capturing));
@@ -562,15 +543,17 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
         PVG_TRY(ensure_c(x->chunk_start, sizeof(uint32_t) * emit_chunks(pair_cap), capturing));
     }
     f->views = views;
-    f->one_scene = scene_stride == 0 || n_views == 1;
+    f->one_scene = true;
+    for (int v = 1; v < n_views; v++)
+        if (views[v].mu != views[0].mu || views[v].n != views[0].n) f->one_scene = false;
     f->n_items = NV;
     f->total_tiles = tiles;
     f->total_pix = pix;
     f->tile_w = x->cfg.tile_w;
     f->tile_h = x->cfg.tile_h;
     f->px = x->cfg.pixels_per_thread ? x->cfg.pixels_per_thread : 1;
-    f->n = scene->n;
-    f->sh_degree = scene->sh_degree;
+    f->n = views[0].n;
+    f->sh_degree = views[0].sh_degree;
     f->dilation = x->cfg.dilation;
     f->stream = s;
     f->valid = false;
@@ -578,14 +561,14 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     f->n_feat = n_feat;
     f->n_sem = nsem;
 
-    PVG_TRY(stage_views(*f->stage_fwd, views, s, capturing));
+    if (!dev_views) PVG_TRY(stage_views(*f->stage_fwd, views, s, capturing));
     PVG_CUDA(cudaMemsetAsync(f->counters.p, 0, 4 * sizeof(uint32_t), s));
 
     Params p;
     std::memset(&p, 0, sizeof(p));
-    p.views = ptr<ViewDesc>(f->stage_fwd->dev);
+    p.views = dev_views ? dev_views : ptr<ViewDesc>(f->stage_fwd->dev);
     p.n_views = n_views;
-    p.sh_degree = scene->sh_degree;
+    p.sh_degree = views[0].sh_degree;
     p.tile_w = x->cfg.tile_w;
     p.tile_h = x->cfg.tile_h;
     p.px = f->px;
@@ -684,7 +667,7 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     }
     f->pair_capacity = pair_cap;
     p.pair_vals = ptr<uint32_t>(f->pair_vals);
-    if (!frame) p.pix_T = nullptr;  // inference only: no state for a backward pass
+    if (!keep_state) p.pix_T = nullptr;  // inference only: no state for a backward pass
     tm.begin(PVG_STAGE_COMPOSITE, s);
     launch_composite(p, s);
     if (n_feat) launch_composite_feat(p, s);
@@ -694,6 +677,98 @@ static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int
     f->valid = true;
     return PVG_OK;
 }
+
+static pvg_status_t render_fwd_impl(pvg_ctx_t *x, const pvg_scene_t *scenes, int scene_stride,
+                                    const pvg_camera_t *cams, int32_t n_views, const pvg_image_t *out,
+                                    pvg_frame_t *frame, void *stream_) {
+    if (!x || !out || !scenes) return PVG_ERR_INVALID;
+    for (int v = 0; v < n_views; v++)
+        if (!out[v].rgb) return PVG_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream_;
+    const bool capturing = is_capturing(s);
+    if (capturing && x->cfg.sync_sizes) return PVG_ERR_INVALID;  // a graph cannot hold the size read-back
+    pvg_frame *f = frame ? frame : x->own_frame;
+    std::vector<ViewDesc> views;
+    uint32_t NV, tiles, pix;
+    PVG_TRY(build_views(x, scenes, scene_stride, cams, n_views, views, &NV, &tiles, &pix));
+    const pvg_scene_t *scene = &scenes[0];
+    // extra channels: one mask for the call, channel values of every scene
+    const int fmask = out[0].feat_mask;
+    if (fmask & ~(kFeatVbar | kFeatRho | kFeatSem)) return PVG_ERR_INVALID;
+    const int nsem = (fmask & kFeatSem) ? scene->n_sem : 0;
+    if ((fmask & kFeatSem) && (nsem < 1 || nsem > kMaxSem)) return PVG_ERR_INVALID;
+    for (int v = 0; v < n_views; v++) {
+        if (out[v].feat_mask != fmask || (fmask && !out[v].feat)) return PVG_ERR_INVALID;
+        if ((fmask & kFeatSem) && ((views[v].n > 0 && !views[v].sem) || views[v].n_sem != nsem))
+            return PVG_ERR_INVALID;
+    }
+    for (int v = 0; v < n_views; v++) {
+        views[v].out_rgb = out[v].rgb;
+        views[v].out_depth = out[v].depth;
+        views[v].out_alpha = out[v].alpha;
+        views[v].out_feat = fmask ? out[v].feat : nullptr;
+    }
+    return enqueue_forward(x, f, views, nullptr, NV, tiles, pix, fmask, nsem, frame != nullptr, capturing, s);
+}
+
+// ------------------------------------------------------------------ render-server hooks (serve.cu)
+
+namespace pvg {
+
+pvg_status_t serve_view_desc(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cam, const pvg_image_t *dst,
+                             ViewDesc *out, uint32_t *tiles, uint32_t *pix) {
+    if (!x || !dst || !dst->rgb || dst->feat_mask) return PVG_ERR_INVALID;
+    std::vector<ViewDesc> v;
+    uint32_t NV = 0, T = 0, P = 0;
+    PVG_TRY(build_views(x, scene, 0, cam, 1, v, &NV, &T, &P));
+    v[0].out_rgb = dst->rgb;
+    v[0].out_depth = dst->depth;
+    v[0].out_alpha = dst->alpha;
+    v[0].out_feat = nullptr;
+    *out = v[0];
+    *tiles = T;
+    *pix = P;
+    return PVG_OK;
+}
+
+pvg_status_t serve_reserve(pvg_ctx_t *x, pvg_frame_t *f, uint64_t items, uint64_t tiles, uint64_t pix,
+                           uint64_t pairs, int max_views) {
+    if (!x || !f || items >= (1ull << 31) || tiles >= (1ull << 31) || pix >= (1ull << 32) || pairs > 0xfffffff0ull)
+        return PVG_ERR_INVALID;
+    for (DevBuf *b : {&x->item_cnt, &x->item_zkey, &x->alt_keys, &x->alt_vals, &x->vis_off, &f->sgid, &f->inv,
+                      &f->szkey, &f->vis_cnt})
+        PVG_TRY(ensure(*b, sizeof(uint32_t) * items));
+    PVG_TRY(ensure(x->proj, sizeof(float4) * 4 * items));
+    PVG_TRY(ensure(f->rec, sizeof(float4) * 3 * items));
+    PVG_TRY(ensure(f->ell, sizeof(float4) * 2 * items));
+    PVG_TRY(ensure(f->rowtab, sizeof(uint4) * items));
+    PVG_TRY(ensure(f->rect, sizeof(uint2) * items));
+    PVG_TRY(ensure(f->ranges, sizeof(uint2) * tiles));
+    PVG_TRY(ensure(f->tile_order, sizeof(uint32_t) * tiles));
+    PVG_TRY(ensure(f->pix_T, sizeof(float) * pix));
+    PVG_TRY(ensure(f->pix_last, sizeof(uint32_t) * pix));
+    PVG_TRY(ensure(f->pix_neval, sizeof(uint32_t) * 2 * pix));
+    for (DevBuf *b : {&f->pair_vals, &x->pair_keys, &x->pair_keys2, &x->pair_vals2})
+        PVG_TRY(ensure(*b, sizeof(uint32_t) * pairs));
+    PVG_TRY(ensure(x->chunk_start, sizeof(uint32_t) * emit_chunks((uint32_t)pairs)));
+    PVG_TRY(ensure(f->stage_fwd->dev, sizeof(ViewDesc) * (size_t)max_views));
+    return PVG_OK;
+}
+
+ViewDesc *serve_view_buffer(pvg_frame_t *f) { return ptr<ViewDesc>(f->stage_fwd->dev); }
+
+const uint32_t *serve_counters(pvg_frame_t *f) { return ptr<uint32_t>(f->counters); }
+
+pvg_status_t serve_forward(pvg_ctx_t *x, pvg_frame_t *f, std::vector<ViewDesc> &views, uint32_t NV, uint32_t tiles,
+                           uint32_t pix, uint32_t pair_capacity, cudaStream_t s) {
+    if (!x || !f || views.empty() || x->cfg.sync_sizes || pair_capacity == 0 || pair_capacity > 0xfffffff0u)
+        return PVG_ERR_INVALID;
+    PVG_TRY(ensure(f->stage_fwd->dev, sizeof(ViewDesc) * views.size()));
+    x->cfg.pair_capacity = pair_capacity;
+    return enqueue_forward(x, f, views, ptr<ViewDesc>(f->stage_fwd->dev), NV, tiles, pix, 0, 0, false, false, s);
+}
+
+}  // namespace pvg
 
 extern "C" pvg_status_t pvg_render_fwd(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cams,
                                        int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame,

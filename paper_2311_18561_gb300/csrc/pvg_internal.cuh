@@ -19,7 +19,10 @@
 //   pixels    final transmittance and last blended list position      [sum HW]
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
+
+#include "../../include/pvg.h"
 
 namespace pvg {
 
@@ -423,6 +426,18 @@ cudaError_t launch_l1_loss(const float *pred, const float *target, int64_t n, fl
 size_t rgb_loss_partials(int channels, int height, int width);
 cudaError_t launch_rgb_loss(const float *pred, const float *target, int channels, int height, int width,
                             float lambda_r, float *dl, float *loss, void *partials, cudaStream_t s);
+// render-server hooks (api.cu): one request's view descriptor built on the
+// host (bases 0), workspace reservation, the views' device buffer of a
+// frame, its counters (visible, pairs, overflow) and the forward launch
+// sequence over descriptors written to that buffer on the stream
+pvg_status_t serve_view_desc(pvg_ctx_t *x, const pvg_scene_t *scene, const pvg_camera_t *cam, const pvg_image_t *dst,
+                             ViewDesc *out, uint32_t *tiles, uint32_t *pix);
+pvg_status_t serve_reserve(pvg_ctx_t *x, pvg_frame_t *f, uint64_t items, uint64_t tiles, uint64_t pix,
+                           uint64_t pairs, int max_views);
+ViewDesc *serve_view_buffer(pvg_frame_t *f);
+const uint32_t *serve_counters(pvg_frame_t *f);
+pvg_status_t serve_forward(pvg_ctx_t *x, pvg_frame_t *f, std::vector<ViewDesc> &views, uint32_t NV, uint32_t tiles,
+                           uint32_t pix, uint32_t pair_capacity, cudaStream_t s);
 // extra channels
 int feat_count(int mask, int n_sem);
 void launch_composite_feat(const Params &p, cudaStream_t s);

@@ -14,7 +14,7 @@ from .render import abi_scene
 
 class Server:
     def __init__(self, max_batch_views=16, n_streams=2, memory_budget=8 << 30, max_pending=4096, tile=(16, 16),
-                 pixels_per_thread=1):
+                 pixels_per_thread=1, gate_timeout_us=1_000_000, pipeline_depth=2, pair_capacity=0):
         self._lib = abi.lib()
         c = abi.ServeConfig()
         self._lib.pvg_serve_config_default(C.byref(c))
@@ -24,6 +24,9 @@ class Server:
         c.max_pending = int(max_pending)
         c.tile_w, c.tile_h = int(tile[0]), int(tile[1])
         c.pixels_per_thread = int(pixels_per_thread)
+        c.gate_timeout_us = int(gate_timeout_us)
+        c.pipeline_depth = int(pipeline_depth)
+        c.pair_capacity = int(pair_capacity)
         h = C.c_void_p()
         abi.check(self._lib.pvg_serve_create(C.byref(h), C.byref(c)), "pvg_serve_create")
         self.handle = h
@@ -55,7 +58,7 @@ class Server:
     @staticmethod
     def _stats(s):
         return dict(submit_ms=s.submit_ms, start_ms=s.start_ms, done_ms=s.done_ms, batch_views=s.batch_views,
-                    status=s.status)
+                    status=s.status, gpu_ms=s.gpu_ms, attempts=s.attempts)
 
     def poll(self, rid):
         done, s = C.c_int32(), abi.ReqStats()
@@ -77,6 +80,19 @@ class Server:
         abi.check(self._lib.pvg_serve_counters(self.handle, C.byref(q), C.byref(b), C.byref(v), C.byref(m)),
                   "pvg_serve_counters")
         return dict(queued=q.value, batches=b.value, views=v.value, in_flight_bytes=m.value)
+
+    def arena(self):
+        """Requeues so far and the per-worker arena: Gaussians, pixels and
+        pairs per batch, and the free device memory measured at creation."""
+        v = [C.c_int64() for _ in range(5)]
+        abi.check(self._lib.pvg_serve_arena(self.handle, *[C.byref(x) for x in v]), "pvg_serve_arena")
+        return dict(zip(("requeues", "items_per_batch", "pixels_per_batch", "pairs_per_batch", "free_bytes"),
+                        (x.value for x in v)))
+
+    def debug_withhold(self, n):
+        """Test hook: the next n submitted requests are never published in
+        the ring, so the gather kernel's bounded wait runs out for them."""
+        abi.check(self._lib.pvg_serve_debug_withhold(self.handle, int(n)), "pvg_serve_debug_withhold")
 
     def close(self):
         if self.handle:

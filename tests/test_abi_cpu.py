@@ -66,3 +66,18 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "pvg_oracle" not in text, f
+
+
+def test_serving_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "serve_sizes.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pvg.h"\nint main(void){\n'
+                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(pvg_serve_config_t), sizeof(pvg_req_stats_t),'
+                   ' offsetof(pvg_serve_config_t, gate_timeout_us), offsetof(pvg_serve_config_t, pair_capacity),'
+                   ' offsetof(pvg_req_stats_t, gpu_ms), offsetof(pvg_req_stats_t, attempts));\n'
+                   'return 0;}\n')
+    exe = tmp_path / "serve_sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(abi.ServeConfig), C.sizeof(abi.ReqStats), abi.ServeConfig.gate_timeout_us.offset,
+            abi.ServeConfig.pair_capacity.offset, abi.ReqStats.gpu_ms.offset, abi.ReqStats.attempts.offset]
+    assert got == want

@@ -85,7 +85,9 @@ def test_allocation_failure_is_reported_and_the_next_call_recovers():
 
 def test_server_survives_allocation_failures():
     scenes = [R.scene_to_device(synth.make_urban_scene(20_000, seed=3))]
-    srv = S.Server(max_batch_views=1, n_streams=1)
+    # a 1 MiB budget reserves almost no arena: every first request of a size
+    # grows the worker's workspace while serving
+    srv = S.Server(max_batch_views=1, n_streams=1, memory_budget=1 << 20)
     sid = srv.add_scene(scenes[0])
     cams = [synth.street_camera(0.1 * k, 248, 75) for k in range(6)]
     abi.lib().pvg_debug_fail_allocations(2)  # the worker's first launches cannot grow their workspace

@@ -2,7 +2,10 @@
 resident scenes with requests of mixed resolution, time and pose.  Each
 request's image is bit-identical alone and in the mix, and equals a direct
 pvg_render_fwd call; the memory budget limits batches; a full queue
-answers BUSY.  GPU only."""
+answers BUSY; the gather kernel's bounded wait for an unpublished ring slot
+runs out with PVG_ERR_TIMEOUT while the server goes on; a pair count above
+a batch's reservation requeues its requests; the arenas follow the free
+device memory.  GPU only."""
 import numpy as np
 import pytest
 import torch
@@ -114,3 +117,80 @@ def test_unknown_scene_and_request():
         srv.poll(12345)
     assert e.value.status == 7
     srv.close()
+
+
+def test_unpublished_slot_times_out_on_the_device_and_the_server_goes_on():
+    """The gather kernel waits (bounded, 20 ms here) for every slot of its
+    batch; two requests whose slots are never published complete with
+    PVG_ERR_TIMEOUT, the requests batched with them render normally, and so
+    does everything after them."""
+    scenes = _scenes()
+    srv = S.Server(max_batch_views=8, n_streams=1, gate_timeout_us=20_000)
+    ids = [srv.add_scene(s) for s in scenes]
+    reqs = _requests(6, seed=3)
+    srv.debug_withhold(2)
+    outs, rids = [], []
+    for sid, cam in reqs:
+        o = _out(cam)
+        rids.append(srv.submit(ids[sid], cam, o))
+        outs.append(o)
+    stats = []
+    for rid in rids:
+        try:
+            srv.wait(rid, 30.0)
+        except abi.PVGError as e:  # wait returns the request's status
+            assert e.status == 4
+        stats.append(srv.poll(rid)[1])
+    assert [st["status"] for st in stats[:2]] == [4, 4]  # PVG_ERR_TIMEOUT
+    assert all(st["status"] == 0 for st in stats[2:])
+    assert stats[0]["gpu_ms"] >= 15.0  # the device waited out its bound
+    r = R.Renderer()
+    for (sid, cam), o, st in zip(reqs[2:], outs[2:], stats[2:]):
+        d = r.forward(scenes[sid], [cam])[0]
+        for k in ("rgb", "depth", "alpha"):
+            assert torch.equal(o[k], d[k])
+    for sid, cam in _requests(3, seed=4):
+        o = _out(cam)
+        assert srv.wait(srv.submit(ids[sid], cam, o), 30.0)["status"] == 0
+        d = r.forward(scenes[sid], [cam])[0]
+        assert torch.equal(o["rgb"], d["rgb"])
+    srv.close()
+
+
+def test_pair_count_above_the_reservation_requeues():
+    """With 3,000 pairs per batch reserved, the GPU's pair count of the
+    first batches exceeds the reservation: their requests go back to the
+    queue with the measured density and are rendered again with a larger
+    reservation, ending bit-identical to direct renders."""
+    scenes = _scenes()
+    srv = S.Server(max_batch_views=8, n_streams=1, pair_capacity=3000)
+    ids = [srv.add_scene(s) for s in scenes]
+    reqs = _requests(8, seed=5)
+    outs = [_out(cam) for _, cam in reqs]
+    rids = [srv.submit(ids[sid], cam, o) for (sid, cam), o in zip(reqs, outs)]
+    stats = [srv.wait(rid, 60.0) for rid in rids]
+    assert all(st["status"] == 0 for st in stats)
+    assert max(st["attempts"] for st in stats) >= 2
+    assert srv.arena()["requeues"] >= 1
+    r = R.Renderer()
+    for (sid, cam), o in zip(reqs, outs):
+        d = r.forward(scenes[sid], [cam])[0]
+        for k in ("rgb", "depth", "alpha"):
+            assert torch.equal(o[k], d[k])
+    srv.close()
+
+
+def test_arenas_follow_the_free_device_memory():
+    free, _ = torch.cuda.mem_get_info()
+    srv = S.Server(n_streams=2, memory_budget=2 << 30)
+    a = srv.arena()
+    assert 0.5 * free <= a["free_bytes"] <= 1.5 * free
+    budget = min(2 << 30, a["free_bytes"] // 10 * 9)
+    assert a["items_per_batch"] == (budget // 2) * 45 // 100 // 204
+    assert a["pixels_per_batch"] == (budget // 2) * 10 // 100 // 16
+    srv.close()
+    # a budget above the free memory is clamped to 90 % of it
+    big = S.Server(n_streams=1, memory_budget=1 << 50, max_pending=16)
+    b = big.arena()
+    assert b["items_per_batch"] <= (b["free_bytes"] // 10 * 9) * 45 // 100 // 204
+    big.close()
