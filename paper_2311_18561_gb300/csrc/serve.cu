@@ -150,7 +150,7 @@ __global__ void k_serve_gather(Slot *ring, const ViewDesc *scene_tab, GatherArgs
     d.out_feat = nullptr;
     views[v] = d;
     gate_ok[v] = ok ? 1u : 0u;
-    sl->t_gather_ns = globaltimer_ns();
+    sl->t_gather_ns = t0;  // the batch's GPU time starts before the wait
 }
 
 __global__ void k_serve_complete(Slot *ring, GatherArgs a, const uint32_t *counters, const uint32_t *gate_ok) {
