@@ -80,16 +80,18 @@ def parse_args():
     ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched", "serving"), default="urban")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="tile_w,tile_h,pixels_per_thread (default: autotune)")
-    ap.add_argument("--serve-rate", type=float, default=1000.0, help="request rate of the serving leg (req/s)")
+    ap.add_argument("--serve-rate", type=float, default=None,
+                    help="request rate of a single serving leg (req/s; default: sweep 200, 500, 1000, 2000)")
     ap.add_argument("--serve-seconds", type=float, default=None,
-                    help="seconds of arrivals per serving leg (default 2 for the leg after the headline "
-                         "step, 10 per rate for --workload serving)")
+                    help="seconds of arrivals per serving rate (default 5 after the headline step, 10 for "
+                         "--workload serving)")
     ap.add_argument("--dp", action="store_true",
                     help="with N > 1 ranks: data-parallel training step, the per-Gaussian gradients "
                          "summed over ranks in the step (default: independent replicas)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-legs", action="store_true",
-                    help="skip the paper-loss and extra-channel legs (timed after the headline step)")
+                    help="skip the legs timed after the headline step: paper loss, extra channels, the "
+                         "training (1M, 1242x375) and batched (3M, 64 views) configurations")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="wall-clock budget of the oracle's bounded sample")
     return ap.parse_args()
@@ -264,10 +266,138 @@ def ncu_traffic(kernel, config):
         return None
 
 
+# --------------------------------------------------------------------------- shared timing helpers
+
+def timed_steps(fn, steps, flush=None):
+    """Per-step CUDA events around fn on the current stream (L2 flushed
+    before each step, outside the events); returns the summed milliseconds."""
+    import torch
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def capture_graph(fn, dev):
+    """fn's launches as one CUDA graph (its buffers are already sized) and
+    the number of library kernels it holds."""
+    import torch
+
+    from paper_2311_18561_gb300 import render as R
+
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    n0 = R.kernel_launches()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g, R.kernel_launches() - n0
+
+
+def alu_roof(stage, stage_ms, E, B, fp32, traffic=None):
+    """ALU roofline of a compositing stage: E in-footprint evaluations x 8
+    + B blends x the stage's per-blend FP32 instructions, per launch, over
+    the measured lane-FMA rate of the FMA probe."""
+    ops = E * OPS_PER_EVAL + B * OPS_PER_BLEND[stage]
+    ach = ops / (stage_ms[stage] * 1e-3)
+    peak = fp32["lane_fma_per_s"]
+    kern = "k_composite" if stage == "composite" else "k_composite_bwd"
+    return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+            "unit": "T FP32-lane-instr/s", "frac": ach / peak, "traffic": traffic,
+            "work": "E=%d in-footprint evaluations x %d + %d blended x %d FP32 instructions"
+                    % (E, OPS_PER_EVAL, B, OPS_PER_BLEND[stage]),
+            "peak_kind": "measured (FMA probe)",
+            "peak_source": "FP32 lane-FMA rate of the FMA probe in this run (%d SMs; %.1f T/s derived from "
+                           "%d SMs x 128 lanes x %.0f MHz)" % (fp32["sm_count"], fp32["derived_lane_per_s"] / 1e12,
+                                                              fp32["sm_count"], peaks()["sm_max_mhz"])}
+
+
+def hbm_algo_bytes(stage, n_gauss, M, K):
+    """Algorithmic bytes per launch of the HBM-bound stages."""
+    return {"project": n_gauss * 68 + n_gauss * 8, "finalize": M * (68 + 192 + 48 + 8 + 4),
+            "preprocess_bwd": M * (260 + 40 + 260) + (n_gauss - M) * 260, "depth_sort": M * 4 * 20,
+            "pairs": M * 12 + K * 8, "tile_sort": K * 40}.get(stage, 0)
+
+
+def dominant_roof(stage_ms, E, B, n_gauss, M, K, fp32, traffic=None):
+    dominant = max(stage_ms, key=stage_ms.get)
+    if dominant in ("composite", "composite_bwd"):
+        return alu_roof(dominant, stage_ms, E, B, fp32, traffic)
+    pk = peaks()
+    b = hbm_algo_bytes(dominant, n_gauss, M, K)
+    ach = b / (stage_ms[dominant] * 1e-3) / 1e9
+    return {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": pk["source"]}
+
+
+def stage_profile(r, fn, steps, flush=None):
+    """Per-stage milliseconds (library event timer) per eager call of fn,
+    summed over the library calls fn makes."""
+    from paper_2311_18561_gb300 import render as R
+
+    R.profile_enable(r, True)
+    R.profile_read(r)
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        fn()
+    stages = R.profile_read(r)
+    R.profile_enable(r, False)
+    return {k: v[0] / max(steps, 1) for k, v in stages.items()}
+
+
+def tuned_step(dev, st, cams, targets, tile_arg="", tune_configs=None):
+    """A renderer in the autotuned (or given) configuration whose pair
+    capacity comes from one sized render (2x headroom), and its training
+    step over `cams`: forward, L1 against `targets`, backward, never reading
+    a size back (one CUDA graph)."""
+    import torch
+
+    from paper_2311_18561_gb300 import render as R
+
+    if tile_arg:
+        best, table = tuple(int(v) for v in tile_arg.split(",")), None
+    else:
+        from paper_2311_18561_gb300 import tune
+
+        kw = {} if tune_configs is None else {"configs": tune_configs}
+        best, table = tune.tune(st, cams, backward=True, use_cache=False, **kw)
+    probe, pfr = R.Renderer(tile=best[:2], pixels_per_thread=best[2]), R.Frame()
+    probe.forward(st, cams, frame=pfr)
+    pair_capacity = max(1 << 20, 2 * pfr.stats()[1])
+    probe.close()
+    pfr.close()
+    r = R.Renderer(tile=best[:2], pixels_per_thread=best[2], sync_sizes=False, pair_capacity=pair_capacity)
+    fr = R.Frame()
+    outs = r.alloc_images(cams)
+    grad_flat, grads = R.flat_gradients(st)
+    dls = [torch.empty_like(o["rgb"]) for o in outs]
+    losses = torch.empty(len(cams), device=dev)
+
+    def step():
+        r.forward(st, cams, outs=outs, frame=fr)
+        for v, o in enumerate(outs):
+            R.l1_loss(r, o["rgb"], targets[v], dl=dls[v], loss=losses[v:v + 1])
+        r.backward(st, cams, fr, [dict(rgb=d) for d in dls], grads=grads)
+
+    return dict(best=best, table=table, r=r, fr=fr, outs=outs, grads=grads, grad_flat=grad_flat, dls=dls,
+                losses=losses, step=step, pair_capacity=pair_capacity)
+
+
 # --------------------------------------------------------------------------- ours
 
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -286,35 +416,15 @@ def run_ours(args):
     st = R.scene_to_device(scene, dev)
     target_host = torch.from_numpy(synth.random_image(H_PIX, W_PIX, seed=1)).pin_memory()
     target = target_host.to(dev)
-    if args.tile:
-        tw, th, px = (int(v) for v in args.tile.split(","))
-        best, table = (tw, th, px), None
-    else:
-        from paper_2311_18561_gb300 import tune
-
-        best, table = tune.tune(st, [cam], backward=True, use_cache=False)
-    # pair capacity from one sized render (2x headroom): the timed renderer
-    # then never reads a size back to the host, so a step is one CUDA graph
-    probe, pfr = R.Renderer(tile=best[:2], pixels_per_thread=best[2]), R.Frame()
-    probe.forward(st, [cam], frame=pfr)
-    pair_capacity = max(1 << 20, 2 * pfr.stats()[1])
-    probe.close()
-    pfr.close()
-    r = R.Renderer(tile=best[:2], pixels_per_thread=best[2], sync_sizes=False, pair_capacity=pair_capacity)
-    fr = R.Frame()
-    outs = r.alloc_images([cam])
-    # gradients as views of one flat buffer, so that a data-parallel step
-    # sums them over ranks with a single all-reduce
-    grad_flat, grads = R.flat_gradients(st)
+    ts = tuned_step(dev, st, [cam], [target], args.tile)
+    best, table, r, fr, outs = ts["best"], ts["table"], ts["r"], ts["fr"], ts["outs"]
+    grad_flat, grads, pair_capacity = ts["grad_flat"], ts["grads"], ts["pair_capacity"]
+    dl, loss = ts["dls"][0], ts["losses"][0:1]
     dp = args.dp and world > 1
-    dl = torch.empty(3, H_PIX, W_PIX, device=dev)
-    loss = torch.empty(1, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     def step():
-        r.forward(st, [cam], outs=outs, frame=fr)
-        R.l1_loss(r, outs[0]["rgb"], target, dl=dl, loss=loss)
-        r.backward(st, [cam], fr, [dict(rgb=dl)], grads=grads)
+        ts["step"]()
         if dp:
             R.allreduce_gradients(grad_flat)
 
@@ -326,40 +436,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(fn, steps):
-        """Per-step CUDA events around fn (L2 flushed before each step, outside
-        the events); returns the summed step milliseconds."""
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in evs:
-            flush.zero_()
-            a.record()
-            fn()
-            b.record()
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs)
-
-    def capture(fn):
-        """fn's launches as one CUDA graph (buffers are already sized) and
-        the number of library kernels it holds."""
-        side = torch.cuda.Stream(device=dev)
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            fn()
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        n0 = R.kernel_launches()
-        with torch.cuda.graph(g):
-            fn()
-        torch.cuda.synchronize()
-        return g, R.kernel_launches() - n0
-
     for _ in range(max(3, args.warmup)):
         step()
     barrier()
     # (a data-parallel step keeps its collective outside a captured graph)
-    step_graph, launches_per_step = capture(step) if not dp else (None, 35)
-    fwd_graph, _ = capture(fwd_only)
+    step_graph, launches_per_step = capture_graph(step, dev) if not dp else (None, 35)
+    fwd_graph, _ = capture_graph(fwd_only, dev)
     barrier()
 
     # ---- timed region: K full steps, each one replay of the captured step
@@ -367,24 +449,18 @@ def run_ours(args):
     clocks.start()
     barrier()
     t0 = time.perf_counter()
-    step_ms = timed(step_graph.replay if step_graph is not None else step, args.steps)
+    step_ms = timed_steps(step_graph.replay if step_graph is not None else step, args.steps, flush)
     barrier()
     wall = time.perf_counter() - t0
     launches = launches_per_step * args.steps
     # forward-only rate (same protocol)
-    fwd_ms = timed(fwd_graph.replay, args.steps) / args.steps
+    fwd_ms = timed_steps(fwd_graph.replay, args.steps, flush) / args.steps
     # the FP32 peak of the ALU rooflines, at the clocks sampled here
     fp32 = measure_fp32_peak(dev)
     clk = clocks.stop()
     # per-stage times from the library's event timer, in eager steps after
     # the timed region (the events add a little time of their own)
-    R.profile_enable(r, True)
-    R.profile_read(r)
-    for _ in range(args.steps):
-        flush.zero_()
-        step()
-    stages = R.profile_read(r)
-    R.profile_enable(r, False)
+    stage_ms = stage_profile(r, step, args.steps, flush)
 
     M, K, ov = fr.stats()
     if ov:
@@ -444,10 +520,11 @@ def run_ours(args):
     for _ in range(0 if args.no_legs else 3):
         step_paper_loss()
     if not args.no_legs:
-        paper_graph, _ = capture(step_paper_loss)
-        paper_step_ms = timed(paper_graph.replay, args.steps) / args.steps
-        loss_graph, _ = capture(lambda: R.rgb_loss(r, outs[0]["rgb"], target, lambda_r=0.2, dl=dl, loss=loss3))
-        loss_ms = timed(loss_graph.replay, args.steps) / args.steps
+        paper_graph, _ = capture_graph(step_paper_loss, dev)
+        paper_step_ms = timed_steps(paper_graph.replay, args.steps, flush) / args.steps
+        loss_graph, _ = capture_graph(lambda: R.rgb_loss(r, outs[0]["rgb"], target, lambda_r=0.2, dl=dl,
+                                                         loss=loss3), dev)
+        loss_ms = timed_steps(loss_graph.replay, args.steps, flush) / args.steps
         # separable filtering: 5 moments and 3 derivative maps x 2 passes x 11 taps,
         # 3 products, ~20 for S and its derivatives, 5 for the gradient, 3 for L1
         loss_ops = 3 * W_PIX * H_PIX * OPS_PER_LOSS_PIXEL
@@ -479,44 +556,16 @@ def run_ours(args):
 
         for _ in range(3):
             step_features()
-        feat_graph, _ = capture(step_features)
+        feat_graph, _ = capture_graph(step_features, dev)
         features = {"channels": "v_bar (3) + rho (1) + 19 semantic classes",
-                    "step_ms": timed(feat_graph.replay, args.steps) / args.steps}
+                    "step_ms": timed_steps(feat_graph.replay, args.steps, flush) / args.steps}
         del st_f, outs_f, dl_feat, grads_f, feat_graph
 
     # ---- roofline of the dominant stage
-    stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items()}
-    dominant = max(stage_ms, key=stage_ms.get)
+    roof = dominant_roof(stage_ms, E, B, N_GAUSS, M, K, fp32,
+                         traffic=ncu_traffic("k_composite_bwd", "%dx%dx%d" % best) if args.workload == "urban"
+                         else None)
     pk = peaks()
-    roof = None
-    alu_peak = fp32["lane_fma_per_s"]  # measured lane-FMA rate (FMA probe)
-
-    def alu_roof(stage):
-        ops = E * OPS_PER_EVAL + B * OPS_PER_BLEND[stage]
-        ach = ops / (stage_ms[stage] * 1e-3)
-        kern = "k_composite" if stage == "composite" else "k_composite_bwd"
-        return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak / 1e12,
-                "unit": "T FP32-lane-instr/s", "frac": ach / alu_peak,
-                "traffic": ncu_traffic(kern, "%dx%dx%d" % best) if args.workload == "urban" else None,
-                "work": "E=%d in-footprint evaluations x %d + %d blended x %d FP32 instructions"
-                        % (E, OPS_PER_EVAL, B, OPS_PER_BLEND[stage]),
-                "peak_kind": "measured (FMA probe)",
-                "peak_source": "FP32 lane-FMA rate of the FMA probe in this run (%d SMs; %.1f T/s derived from "
-                               "%d SMs x 128 lanes x %.0f MHz)" % (fp32["sm_count"], fp32["derived_lane_per_s"] / 1e12,
-                                                                  fp32["sm_count"], pk["sm_max_mhz"])}
-
-    if dominant in ("composite", "composite_bwd"):
-        roof = alu_roof(dominant)
-    else:
-        # HBM-bound stages: algorithmic bytes per launch
-        algo = {"project": N_GAUSS * 68 + N_GAUSS * 8, "finalize": M * (68 + 192 + 48 + 8 + 4),
-                "preprocess_bwd": M * (260 + 40 + 260), "depth_sort": M * 4 * 20,
-                "pairs": M * 12 + K * 8, "tile_sort": K * 40}
-        b = algo.get(dominant, 0)
-        ach = b / (stage_ms[dominant] * 1e-3) / 1e9
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_kind": pk["source"]}
-
     out = {
         "metric": METRIC, "value": job_value(world, mpix, ms_step), "unit": "Mpix/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -535,7 +584,7 @@ def run_ours(args):
         "render_fwd": {"ms": fwd_ms, "mpix_s": job_value(world, mpix, fwd_ms)},
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "visible": M, "pairs": K, "evals": E, "blended_evals": B, "overflow": ov,
-        "roofline_composite_fwd": alu_roof("composite"),
+        "roofline_composite_fwd": alu_roof("composite", stage_ms, E, B, fp32),
         "sm_count": fp32["sm_count"],
         "fp32_peak": {"value": fp32["lane_fma_per_s"] / 1e12, "unit": "T lane-FMA/s", "kind": "measured",
                       **{k: v for k, v in fp32.items() if k != "lane_fma_per_s"}},
@@ -554,10 +603,21 @@ def run_ours(args):
         "paper_loss_step": paper_loss,
         "features_step": features,
     }
-    if not args.no_serve:
-        del st, grads, flush
+    del flush
+    if rank == 0 and not args.no_legs and args.workload == "urban":
+        # the other configurations, each with its own roofline
+        del st, grads, grad_flat, ts, r, fr, outs
         torch.cuda.empty_cache()
-        out["serving"] = serving_leg(dev, args.serve_rate, args.serve_seconds or 2.0, config=best)
+        out["training"] = training_leg(dev, max(3, args.steps // 2), fp32)
+        torch.cuda.empty_cache()
+        out["batched"] = batched_leg(dev, max(3, args.steps // 4), fp32)
+        torch.cuda.empty_cache()
+    if not args.no_serve and rank == 0:
+        torch.cuda.empty_cache()
+        rates = [args.serve_rate] if args.serve_rate else [200.0, 500.0, 1000.0, 2000.0]
+        out["serving"] = {"legs": [serving_leg(dev, rt, args.serve_seconds or 5.0, config=(16, 16, 1))
+                                   for rt in rates]}
+        release_serve_scenes()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scene, cam, args.cpu_seconds)
     if world > 1:
@@ -567,9 +627,105 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
+def training_leg(dev, steps, fp32):
+    """The training configuration: a 1M-Gaussian urban-distribution scene
+    at 1242x375 (f = 720), frame 25, forward + L1 + backward as one CUDA
+    graph in the autotuned configuration; stage times, K / E counts and
+    the roofline of its dominant stage."""
+    import torch
+
+    from paper_2311_18561_gb300 import render as R
+    from paper_2311_18561_gb300 import synth
+
+    n, w, h, f = WORKLOADS["training"][:4]
+    scene = R.scene_to_device(synth.make_urban_scene(n, seed=0), dev)
+    cam = synth.street_camera(FRAME / 49.0, w, h, fx=f)
+    target = torch.from_numpy(synth.random_image(h, w, seed=1)).to(dev)
+    ts = tuned_step(dev, scene, [cam], [target])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        ts["step"]()
+    g, launches = capture_graph(ts["step"], dev)
+    ms = timed_steps(g.replay, steps, flush) / steps
+    stage_ms = stage_profile(ts["r"], ts["step"], steps, flush)
+    M, K, ov = ts["fr"].stats()
+    ts["r"].forward(scene, [cam], outs=ts["outs"], frame=ts["fr"])
+    E, B = R.eval_count(ts["r"], ts["fr"])
+    mpix = w * h / 1e6
+    best = ts["best"]
+    return {"workload": WORKLOADS["training"][4], "ms_per_step": ms, "mpix_s": mpix / (ms * 1e-3),
+            "tile": "%dx%d, %d px/thread (autotuned)" % best, "steps": steps, "gpu_launches_per_step": launches,
+            "l2": "flushed before every step", "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "visible": M, "pairs": K, "evals": E, "blended_evals": B, "overflow": ov,
+            "roofline": dominant_roof(stage_ms, E, B, n, M, K, fp32),
+            "roofline_composite_bwd": alu_roof("composite_bwd", stage_ms, E, B, fp32)}
+
+
+def batched_leg(dev, steps, fp32):
+    """64 views (22 x 1920x1280, 21 x 1242x375, 21 x 960x640, own t each) of
+    a 3M-Gaussian urban scene: forward + L1 + backward replayed as one CUDA
+    graph, against one launch sequence per view; the stage split of both
+    (where the batched step spends its time against 64 single views)."""
+    import torch
+
+    from paper_2311_18561_gb300 import batch as Bt
+    from paper_2311_18561_gb300 import render as R
+    from paper_2311_18561_gb300 import synth
+
+    scene = R.scene_to_device(synth.make_urban_scene(3_000_000, seed=0), dev)
+    cams = synth.batched_views(seed=0, n_views=64)
+    g = Bt.BatchGraph(scene, cams, autotune=True,
+                      tune_configs=((16, 16, 1), (16, 16, 2), (16, 16, 4), (32, 16, 4), (16, 32, 4), (32, 32, 4)))
+    mpix = g.pixels / 1e6
+    for _ in range(3):
+        g.replay()
+    ms_graph = timed_steps(g.replay, steps) / steps
+    over = g.overflowed()
+    tw, th, px = g.config
+    # the same 64-view step eagerly, for the stage split
+    stages_batched = stage_profile(g.r, g._enqueue, 2)
+    M, K, _ = g.frame.stats()
+    g.r.forward(scene, cams, outs=g.outs, frame=g.frame)
+    E, B = R.eval_count(g.r, g.frame)
+    # one launch sequence per view
+    r1 = R.Renderer(tile=(tw, th), pixels_per_thread=px)
+    f1 = R.Frame()
+    o1 = {}
+    grads = {k: torch.empty_like(scene[k]) for k in R.PARAM_NAMES}
+
+    def per_view():
+        for v, cam in enumerate(cams):
+            key = (cam["width"], cam["height"])
+            if key not in o1:
+                o1[key] = r1.alloc_images([cam])
+            o = r1.forward(scene, [cam], outs=o1[key], frame=f1)[0]
+            dl = R.l1_loss(r1, o["rgb"], g.targets[v])[1]
+            r1.backward(scene, [cam], f1, [dict(rgb=dl)], grads=grads)
+
+    per_view()
+    ms_per_view = timed_steps(per_view, max(2, steps // 2)) / max(2, steps // 2)
+    stages_per_view = stage_profile(r1, per_view, 1)
+    r1.close()
+    f1.close()
+    return {"workload": "batched: 64 views (22x1920x1280, 21x1242x375, 21x960x640), 3M Gaussians SH-3, "
+                        "fwd + L1 + bwd", "mpix_per_batch": mpix, "tile": "%dx%d, %d px/thread (autotuned)" % g.config,
+            "pair_capacity": g.pair_capacity, "overflow": over, "visible": M, "pairs": K, "evals": E,
+            "blended_evals": B,
+            "graph": {"ms": ms_graph, "mpix_s": mpix / (ms_graph * 1e-3)},
+            "one_launch_per_view": {"ms": ms_per_view, "mpix_s": mpix / (ms_per_view * 1e-3)},
+            "stages_ms_batched": {k: round(v, 3) for k, v in stages_batched.items()},
+            "stages_ms_per_view_sum": {k: round(v, 3) for k, v in stages_per_view.items()},
+            "roofline": dominant_roof(stages_batched, E, B, 64 * 3_000_000, M, K, fp32)}
+
+
 # --------------------------------------------------------------------------- serving
 
 SERVE_SCENES = None
+
+
+def release_serve_scenes():
+    global SERVE_SCENES
+    SERVE_SCENES = None
 
 
 def serve_scenes(dev):
@@ -596,7 +752,8 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
     """Poisson arrivals at `rate` req/s for `seconds` (random scene, pose on
     the street path +-2 m, t ~ U[0,1], resolution from {640x480, 1242x375,
     1920x1280}) served by the continuous-batching server, then the same
-    schedule served one request per launch, synchronously."""
+    schedule served one request per launch, synchronously (the plain path:
+    one pvg_render_fwd call per request and a wait for its image)."""
     import collections
 
     import torch
@@ -616,16 +773,22 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
     srv = S.Server(max_batch_views=max_batch_views, n_streams=n_streams, memory_budget=24 << 30,
                    tile=config[:2], pixels_per_thread=config[2])
     ids = [srv.add_scene(sc) for sc in scenes]
-    # warm-up: grow every worker's workspace to the worst case, full
-    # batches of the largest scene at the largest resolution
+    # warm-up: every scene at every resolution once (the server learns each
+    # scene's pairs per pixel), then a burst of full batches
     warm = []
+    for sid in ids:
+        for w, h in synth.SERVE_RESOLUTIONS:
+            cam = synth.street_camera(0.5, w, h)
+            warm.append((srv.submit(sid, cam, dict(rgb=buf(cam))), cam))
     for k in range(2 * n_streams * max_batch_views):
         cam = synth.street_camera(0.5, 1920, 1280)
-        warm.append(srv.submit(ids[-1], cam, dict(rgb=buf(cam))))
-    for rid in warm:
+        warm.append((srv.submit(ids[k % len(ids)], cam, dict(rgb=buf(cam))), cam))
+    for rid, cam in warm:
         srv.wait(rid, 120.0)
         srv.release(rid)
     torch.cuda.synchronize()
+    c0 = srv.counters()
+    requeues0 = srv.arena()["requeues"]
     stats, outstanding, i = [], collections.deque(), 0
     t0 = time.perf_counter()
     while i < len(reqs) or outstanding:
@@ -646,13 +809,18 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
             outstanding.popleft()
         time.sleep(0.0002)
     counters = srv.counters()
+    arena = srv.arena()
     srv.close()
     lat = [st["done_ms"] - st["submit_ms"] for st, _ in stats]
     span_ms = max(st["done_ms"] for st, _ in stats) - min(st["submit_ms"] for st, _ in stats)
     pix = sum(c["width"] * c["height"] for _, c in stats)
     p50, p99 = _percentiles(lat)
+    batches = counters["batches"] - c0["batches"]
+    views = counters["views"] - c0["views"]
     served = {"p50_ms": p50, "p99_ms": p99, "mpix_s": pix / (span_ms * 1e-3) / 1e6, "requests": len(stats),
-              "launches": counters["batches"], "mean_views_per_launch": counters["views"] / max(1, counters["batches"]),
+              "launches": batches, "mean_views_per_launch": views / max(1, batches),
+              "mean_gpu_ms_per_request": sum(st["gpu_ms"] for st, _ in stats) / max(1, len(stats)),
+              "requeues": arena["requeues"] - requeues0,
               "errors": sum(1 for st, _ in stats if st["status"] != 0)}
     # one request per launch, synchronous, same schedule
     r = R.Renderer(tile=config[:2], pixels_per_thread=config[2])
@@ -676,8 +844,9 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
     q50, q99 = _percentiles(lat1)
     one = {"p50_ms": q50, "p99_ms": q99, "mpix_s": pix / span1 / 1e6}
     return {"rate_req_s": rate, "seconds": seconds, "scenes": list(synth.SERVE_SCENE_SIZES),
-            "max_batch_views": max_batch_views, "streams": n_streams, "served": served,
-            "one_request_per_launch": one}
+            "max_batch_views": max_batch_views, "streams": n_streams,
+            "arena_per_worker": {k: arena[k] for k in ("items_per_batch", "pixels_per_batch", "pairs_per_batch")},
+            "free_bytes_at_create": arena["free_bytes"], "served": served, "one_request_per_launch": one}
 
 
 def run_serving(args):
@@ -687,88 +856,23 @@ def run_serving(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    rates = [200.0, 500.0, 1000.0, 2000.0]
+    rates = [args.serve_rate] if args.serve_rate else [200.0, 500.0, 1000.0, 2000.0]
     res = [serving_leg(dev, rt, args.serve_seconds or 10.0) for rt in rates]
     if rank == 0:
         print(json.dumps({"metric": METRIC, "workload": "serving sweep", "legs": res}), flush=True)
 
 
 def run_batched(args):
-    """64 views (22 x 1920x1280, 21 x 1242x375, 21 x 960x640, own t each) of
-    a 3M-Gaussian urban scene: forward + L1 + backward replayed as one CUDA
-    graph, against the same calls uncaptured and against one launch
-    sequence per view."""
+    """The batched configuration on its own (see batched_leg)."""
     import torch
-
-    from paper_2311_18561_gb300 import batch as B
-    from paper_2311_18561_gb300 import render as R
-    from paper_2311_18561_gb300 import synth
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scene = R.scene_to_device(synth.make_urban_scene(3_000_000, seed=0), dev)
-    cams = synth.batched_views(seed=0, n_views=64)
-    g = B.BatchGraph(scene, cams, autotune=not args.tile,
-                     config=tuple(int(v) for v in args.tile.split(",")) if args.tile else None,
-                     tune_configs=((16, 16, 1), (16, 16, 2), (16, 16, 4), (32, 16, 4), (16, 32, 4), (32, 32, 4)))
-    mpix = g.pixels / 1e6
-
-    def timed(fn, steps):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in evs:
-            a.record()
-            fn()
-            b.record()
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs) / steps
-
-    for _ in range(max(3, args.warmup)):
-        g.replay()
-    ms_graph = timed(g.replay, args.steps)
-    over = g.overflowed()
-    tw, th, px = g.config
-    # uncaptured, one call for all views (size read-back per call)
-    r = R.Renderer(tile=(tw, th), pixels_per_thread=px)
-    fr = R.Frame()
-    outs = r.alloc_images(cams)
-    grads = {k: torch.empty_like(scene[k]) for k in R.PARAM_NAMES}
-
-    def direct():
-        r.forward(scene, cams, outs=outs, frame=fr)
-        dls = []
-        for v, o in enumerate(outs):
-            dls.append(dict(rgb=R.l1_loss(r, o["rgb"], g.targets[v])[1]))
-        r.backward(scene, cams, fr, dls, grads=grads)
-
-    direct()
-    ms_direct = timed(direct, max(3, args.steps // 4))
-    fr.close()
-    del outs
-    # one launch sequence per view
-    r1 = R.Renderer(tile=(tw, th), pixels_per_thread=px)
-    f1 = R.Frame()
-    o1 = {}
-
-    def per_view():
-        for v, cam in enumerate(cams):
-            key = (cam["width"], cam["height"])
-            if key not in o1:
-                o1[key] = r1.alloc_images([cam])
-            o = r1.forward(scene, [cam], outs=o1[key], frame=f1)[0]
-            dl = R.l1_loss(r1, o["rgb"], g.targets[v])[1]
-            r1.backward(scene, [cam], f1, [dict(rgb=dl)], grads=grads)
-
-    per_view()
-    ms_per_view = timed(per_view, max(2, args.steps // 8))
+    fp32 = measure_fp32_peak(dev)
+    res = batched_leg(dev, max(3, args.steps), fp32)
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "workload": "batched: 64 views (22x1920x1280, 21x1242x375, 21x960x640), "
-            "3M Gaussians SH-3, fwd + L1 + bwd", "mpix_per_batch": mpix, "config": list(g.config),
-            "pair_capacity": g.pair_capacity, "overflow": over,
-            "graph": {"ms": ms_graph, "mpix_s": mpix / (ms_graph * 1e-3)},
-            "uncaptured_one_call": {"ms": ms_direct, "mpix_s": mpix / (ms_direct * 1e-3)},
-            "one_launch_per_view": {"ms": ms_per_view, "mpix_s": mpix / (ms_per_view * 1e-3)}}), flush=True)
+        print(json.dumps({"metric": METRIC, **res}), flush=True)
 
 
 # --------------------------------------------------------------------------- oracle
