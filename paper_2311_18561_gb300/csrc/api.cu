@@ -830,9 +830,10 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     struct { float *p; size_t n; } zero[] = {
         {grads->mu, 3 * N}, {grads->vel, 3 * N}, {grads->tau, N}, {grads->beta, N}, {grads->period, N},
         {grads->scale, 3 * N}, {grads->quat, 4 * N}, {grads->opacity, N}, {grads->sh, 3 * K * N}};
-    // one view: k_preprocess_bwd writes every entry (zeros for invisible
-    // Gaussians); several views accumulate with atomics into zeroed arrays
-    if (n_views > 1 || f->n_items == 0)
+    // k_preprocess_bwd (one view) and k_preprocess_bwd_views (several views
+    // of the scene) write every entry, zeros for the Gaussians no view sees;
+    // without visible items nothing runs, so the arrays are zeroed here
+    if (f->n_items == 0)
         for (auto &z : zero)
             if (z.p && z.n) PVG_CUDA(cudaMemsetAsync(z.p, 0, sizeof(float) * z.n, s));
     if (scene->sky && grads->sky)

@@ -53,6 +53,20 @@ __device__ __forceinline__ void sh_coef_adjoint(float x, float y, float z, const
         for (int c = 0; c < 3; c++) put(gsh, 3 * (size_t)k + c, gcol[c] * Y[k], atomic);
 }
 
+// dL/dsh[k][c] += gcol[c] Y_k(d) into acc[(3 k + c) * stride] (shared
+// memory, one column per thread)
+template <int D>
+__device__ __forceinline__ void sh_coef_accumulate(float x, float y, float z, const float (&gcol)[3], float *acc,
+                                                   int stride) {
+    constexpr int K = (D + 1) * (D + 1);
+    float Y[16], dY[16][3];
+    sh_eval<D, false>(x, y, z, Y, dY);
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[(3 * k + c) * stride] += gcol[c] * Y[k];
+}
+
 // dL/ddir = sum_k (gcol . sh_k) dY_k(d), reading the coefficients in
 // groups of four basis functions (three float4) when the rows allow it
 template <int D>
@@ -97,12 +111,14 @@ constexpr int kSmall = 17;
 
 // Adjoint of the projection and colour of visible item i of view V, from
 // the image-space gradients of its depth position m.  The SH coefficients'
-// gradients go to V.g_sh directly (written, or accumulated with `atomic`);
-// the others are returned.  False if the projection culls the item (then
-// nothing is written).
+// gradients go to V.g_sh directly (written, or accumulated with `atomic`),
+// or, with sh_acc, are added to sh_acc[(3 k + c) * sh_stride]; the others
+// are returned.  False if the projection culls the item (then nothing is
+// written).
 template <int D>
 __device__ __forceinline__ bool item_adjoint(const Params &P, const ViewDesc &V, uint32_t i, uint32_t m,
-                                             bool atomic, SmallGrads &out) {
+                                             bool atomic, SmallGrads &out, float *sh_acc = nullptr,
+                                             int sh_stride = 0) {
     constexpr int K = (D + 1) * (D + 1);
     Fwd F;
     if (!project(V, i, P.dilation, P.tile_w, P.tile_h, F)) return false;
@@ -211,7 +227,8 @@ __device__ __forceinline__ bool item_adjoint(const Params &P, const ViewDesc &V,
         dx *= inv; dy *= inv; dz *= inv;
         const float *shp = V.sh + (size_t)i * K * 3;
         const bool vec = aligned16(V.sh) && (!V.g_sh || aligned16(V.g_sh));
-        if (V.g_sh) sh_coef_adjoint<D>(dx, dy, dz, gcol, V.g_sh + (size_t)i * K * 3, vec, atomic);
+        if (sh_acc) sh_coef_accumulate<D>(dx, dy, dz, gcol, sh_acc, sh_stride);
+        else if (V.g_sh) sh_coef_adjoint<D>(dx, dy, dz, gcol, V.g_sh + (size_t)i * K * 3, vec, atomic);
         float gd[3];
         sh_dir_adjoint<D>(dx, dy, dz, gcol, shp, vec, gd);
         const float dot = dx * gd[0] + dy * gd[1] + dz * gd[2];
@@ -269,29 +286,66 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *sm
     return r;
 }
 
-__device__ __forceinline__ void put_small(const ViewDesc &V, uint32_t i, const SmallGrads &q) {
-    if (V.g_mu) for (int k = 0; k < 3; k++) atomicAdd(V.g_mu + 3 * (size_t)i + k, q.mu[k]);
-    if (V.g_vel) for (int k = 0; k < 3; k++) atomicAdd(V.g_vel + 3 * (size_t)i + k, q.vel[k]);
-    if (V.g_scale) for (int k = 0; k < 3; k++) atomicAdd(V.g_scale + 3 * (size_t)i + k, q.scale[k]);
-    if (V.g_quat) for (int k = 0; k < 4; k++) atomicAdd(V.g_quat + 4 * (size_t)i + k, q.quat[k]);
-    if (V.g_tau) atomicAdd(V.g_tau + i, q.tau);
-    if (V.g_beta) atomicAdd(V.g_beta + i, q.beta);
-    if (V.g_period) atomicAdd(V.g_period + i, q.period);
-    if (V.g_opac) atomicAdd(V.g_opac + i, q.opac);
-}
+// Several views of one scene: one thread per Gaussian walks the views
+// that see it (found 64 at a time from the inverse map, coalesced across
+// the warp), accumulates the item adjoints over those views -- the 17 small
+// gradients in registers, the SH-coefficient gradients in a column of
+// shared memory -- and writes every gradient entry once: no atomics and no
+// zeroing pass.
+constexpr int kViewsThreads = 128;
 
-// Several views (`atomic`): the gradients were zeroed before; every view's
-// visible items accumulate theirs, one thread per item.
 template <int D>
-__global__ void __launch_bounds__(256) k_preprocess_bwd_atomic(Params P) {
-    const uint32_t n = P.n_items;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
-        const uint32_t m = P.inv[g];
-        if (m == 0xffffffffu) continue;
-        const int view = view_of_item(P.views, P.n_views, g);
-        const ViewDesc &V = P.views[view];
-        SmallGrads q;
-        if (item_adjoint<D>(P, V, g - V.item_base, m, true, q)) put_small(V, g - V.item_base, q);
+__global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P) {
+    constexpr int K = (D + 1) * (D + 1);
+    extern __shared__ float s_sh[];  // [3 K][kViewsThreads]
+    const int tid = threadIdx.x;
+    const ViewDesc &V0 = P.views[0];  // every view renders the same scene (gradient pointers too)
+    const uint32_t n = V0.n;
+    float *col = V0.g_sh ? s_sh + tid : nullptr;
+    for (uint32_t i = blockIdx.x * kViewsThreads + tid; i < n; i += gridDim.x * kViewsThreads) {
+        SmallGrads acc = SmallGrads{};
+        if (col)
+#pragma unroll
+            for (int c = 0; c < 3 * K; c++) col[c * kViewsThreads] = 0.f;
+        for (int v0 = 0; v0 < P.n_views; v0 += 64) {
+            const int vn = min(64, P.n_views - v0);
+            unsigned long long mask = 0ull;
+            for (int v = 0; v < vn; v++)
+                if (P.inv[P.views[v0 + v].item_base + i] != 0xffffffffu) mask |= 1ull << v;
+            while (mask) {
+                const int v = __ffsll((long long)mask) - 1;
+                mask &= mask - 1ull;
+                const ViewDesc &V = P.views[v0 + v];
+                SmallGrads q;
+                if (!item_adjoint<D>(P, V, i, P.inv[V.item_base + i], false, q, col, kViewsThreads)) continue;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    acc.mu[k] += q.mu[k];
+                    acc.vel[k] += q.vel[k];
+                    acc.scale[k] += q.scale[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) acc.quat[k] += q.quat[k];
+                acc.tau += q.tau;
+                acc.beta += q.beta;
+                acc.period += q.period;
+                acc.opac += q.opac;
+            }
+        }
+        if (V0.g_mu) for (int k = 0; k < 3; k++) V0.g_mu[3 * (size_t)i + k] = acc.mu[k];
+        if (V0.g_vel) for (int k = 0; k < 3; k++) V0.g_vel[3 * (size_t)i + k] = acc.vel[k];
+        if (V0.g_scale) for (int k = 0; k < 3; k++) V0.g_scale[3 * (size_t)i + k] = acc.scale[k];
+        if (V0.g_quat) for (int k = 0; k < 4; k++) V0.g_quat[4 * (size_t)i + k] = acc.quat[k];
+        if (V0.g_tau) V0.g_tau[i] = acc.tau;
+        if (V0.g_beta) V0.g_beta[i] = acc.beta;
+        if (V0.g_period) V0.g_period[i] = acc.period;
+        if (V0.g_opac) V0.g_opac[i] = acc.opac;
+        if (col) {
+            float g[3 * K];
+#pragma unroll
+            for (int c = 0; c < 3 * K; c++) g[c] = col[c * kViewsThreads];
+            store_floats<3 * K>(V0.g_sh + (size_t)i * 3 * K, g, aligned16(V0.g_sh));
+        }
     }
 }
 
@@ -405,14 +459,21 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
 
 }  // namespace
 
-void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s) {
+void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s) {
     note_launch();
-    if (accumulate_atomic) {
+    if (several_views) {
+        // the host copy of the views: every view has the scene's n items
+        const uint32_t n = p.n_views > 0 ? p.n_items / (uint32_t)p.n_views : 0u;
+        uint32_t grid = (n + kViewsThreads - 1) / kViewsThreads;
+        const uint32_t cap = 16u * (uint32_t)device_sm_count();
+        if (grid > cap) grid = cap;
+        if (grid < 1) grid = 1;
+        const size_t smem = sizeof(float) * 3 * (p.sh_degree + 1) * (p.sh_degree + 1) * kViewsThreads;
         switch (p.sh_degree) {
-            case 0: k_preprocess_bwd_atomic<0><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
-            case 1: k_preprocess_bwd_atomic<1><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
-            case 2: k_preprocess_bwd_atomic<2><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
-            default: k_preprocess_bwd_atomic<3><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+            case 0: k_preprocess_bwd_views<0><<<grid, kViewsThreads, smem, s>>>(p); break;
+            case 1: k_preprocess_bwd_views<1><<<grid, kViewsThreads, smem, s>>>(p); break;
+            case 2: k_preprocess_bwd_views<2><<<grid, kViewsThreads, smem, s>>>(p); break;
+            default: k_preprocess_bwd_views<3><<<grid, kViewsThreads, smem, s>>>(p); break;
         }
         return;
     }

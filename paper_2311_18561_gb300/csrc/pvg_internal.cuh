@@ -399,7 +399,7 @@ cudaError_t set_sh_constants();      // both copies of the SH constants
 cudaError_t set_sh_constants_bwd();  // the adjoint's copy
 void launch_project_count(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);
-void launch_preprocess_bwd(const Params &p, bool accumulate_atomic, cudaStream_t s);
+void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s);
 // sort / scan
 size_t sort_temp_bytes();  // kSortTempBytes
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);

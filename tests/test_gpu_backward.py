@@ -204,3 +204,34 @@ def test_backward_through_the_jacobian_clamp(colour_only):
     _compare_grads(grads, ref)
     # the clamped Gaussians carry gradient
     assert np.count_nonzero(np.abs(ref["mu"][:n_off]).sum(axis=1)) >= n_off - 2
+
+
+def test_backward_of_70_views_sums_the_views():
+    """70 views of one scene (more than the 64 views one pass of the
+    multi-view adjoint groups together), some seeing a Gaussian and some
+    not: the gradients are the sum of the oracle's per-view gradients."""
+    scene = synth.make_fd_scene(seed=9, n=300, sh_degree=2)
+    rng = np.random.default_rng(19)
+    cams = []
+    for k in range(70):
+        eye = (rng.uniform(-1.5, 1.5), rng.uniform(-1.0, 1.0), -3.5)
+        vm = synth.look_at(eye, (rng.uniform(-0.3, 0.3), 0.0, 0.0), (0.0, 1.0, 0.0))
+        w, h = int(rng.integers(20, 40)), int(rng.integers(16, 32))
+        cams.append(synth.make_camera(vm, w, h, synth.focal_from_hfov(w, 55.0), t=float(rng.uniform(0, 1))))
+    st = R.scene_to_device(scene)
+    r = R.Renderer()
+    fr = R.Frame()
+    r.forward(st, cams, frame=fr)
+    dls, ref = [], None
+    for k, cam in enumerate(cams):
+        w_rgb, w_d, w_a = _weights(cam["height"], cam["width"], 100 + k)
+        dls.append(dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"),
+                        depth=torch.tensor(w_d, dtype=torch.float32, device="cuda"),
+                        alpha=torch.tensor(w_a, dtype=torch.float32, device="cuda")))
+        g = oracle.render_bwd(scene, cam, np.transpose(w_rgb, (1, 2, 0)), w_d, w_a)
+        ref = g if ref is None else {n: ref[n] + g[n] for n in NAMES}
+    # stale values in the gradient buffers must not survive: every entry is written
+    grads = {k: torch.full_like(st[k], 7.0) for k in NAMES}
+    r.backward(st, cams, fr, dls, grads=grads)
+    torch.cuda.synchronize()
+    _compare_grads(grads, ref)
