@@ -235,10 +235,7 @@ void pvg_frame_destroy(pvg_frame_t *frame);
 /* Counters of the last forward into `frame` (synchronises `frame`'s last
  * stream): visible (view, Gaussian) pairs, tile/Gaussian pairs (one per
  * tile of a Gaussian's bounding rectangle that its footprint ellipse
- * o~ G >= 1/255, slightly widened, reaches) and the status bits: 1 = more
- * pairs than the fixed capacity, 2 = a bounded device-side wait of the
- * one-launch sort gave up (not seen in practice: its blocks are launched
- * co-resident); either leaves the images incomplete. */
+ * o~ G >= 1/255, slightly widened, reaches) and the overflow status. */
 pvg_status_t pvg_frame_stats(pvg_frame_t *frame, int64_t *n_visible, int64_t *n_pairs,
                              int32_t *overflowed);
 

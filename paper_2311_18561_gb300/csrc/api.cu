@@ -611,7 +611,7 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
         // position (0xffffffff stays for the invisible items)
         PVG_CUDA(cudaMemsetAsync(p.inv, 0xff, sizeof(uint32_t) * NV, s));
         radix_sort_pairs(p.szkey, p.sgid, ptr<uint32_t>(x->alt_keys), ptr<uint32_t>(x->alt_vals), &p.counters[0], NV,
-                         0, 31, x->temp.p, s, &in_alt, p.inv, &p.counters[3]);
+                         0, 31, x->temp.p, s, &in_alt, p.inv);
         if (in_alt) {  // 31 bits = 4 passes: never taken, kept for safety
             PVG_CUDA(cudaMemcpyAsync(p.szkey, x->alt_keys.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
             PVG_CUDA(cudaMemcpyAsync(p.sgid, x->alt_vals.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
@@ -655,8 +655,7 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
         tm.end(PVG_STAGE_PAIRS, s);
         tm.begin(PVG_STAGE_TILE_SORT, s);
         bool t_alt = false;
-        radix_sort_pairs(E_keys, E_vals, F_keys, F_vals, &p.counters[1], pair_cap, 0, tbits, x->temp.p, s, &t_alt,
-                         nullptr, &p.counters[3]);
+        radix_sort_pairs(E_keys, E_vals, F_keys, F_vals, &p.counters[1], pair_cap, 0, tbits, x->temp.p, s, &t_alt);
         p.pair_keys = t_alt ? F_keys : E_keys;
         p.pair_vals = ptr<uint32_t>(f->pair_vals);
         launch_ranges(p, s);
@@ -936,7 +935,7 @@ extern "C" pvg_status_t pvg_frame_stats(pvg_frame_t *f, int64_t *n_visible, int6
     PVG_CUDA(cudaStreamSynchronize(f->stream));
     if (n_visible) *n_visible = f->h_counters[0];
     if (n_pairs) *n_pairs = f->h_counters[1];
-    if (overflowed) *overflowed = (int32_t)((f->h_counters[2] ? 1u : 0u) | (f->h_counters[3] ? 2u : 0u));
+    if (overflowed) *overflowed = (int32_t)f->h_counters[2];
     return PVG_OK;
 }
 

@@ -394,9 +394,7 @@ int device_sm_count();
 constexpr int kMaxSortBlocks = 1024;
 constexpr int kSortRadix = 256;
 constexpr int kMaxScanBlocks = 1024;
-constexpr int kSortBarrierWords = 4;  // the one-launch sort's grid barrier and error word
-constexpr size_t kSortTempBytes =
-    sizeof(uint32_t) * ((size_t)kSortRadix * kMaxSortBlocks + kMaxScanBlocks + kSortBarrierWords);
+constexpr size_t kSortTempBytes = sizeof(uint32_t) * ((size_t)kSortRadix * kMaxSortBlocks + kMaxScanBlocks);
 cudaError_t set_sh_constants();      // both copies of the SH constants
 cudaError_t set_sh_constants_bwd();  // the adjoint's copy
 void launch_project_count(const Params &p, cudaStream_t s);
@@ -406,12 +404,10 @@ void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s);
 size_t sort_temp_bytes();  // kSortTempBytes
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);
 // inv_out (optional): the last pass also writes inv_out[value] = the
-// value's final position.  err (optional): with it, the sort may run as
-// one cooperative launch whose bounded grid barriers set *err (device
-// memory) if a wait gives up; without it, the multi-launch passes run.
+// value's final position
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out = nullptr, uint32_t *err = nullptr);
+                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out = nullptr);
 void scan_count_pairs(const Params &p, void *temp, cudaStream_t s);
 void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
 size_t emit_chunks(uint32_t capacity);

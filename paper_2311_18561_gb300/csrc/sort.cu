@@ -21,8 +21,6 @@
 // (stability across blocks); inside a block, tiles are taken in order and
 // ranked stably within each warp with __match_any_sync.
 #include <algorithm>
-#include <atomic>
-#include <cstring>
 #include "pvg_internal.cuh"
 
 namespace pvg {
@@ -83,15 +81,6 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *smem, 
     *total = smem[32];
     __syncthreads();
     return r;
-}
-
-__device__ __forceinline__ void segment_of_block(uint32_t n, int G, int blk, int align, uint32_t *b0, uint32_t *b1) {
-    uint32_t seg = (n + G - 1) / G;
-    seg = (seg + align - 1) / align * align;
-    const uint64_t s = (uint64_t)blk * seg;
-    *b0 = (uint32_t)(s < n ? s : n);
-    const uint64_t e = s + seg;
-    *b1 = (uint32_t)(e < n ? e : n);
 }
 
 __device__ __forceinline__ void segment_of(uint32_t n, int G, int align, uint32_t *b0, uint32_t *b1) {
@@ -214,25 +203,18 @@ int sort_blocks(uint32_t capacity, int tile) {
 
 // ---------------------------------------------------------------- radix
 
-// digit histogram of block blk's segment of keys[0, n): hist[d * G + blk]
-template <int ITEMS>
-__device__ __forceinline__ void radix_hist_segment(const uint32_t *keys, uint32_t n, int G, int blk, int shift,
-                                                   uint32_t mask, uint32_t *hist, uint32_t *sh) {
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) sh[d] = 0;
-    __syncthreads();
-    uint32_t b0, b1;
-    segment_of_block(n, G, blk, kSortThreads * ITEMS, &b0, &b1);
-    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kSortThreads) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * G + blk] = sh[d];
-}
-
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *keys, const uint32_t *d_n,
                                                                 uint32_t cap, int shift, uint32_t mask,
                                                                 uint32_t *hist) {
     __shared__ uint32_t sh[kRadix];
-    radix_hist_segment<ITEMS>(keys, min(*d_n, cap), gridDim.x, blockIdx.x, shift, mask, hist, sh);
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) sh[d] = 0;
+    __syncthreads();
+    uint32_t b0, b1;
+    segment_of(min(*d_n, cap), gridDim.x, kSortThreads * ITEMS, &b0, &b1);
+    for (uint32_t i = b0 + threadIdx.x; i < b1; i += kSortThreads) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d * gridDim.x + blockIdx.x] = sh[d];
 }
 
 // Row scan of the digit-major histogram hist[d * G + b], one block per
@@ -408,28 +390,27 @@ struct SortSmem {
     uint32_t scan[33];
 };
 
-// Scatter of block blk's segment of keys[0, n) to its digit positions
-// (the pass's digit bases: exclusive prefix of the digit totals plus the
-// block's exclusive prefix hist[d * G + blk]).  NB: ballots per key in the
-// ranking (the pass's digit width, or 8).
+// NB: ballots per key in the ranking (the pass's digit width, or 8)
 template <int ITEMS, int NB>
-__device__ __forceinline__ void radix_scatter_segment(const uint32_t *__restrict__ keys_in,
-                                                      const uint32_t *__restrict__ vals_in,
-                                                      uint32_t *__restrict__ keys_out,
-                                                      uint32_t *__restrict__ vals_out, uint32_t n, int G, int blk,
-                                                      int shift, uint32_t mask, const uint32_t *hist,
-                                                      const uint32_t *totals, uint32_t *__restrict__ inv_out,
-                                                      SortSmem<kSortThreads * ITEMS> &S) {
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
+                                                                  const uint32_t *__restrict__ vals_in,
+                                                                  uint32_t *__restrict__ keys_out,
+                                                                  uint32_t *__restrict__ vals_out,
+                                                                  const uint32_t *d_n, uint32_t cap, int shift,
+                                                                  uint32_t mask, const uint32_t *hist,
+                                                                  const uint32_t *totals,
+                                                                  uint32_t *__restrict__ inv_out) {
     constexpr int kSortTile = kSortThreads * ITEMS;
+    __shared__ SortSmem<kSortTile> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         // digit bases: exclusive prefix of the per-digit totals (one thread per digit)
         uint32_t tot;
         const uint32_t dbase = block_excl_scan(totals[tid], S.scan, &tot);
-        S.base[tid] = dbase + hist[tid * G + blk];
+        S.base[tid] = dbase + hist[tid * gridDim.x + blockIdx.x];
     }
     uint32_t b0, b1;
-    segment_of_block(n, G, blk, kSortTile, &b0, &b1);
+    segment_of(min(*d_n, cap), gridDim.x, kSortTile, &b0, &b1);
     const uint32_t lt = lanemask_lt();
     for (uint32_t t0 = b0; t0 < b1; t0 += kSortTile) {
         for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&S.warp_hist[0][0])[k] = 0;
@@ -499,140 +480,6 @@ __device__ __forceinline__ void radix_scatter_segment(const uint32_t *__restrict
     }
 }
 
-
-template <int ITEMS, int NB>
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
-                                                                  const uint32_t *__restrict__ vals_in,
-                                                                  uint32_t *__restrict__ keys_out,
-                                                                  uint32_t *__restrict__ vals_out,
-                                                                  const uint32_t *d_n, uint32_t cap, int shift,
-                                                                  uint32_t mask, const uint32_t *hist,
-                                                                  const uint32_t *totals,
-                                                                  uint32_t *__restrict__ inv_out) {
-    __shared__ SortSmem<kSortThreads * ITEMS> S;
-    radix_scatter_segment<ITEMS, NB>(keys_in, vals_in, keys_out, vals_out, min(*d_n, cap), gridDim.x, blockIdx.x,
-                                     shift, mask, hist, totals, inv_out, S);
-}
-
-// ---------------------------------------------------------------- one-launch sort
-
-// Row scan of hist[d * G + b] over b for digit d by a block of
-// kSortThreads threads (G <= kMaxSortBlocks): each thread sums a run of
-// consecutive entries, the runs' sums are scanned, the runs rewritten as
-// exclusive prefixes; the row total goes to totals[d].
-__device__ __forceinline__ void radix_scan_row(uint32_t *hist, uint32_t *totals, int G, int d, uint32_t *smem) {
-    uint32_t *row = hist + (size_t)d * G;
-    const int per = (G + kSortThreads - 1) / kSortThreads;
-    const int r0 = threadIdx.x * per;
-    uint32_t sum = 0;
-    for (int k = 0; k < per; k++)
-        if (r0 + k < G) sum += row[r0 + k];
-    uint32_t tot;
-    uint32_t run = block_excl_scan(sum, smem, &tot);
-    for (int k = 0; k < per; k++)
-        if (r0 + k < G) {
-            const uint32_t v = row[r0 + k];
-            row[r0 + k] = run;
-            run += v;
-        }
-    if (threadIdx.x == 0) totals[d] = tot;
-    __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long sort_globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Barrier of all G blocks of a cooperative launch (every block is resident,
-// so every block arrives).  The wait is bounded -- an iteration cap and a
-// 1 s globaltimer deadline -- after which the block sets *err and the
-// barrier returns false; the kernel then stops (its result is invalid and
-// *err tells the host).  bar[0] counts the arrivals, bar[1] is the
-// generation; bar[0] must be 0 when the kernel starts.
-constexpr uint32_t kBarrierSpinCap = 1u << 24;
-
-__device__ __forceinline__ bool grid_barrier(uint32_t *bar, uint32_t *err, int G) {
-    __shared__ uint32_t s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t ok = 1;
-        const uint32_t gen = ld_acquire_gpu(&bar[1]);
-        __threadfence();
-        if (atomicAdd(&bar[0], 1u) == (uint32_t)G - 1u) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            st_release_gpu(&bar[1], gen + 1u);
-        } else {
-            const unsigned long long t0 = sort_globaltimer();
-            for (uint32_t it = 0;; ++it) {
-                if (ld_acquire_gpu(&bar[1]) != gen) break;
-                if (it >= kBarrierSpinCap || sort_globaltimer() - t0 > 1000000000ull) {
-                    atomicExch(err, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        if (ok && ld_acquire_gpu(err) != 0u) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0u;
-}
-
-// The whole LSD radix sort of keys[0, min(*d_n, cap)) by bits [begin_bit,
-// end_bit) in one cooperative launch: per digit pass, the digit histograms
-// of the blocks' segments, a barrier, the row scans, a barrier, the
-// scatter, a barrier.  The same partition, ranking and scatter as the
-// multi-launch passes, so the result is the same bit for bit.
-template <int ITEMS>
-__global__ void __launch_bounds__(kSortThreads) k_radix_coop(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
-                                                             uint32_t *vals_alt, const uint32_t *d_n, uint32_t cap,
-                                                             int begin_bit, int end_bit, uint32_t *hist,
-                                                             uint32_t *totals, uint32_t *bar, uint32_t *err,
-                                                             uint32_t *inv_out) {
-    __shared__ SortSmem<kSortThreads * ITEMS> S;
-    const uint32_t n = min(*d_n, cap);
-    const int G = gridDim.x, blk = blockIdx.x;
-    bool alt = false;
-    for (int b = begin_bit; b < end_bit;) {
-        const int nb = (end_bit - b) >= 8 ? 8 : (end_bit - b);
-        const uint32_t mask = (1u << nb) - 1u;
-        const uint32_t *ki = alt ? keys_alt : keys;
-        const uint32_t *vi = alt ? vals_alt : vals;
-        uint32_t *ko = alt ? keys : keys_alt;
-        uint32_t *vo = alt ? vals : vals_alt;
-        radix_hist_segment<ITEMS>(ki, n, G, blk, b, mask, hist, S.base);
-        if (!grid_barrier(bar, err, G)) return;
-        for (int d = blk; d < kRadix; d += G) radix_scan_row(hist, totals, G, d, S.scan);
-        if (!grid_barrier(bar, err, G)) return;
-        uint32_t *inv_pass = b + nb >= end_bit ? inv_out : nullptr;
-        switch (nb) {
-            case 3: radix_scatter_segment<ITEMS, 3>(ki, vi, ko, vo, n, G, blk, b, mask, hist, totals, inv_pass, S); break;
-            case 4: radix_scatter_segment<ITEMS, 4>(ki, vi, ko, vo, n, G, blk, b, mask, hist, totals, inv_pass, S); break;
-            case 5: radix_scatter_segment<ITEMS, 5>(ki, vi, ko, vo, n, G, blk, b, mask, hist, totals, inv_pass, S); break;
-            case 7: radix_scatter_segment<ITEMS, 7>(ki, vi, ko, vo, n, G, blk, b, mask, hist, totals, inv_pass, S); break;
-            default: radix_scatter_segment<ITEMS, 8>(ki, vi, ko, vo, n, G, blk, b, mask, hist, totals, inv_pass, S); break;
-        }
-        if (!grid_barrier(bar, err, G)) return;
-        alt = !alt;
-        b += nb;
-    }
-}
-
 // [start, end) of every tile's run in the sorted keys.  Eight keys per
 // thread per sweep (two 16-byte loads and the two neighbours), so that
 // few dependent sweeps remain.
@@ -668,7 +515,6 @@ struct TempLayout {
     uint32_t *hist;      // kRadix * kMaxSortBlocks
     uint32_t *partials;  // kMaxScanBlocks
     uint32_t *totals;    // kRadix (shares the partials' space: never live together)
-    uint32_t *bar;       // kSortBarrierWords: the one-launch sort's barrier (count, generation) and error word
 };
 
 TempLayout temp_layout(void *temp) {
@@ -676,14 +522,12 @@ TempLayout temp_layout(void *temp) {
     t.hist = (uint32_t *)temp;
     t.partials = t.hist + kRadix * kMaxSortBlocks;
     t.totals = t.partials;
-    t.bar = t.partials + kMaxScanBlocks;
     return t;
 }
 
 }  // namespace
 
-static_assert(kSortTempBytes >= sizeof(uint32_t) * ((size_t)kRadix * kMaxSortBlocks + kMaxScanBlocks +
-                                                     kSortBarrierWords),
+static_assert(kSortTempBytes >= sizeof(uint32_t) * ((size_t)kRadix * kMaxSortBlocks + kMaxScanBlocks),
               "sort scratch layout");
 size_t sort_temp_bytes() { return kSortTempBytes; }
 
@@ -704,129 +548,9 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
                   uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt,
                   uint32_t *inv_out);
 
-// Whether cooperative launches of the one-launch sort work on the current
-// device: probed once per device by sorting a few keys both ways outside
-// any stream capture (a cooperative launch needs every block resident).
-// 0 = unknown, 1 = yes, -1 = no.
-static std::atomic<int> g_coop_ok[64];
-
-template <int ITEMS>
-cudaError_t launch_coop(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                        const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                        cudaStream_t s, uint32_t *err, uint32_t *inv_out) {
-    TempLayout t = temp_layout(temp);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_radix_coop<ITEMS>, kSortThreads, 0);
-    if (e != cudaSuccess) return e;
-    const int sms = device_sm_count();
-    int G = sort_blocks(capacity, kSortThreads * ITEMS);
-    if (G > per_sm * sms) G = per_sm * sms;
-    if (G < 1) return cudaErrorLaunchOutOfResources;
-    if ((e = cudaMemsetAsync(t.bar, 0, sizeof(uint32_t) * kSortBarrierWords, s)) != cudaSuccess) return e;
-    uint32_t *errp = err ? err : t.bar + 2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)G);
-    cfg.blockDim = dim3(kSortThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    note_launch();
-    return cudaLaunchKernelEx(&cfg, k_radix_coop<ITEMS>, keys, vals, keys_alt, vals_alt, d_count, capacity,
-                              begin_bit, end_bit, t.hist, t.totals, t.bar, errp, inv_out);
-}
-
-void radix_sort_pairs_multi(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                            const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                            cudaStream_t s, bool *result_in_alt, uint32_t *inv_out);
-
-static bool coop_sort_usable(cudaStream_t s, void *temp) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        cudaGetLastError();
-        return false;
-    }
-    const int known = g_coop_ok[dev].load();
-    if (known != 0) return known > 0;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
-        cudaGetLastError();
-        return false;  // probe later, outside capture
-    }
-    int attr = 0;
-    if (cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !attr) {
-        cudaGetLastError();
-        g_coop_ok[dev] = -1;
-        return false;
-    }
-    // probe: 3000 keys sorted both ways on a private stream, with private
-    // scratch, must agree bit for bit (25 key bits: 4 passes, both results
-    // in the primary buffers)
-    bool ok = false;
-    cudaStream_t ps = nullptr;
-    uint32_t *d = nullptr;
-    void *ptemp = nullptr;
-    constexpr uint32_t kN = 3000;
-    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) == cudaSuccess &&
-        cudaMalloc(&d, sizeof(uint32_t) * (8 * kN + 4)) == cudaSuccess &&
-        cudaMalloc(&ptemp, kSortTempBytes) == cudaSuccess) {
-        static uint32_t h[2 * kN], res[4 * kN];
-        for (uint32_t i = 0; i < kN; i++) {
-            h[i] = (i * 2654435761u) >> 7;
-            h[kN + i] = i;
-        }
-        uint32_t *k1 = d, *v1 = d + kN, *k2 = d + 2 * kN, *v2 = d + 3 * kN, *a1 = d + 4 * kN, *a2 = d + 5 * kN,
-                 *a3 = d + 6 * kN, *a4 = d + 7 * kN, *cnt = d + 8 * kN;
-        static uint32_t hcnt[4] = {kN, 0u, 0u, 0u};
-        uint32_t flag = 1;
-        bool alt = true;
-        if (cudaMemcpyAsync(k1, h, sizeof(uint32_t) * 2 * kN, cudaMemcpyHostToDevice, ps) == cudaSuccess &&
-            cudaMemcpyAsync(k2, h, sizeof(uint32_t) * 2 * kN, cudaMemcpyHostToDevice, ps) == cudaSuccess &&
-            cudaMemcpyAsync(cnt, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, ps) == cudaSuccess) {
-            radix_sort_pairs_multi(k1, v1, a1, a2, cnt, kN, 0, 25, ptemp, ps, &alt, nullptr);
-            if (launch_coop<kSmallItems>(k2, v2, a3, a4, cnt, kN, 0, 25, ptemp, ps, cnt + 1, nullptr) == cudaSuccess &&
-                cudaMemcpyAsync(res, k1, sizeof(uint32_t) * 2 * kN, cudaMemcpyDeviceToHost, ps) == cudaSuccess &&
-                cudaMemcpyAsync(res + 2 * kN, k2, sizeof(uint32_t) * 2 * kN, cudaMemcpyDeviceToHost, ps) == cudaSuccess &&
-                cudaMemcpyAsync(&flag, cnt + 1, sizeof(flag), cudaMemcpyDeviceToHost, ps) == cudaSuccess &&
-                cudaStreamSynchronize(ps) == cudaSuccess)
-                ok = !alt && flag == 0 && std::memcmp(res, res + 2 * kN, sizeof(uint32_t) * 2 * kN) == 0;
-        }
-    }
-    if (ptemp) cudaFree(ptemp);
-    cudaGetLastError();
-    if (d) cudaFree(d);
-    if (ps) cudaStreamDestroy(ps);
-    g_coop_ok[dev] = ok ? 1 : -1;
-    return ok;
-}
-
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out, uint32_t *err) {
-    if (err && coop_sort_usable(s, temp)) {
-        const int passes = (end_bit - begin_bit + 7) / 8;
-        const cudaError_t e =
-            capacity <= kSmallSort
-                ? launch_coop<kSmallItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp,
-                                           s, err, inv_out)
-                : launch_coop<kSortItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp,
-                                          s, err, inv_out);
-        if (e == cudaSuccess) {
-            *result_in_alt = (passes % 2) == 1;
-            return;
-        }
-        cudaGetLastError();
-    }
-    radix_sort_pairs_multi(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
-                           result_in_alt, inv_out);
-}
-
-void radix_sort_pairs_multi(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                            const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                            cudaStream_t s, bool *result_in_alt, uint32_t *inv_out) {
+                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out) {
     if (capacity <= kSmallSort)
         radix_passes<kSmallItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
                                   result_in_alt, inv_out);
