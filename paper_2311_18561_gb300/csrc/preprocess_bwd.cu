@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     constexpr int kChunk = 512, kPer = kChunk / 256;
     __shared__ float s_g[kSmall][kChunk];
     __shared__ uint16_t s_list[kChunk];
+    __shared__ uint32_t s_mpos[kChunk];  // depth positions of the compacted items
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_vis[kChunk / 32];  // visible items of the chunk (bits)
 
@@ -391,6 +392,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
         for (int q = 0; q < kPer; q++) {
             const int idx = tid * kPer + q;
             if (mv[q] != 0xffffffffu) {
+                s_mpos[pos] = mv[q];
                 s_list[pos++] = (uint16_t)idx;
                 atomicOr(&s_vis[idx >> 5], 1u << (idx & 31));
             } else if (base + idx < n) {
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
             const int idx = s_list[k];
             const uint32_t i = base + idx;
             SmallGrads q;
-            if (!item_adjoint<D>(P, V, i, P.inv[i], false, q)) {  // culled after all: zeros
+            if (!item_adjoint<D>(P, V, i, s_mpos[k], false, q)) {  // culled after all: zeros
                 q = SmallGrads{};
                 if (V.g_sh) {
                     float z[3 * K];
