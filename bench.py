@@ -926,7 +926,41 @@ def cpu_baseline(scene, cam, seconds):
     return {"value": n3 / t / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "sample": "%d random pixels of the 1920x1280 frame; FP64 oracle forward (culled) + backward on "
                       "those pixels, including its per-call preprocess and depth sort of all %d Gaussians "
-                      "(%.1f s)" % (n3, N_GAUSS, t)}
+                      "(%.1f s)" % (n3, N_GAUSS, t),
+            "other_configs": oracle_other_configs()}
+
+
+def oracle_other_configs():
+    """The rest of the oracle's timing plan, bounded to a few seconds: the
+    plain configuration (2,000 Gaussians, 160x120) rendered whole by brute
+    force (every Gaussian for every pixel), and the training configuration
+    (1M Gaussians, 1242x375) forward + backward on a pixel sample."""
+    import numpy as np
+
+    import oracle
+    from paper_2311_18561_gb300 import synth
+
+    out = {}
+    scene = synth.make_plain_scene(seed=0, n=2000)
+    cam = synth.plain_camera()
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, mode="brute")
+    t = time.perf_counter() - t0
+    out["plain_brute_force"] = {"mpix_s": 160 * 120 / t / 1e6, "seconds": t,
+                                "workload": "2,000 Gaussians, 160x120, every Gaussian at every pixel"}
+    n, w, h, f = WORKLOADS["training"][:4]
+    scene = synth.make_urban_scene(n, seed=0)
+    cam = synth.street_camera(FRAME / 49.0, w, h, fx=f)
+    rng = np.random.default_rng(3)
+    P = 2000
+    pix = np.stack([rng.integers(0, w, P), rng.integers(0, h, P)], axis=1).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle_sample_step(scene, cam, pix, np.ones((P, 3)) / P)
+    t = time.perf_counter() - t0
+    out["training_backward"] = {"mpix_s": P / t / 1e6, "seconds": t,
+                                "workload": "1M Gaussians, 1242x375: forward (culled) + backward on %d random "
+                                            "pixels, including the per-call preprocess of all Gaussians" % P}
+    return out
 
 
 def run_reference(args):
