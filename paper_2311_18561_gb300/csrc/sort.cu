@@ -579,16 +579,19 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
         k_radix_scan<<<kRadix, 1024, 0, s>>>(t.hist, t.totals, G);
         note_launch();
         uint32_t *inv_pass = b + nb >= end_bit ? inv_out : nullptr;  // the last pass only
-        switch (nb) {  // the digit widths of the depth sort (31 bits) and tile sorts of up to 2^16 tiles
-            case 3: k_radix_downsweep<ITEMS, 3><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                           t.hist, t.totals, inv_pass); break;
-            case 5: k_radix_downsweep<ITEMS, 5><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                           t.hist, t.totals, inv_pass); break;
-            case 7: k_radix_downsweep<ITEMS, 7><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                           t.hist, t.totals, inv_pass); break;
-            default: k_radix_downsweep<ITEMS, 8><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask,
-                                                                             t.hist, t.totals, inv_pass); break;
+        // one ballot per digit bit: the last pass of a sort by fewer than a
+        // multiple of 8 bits ranks with fewer ballots
+#define PVG_DOWNSWEEP(NBITS)                                                                                    \
+    case NBITS:                                                                                                 \
+        k_radix_downsweep<ITEMS, NBITS><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, \
+                                                                   t.hist, t.totals, inv_pass);                \
+        break;
+        switch (nb) {
+            PVG_DOWNSWEEP(1) PVG_DOWNSWEEP(2) PVG_DOWNSWEEP(3) PVG_DOWNSWEEP(4)
+            PVG_DOWNSWEEP(5) PVG_DOWNSWEEP(6) PVG_DOWNSWEEP(7)
+            default: PVG_DOWNSWEEP(8)
         }
+#undef PVG_DOWNSWEEP
         alt = !alt;
         b += nb;
     }

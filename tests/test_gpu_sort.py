@@ -38,6 +38,18 @@ def test_sort_small_and_ragged(renderer, n, bits):
     _check(renderer, keys, vals, *bits)
 
 
+@pytest.mark.parametrize("width", range(1, 9))
+def test_sort_every_last_digit_width(renderer, width):
+    """A sort by 8 + width bits: the last digit pass has width 1..8 bits
+    (each width ranks with its own number of ballots)."""
+    rng = np.random.default_rng(40 + width)
+    n = 300_001
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    keys[::5] = keys[3]
+    _check(renderer, keys, np.arange(n, dtype=np.uint32), 0, 8 + width)
+    _check(renderer, keys, np.arange(n, dtype=np.uint32), 5, 5 + width)
+
+
 def test_sort_depth_keys_of_a_frame(renderer):
     """Positive float32 depths (31 significant bits), 2M of them."""
     rng = np.random.default_rng(1)
