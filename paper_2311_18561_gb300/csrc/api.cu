@@ -222,9 +222,6 @@ struct pvg_ctx {
     uint32_t *h_pinned = nullptr;
     pvg_frame *own_frame = nullptr;
     StageTimer timer;
-    // work of the backward pass that runs beside the compositor adjoint
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // ------------------------------------------------------------------ misc
@@ -324,13 +321,6 @@ extern "C" pvg_status_t pvg_create(pvg_ctx_t **ctx, const pvg_config_t *cfg) {
         delete x;
         return PVG_ERR_OOM;
     }
-    if (cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x->join, cudaEventDisableTiming) != cudaSuccess) {
-        g_last_error = cudaGetErrorString(cudaGetLastError());
-        pvg_destroy(x);
-        return PVG_ERR_CUDA;
-    }
     *ctx = x;
     return PVG_OK;
 }
@@ -345,9 +335,6 @@ extern "C" void pvg_destroy(pvg_ctx_t *x) {
     if (x->h_pinned) cudaFreeHost(x->h_pinned);
     pvg_frame_destroy(x->own_frame);
     x->timer.destroy();
-    if (x->fork) cudaEventDestroy(x->fork);
-    if (x->join) cudaEventDestroy(x->join);
-    if (x->side) cudaStreamDestroy(x->side);
     delete x;
 }
 
@@ -892,16 +879,6 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     StageTimer &tm = x->timer;
     const bool timer_on = tm.on;
     if (capturing) tm.on = false;
-    // one view: the invisible Gaussians' SH-gradient rows (most of the
-    // per-item adjoint's writes) are zeroed on the side stream while the
-    // compositor adjoint runs
-    bool side_zero = false;
-    if (n_views == 1 && f->n_items > 0 && grads->sh && ((uintptr_t)grads->sh & 15u) == 0) {
-        PVG_CUDA(cudaEventRecord(x->fork, s));
-        PVG_CUDA(cudaStreamWaitEvent(x->side, x->fork, 0));
-        side_zero = launch_zero_invisible_sh(p, x->side);
-        PVG_CUDA(cudaEventRecord(x->join, x->side));
-    }
     tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
     note_launch();
     k_zero_rows<<<device_sm_count() * 4, 256, 0, s>>>(p.g2d, &p.counters[0], 10);
@@ -913,10 +890,6 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     }
     tm.end(PVG_STAGE_COMPOSITE_BWD, s);
     tm.begin(PVG_STAGE_PREPROCESS_BWD, s);
-    if (n_views == 1 && f->n_items > 0 && grads->sh && ((uintptr_t)grads->sh & 15u) == 0) {
-        PVG_CUDA(cudaStreamWaitEvent(s, x->join, 0));
-        p.sh_zeroed = side_zero ? 1 : 0;
-    }
     launch_preprocess_bwd(p, n_views > 1, s);
     if (feat_bwd) launch_feat_param_bwd(p, s);
     tm.end(PVG_STAGE_PREPROCESS_BWD, s);

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
             } else if (base + idx < n) {
 #pragma unroll
                 for (int f = 0; f < kSmall; f++) s_g[f][idx] = 0.f;
-                if (V.g_sh && !rows4 && !P.sh_zeroed) {
+                if (V.g_sh && !rows4) {
                     float z[3 * K];
 #pragma unroll
                     for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
@@ -459,36 +459,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     }
 }
 
-// One view: the SH-gradient rows of the Gaussians the view does not see,
-// zeroed as consecutive float4 (whole sectors), independent of the
-// compositor adjoint, so it can run beside it on another stream.
-template <int D>
-__global__ void __launch_bounds__(256) k_zero_invisible_sh(Params P) {
-    constexpr int R4 = 3 * (D + 1) * (D + 1) / 4;  // float4 per row
-    const ViewDesc &V = P.views[0];
-    float4 *sh4 = reinterpret_cast<float4 *>(V.g_sh);
-    const size_t total = (size_t)V.n * R4;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t i = (uint32_t)(e / R4);
-        if (P.inv[i] == 0xffffffffu) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
 }  // namespace
-
-bool launch_zero_invisible_sh(const Params &p, cudaStream_t s) {
-    if (p.n_views != 1 || p.n_items == 0) return false;
-    const int deg = p.sh_degree;
-    const int K = (deg + 1) * (deg + 1);
-    if ((3 * K) % 4 != 0) return false;  // degree 0 and 2: rows are not whole float4
-    // the gradient pointer is read on the device; the host copy of the view
-    // descriptor decides whether it is usable
-    note_launch();
-    const int grid = 8 * device_sm_count();
-    if (deg == 1) k_zero_invisible_sh<1><<<grid, 256, 0, s>>>(p);
-    else k_zero_invisible_sh<3><<<grid, 256, 0, s>>>(p);
-    return true;
-}
 
 void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s) {
     note_launch();

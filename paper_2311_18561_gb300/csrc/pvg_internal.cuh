@@ -112,7 +112,6 @@ struct Params {
     float *g2d;              // [M*10] image-space gradients by depth position (u, v, conic a b c,
                              // o~, colour with the forward's clamp applied, z)
     int32_t aux;             // backward: some view has depth / opacity-map gradients or a sky map
-    int32_t sh_zeroed;       // backward: the SH-gradient rows of the invisible items are already zero
     // extra channels
     int32_t feat_mask;       // kFeat* bits (0: none)
     int32_t n_feat;          // F
@@ -401,9 +400,6 @@ cudaError_t set_sh_constants_bwd();  // the adjoint's copy
 void launch_project_count(const Params &p, cudaStream_t s);
 void launch_finalize(const Params &p, cudaStream_t s);
 void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s);
-// one view: zeroes the SH-gradient rows of the Gaussians the view does not
-// see (as whole float4, when the rows allow it); false if it did not apply
-bool launch_zero_invisible_sh(const Params &p, cudaStream_t s);
 // sort / scan
 size_t sort_temp_bytes();  // kSortTempBytes
 void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);
