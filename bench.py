@@ -748,7 +748,7 @@ def _percentiles(lat_ms):
     return float(np.percentile(a, 50)), float(np.percentile(a, 99))
 
 
-def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_streams=2, seed=0):
+def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_streams=4, pipeline_depth=1, seed=0):
     """Poisson arrivals at `rate` req/s for `seconds` (random scene, pose on
     the street path +-2 m, t ~ U[0,1], resolution from {640x480, 1242x375,
     1920x1280}) served by the continuous-batching server, then the same
@@ -771,7 +771,7 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
         return pool[key].pop() if pool[key] else torch.empty(3, cam["height"], cam["width"], device=dev)
 
     srv = S.Server(max_batch_views=max_batch_views, n_streams=n_streams, memory_budget=24 << 30,
-                   tile=config[:2], pixels_per_thread=config[2])
+                   tile=config[:2], pixels_per_thread=config[2], pipeline_depth=pipeline_depth)
     ids = [srv.add_scene(sc) for sc in scenes]
     # warm-up: every scene at every resolution once (the server learns each
     # scene's pairs per pixel), then a burst of full batches
@@ -844,7 +844,7 @@ def serving_leg(dev, rate, seconds, config=(16, 16, 1), max_batch_views=16, n_st
     q50, q99 = _percentiles(lat1)
     one = {"p50_ms": q50, "p99_ms": q99, "mpix_s": pix / span1 / 1e6}
     return {"rate_req_s": rate, "seconds": seconds, "scenes": list(synth.SERVE_SCENE_SIZES),
-            "max_batch_views": max_batch_views, "streams": n_streams,
+            "max_batch_views": max_batch_views, "streams": n_streams, "pipeline_depth": pipeline_depth,
             "arena_per_worker": {k: arena[k] for k in ("items_per_batch", "pixels_per_batch", "pairs_per_batch")},
             "free_bytes_at_create": arena["free_bytes"], "served": served, "one_request_per_launch": one}
 

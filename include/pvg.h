@@ -320,13 +320,13 @@ typedef struct pvg_server pvg_server_t;
 
 typedef struct {
     int32_t max_batch_views;  /* views per launch sequence, 1..64 (default 16) */
-    int32_t n_streams;        /* workers, each with its own stream and arena, 1..16 (default 2) */
+    int32_t n_streams;        /* workers, each with its own stream and arena, 1..16 (default 4) */
     int64_t memory_budget;    /* bytes of the workers' arenas together (default 8 GiB), clamped to
                                * 90 % of the free device memory at creation */
     int32_t max_pending;      /* queued requests before submit returns PVG_ERR_BUSY (default 4096) */
     int32_t tile_w, tile_h, pixels_per_thread; /* compositing configuration (16, 16, 1) */
     int32_t gate_timeout_us;  /* bound of the gather kernel's wait for a slot (default 1,000,000) */
-    int32_t pipeline_depth;   /* batches a worker keeps in flight, 1..4 (default 2) */
+    int32_t pipeline_depth;   /* batches a worker keeps in flight, 1..4 (default 1) */
     int32_t pair_capacity;    /* pairs per batch; 0 (default) = the arena's share */
     int32_t reserved0;
 } pvg_serve_config_t;

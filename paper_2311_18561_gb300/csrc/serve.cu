@@ -509,14 +509,14 @@ extern "C" void pvg_serve_config_default(pvg_serve_config_t *c) {
     if (!c) return;
     std::memset(c, 0, sizeof(*c));
     c->max_batch_views = 16;
-    c->n_streams = 2;
+    c->n_streams = 4;
     c->memory_budget = (int64_t)8 << 30;
     c->max_pending = 4096;
     c->tile_w = 16;
     c->tile_h = 16;
     c->pixels_per_thread = 1;
     c->gate_timeout_us = 1000000;
-    c->pipeline_depth = 2;
+    c->pipeline_depth = 1;
     c->pair_capacity = 0;
 }
 

@@ -13,8 +13,8 @@ from .render import abi_scene
 
 
 class Server:
-    def __init__(self, max_batch_views=16, n_streams=2, memory_budget=8 << 30, max_pending=4096, tile=(16, 16),
-                 pixels_per_thread=1, gate_timeout_us=1_000_000, pipeline_depth=2, pair_capacity=0):
+    def __init__(self, max_batch_views=16, n_streams=4, memory_budget=8 << 30, max_pending=4096, tile=(16, 16),
+                 pixels_per_thread=1, gate_timeout_us=1_000_000, pipeline_depth=1, pair_capacity=0):
         self._lib = abi.lib()
         c = abi.ServeConfig()
         self._lib.pvg_serve_config_default(C.byref(c))
