@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
                 const float4 g = s0[k];
                 const float2 q = s1[k];
                 const float dx = __fsub_rn(fx, g.x);
+                const FalloffColumn fc = falloff_column(g.z, g.w, dx);
                 float w[kFPX];
                 bool any = false;
 #pragma unroll
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
                     w[p] = 0.f;
                     if (done & (1u << p)) continue;
                     const float dy = __fsub_rn(fy[p], g.y);
-                    const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
+                    const float e = falloff_exp2(fc, q.x, dy);
                     const float raw = __fmul_rn(q.y, ex2_approx(e));
                     if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
                     const float alpha = fminf(kAlphaCap, raw);

@@ -126,11 +126,12 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
                 const float4 g = s0[k];
                 const float2 q = s1[k];
                 const float dx = __fsub_rn(fx, g.x);
+                const FalloffColumn fc = falloff_column(g.z, g.w, dx);
 #pragma unroll
                 for (int p = 0; p < kFPX; p++) {
                     if (pos >= last[p]) continue;
                     const float dy = __fsub_rn(fy[p], g.y);
-                    const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
+                    const float e = falloff_exp2(fc, q.x, dy);
                     const float G = ex2_approx(e);
                     const float raw = __fmul_rn(q.y, G);
                     if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255

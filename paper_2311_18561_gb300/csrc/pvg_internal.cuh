@@ -323,19 +323,31 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 
 // Gaussian falloff exponent in base-2 units for the record's prescaled
 // conic (a', b', c') = -log2(e) (a/2, b, c/2): the pixel weight is
-// 2^(a' dx^2 + b' dx dy + c' dy^2).  Written with explicit roundings so
-// every kernel that calls it gets bit-identical results.
-__device__ __forceinline__ float falloff_exp2(float ap, float bp, float cp, float dx, float dy) {
-    const float t = __fmaf_rn(bp, dy, __fmul_rn(ap, dx));
-    return __fmaf_rn(__fmul_rn(cp, dy), dy, __fmul_rn(dx, t));
+// 2^(a' dx^2 + b' dx dy + c' dy^2) = 2^(A + dy (B + c' dy)) with the
+// column terms A = a' dx^2 and B = b' dx computed once per entry and pixel
+// column (a thread's pixels share dx), leaving two fused multiply-adds per
+// pixel.  Written with explicit roundings so every kernel that evaluates
+// it gets bit-identical results.
+struct FalloffColumn {
+    float A, B;
+};
+
+__device__ __forceinline__ FalloffColumn falloff_column(float ap, float bp, float dx) {
+    FalloffColumn c;
+    c.A = __fmul_rn(__fmul_rn(ap, dx), dx);
+    c.B = __fmul_rn(bp, dx);
+    return c;
 }
 
-// falloff_exp2 for two pixels of one column (same dx, rows dy.x, dy.y),
-// operands given as pairs: adx = (a' dx, a' dx), bp = (b', b'),
-// cp = (c', c'), dx2 = (dx, dx); the same roundings in each half
-__device__ __forceinline__ float2 falloff_exp2_x2(float2 adx, float2 bp, float2 cp, float2 dx2, float2 dy) {
-    const float2 t = fma2(bp, dy, adx);
-    return fma2(mul2(cp, dy), dy, mul2(dx2, t));
+__device__ __forceinline__ float falloff_exp2(const FalloffColumn &c, float cp, float dy) {
+    return __fmaf_rn(__fmaf_rn(cp, dy, c.B), dy, c.A);
+}
+
+// falloff_exp2 for two pixels of one column (rows dy.x, dy.y), operands as
+// pairs: A2 = (A, A), B2 = (B, B), cp2 = (c', c'); the same roundings in
+// each half
+__device__ __forceinline__ float2 falloff_exp2_x2(float2 A2, float2 B2, float2 cp2, float2 dy) {
+    return fma2(fma2(cp2, dy, B2), dy, A2);
 }
 
 // Sky background (Sec. 3.4, C_f = C + (1 - O) f_sky(d)): the four texels

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
             const float4 col = s2[k];
             const uint32_t pos = base + k + 1 - r.x;  // list position after this entry
             const float dx = __fsub_rn(fx, g.x);
+            const FalloffColumn fc = falloff_column(g.z, g.w, dx);
 #pragma unroll
             for (int p = 0; p < PX; p++) {
                 if (done & (1u << p)) continue;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
                     const float2 h = s_half[k];
                     if (fabsf(dx) <= h.x && fabsf(dy) <= h.y) neval[p]++;
                 }
-                const float e = falloff_exp2(g.z, g.w, q.x, dx, dy);
+                const float e = falloff_exp2(fc, q.x, dy);
                 const float raw = __fmul_rn(q.y, ex2_approx(e));
                 if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
                 const float alpha = fminf(kAlphaCap, raw);
@@ -221,15 +222,15 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
             const float2 E = sE[k];
             const uint32_t pos = base + k + 1 - r.x;  // list position after this entry
             const float dx = __fsub_rn(fx, A.x);
-            const float adx = __fmul_rn(A.y, dx);
-            const float2 dx2 = make_float2(dx, dx), adx2 = make_float2(adx, adx);
-            const float2 v2 = make_float2(A.z, A.w), bp2 = make_float2(B.x, B.y), cp2 = make_float2(B.z, B.w);
+            const FalloffColumn fc = falloff_column(A.y, B.x, dx);
+            const float2 A2 = make_float2(fc.A, fc.A), B2 = make_float2(fc.B, fc.B);
+            const float2 v2 = make_float2(A.z, A.w), cp2 = make_float2(B.z, B.w);
             const float2 o2 = make_float2(Cq.x, Cq.y), r2 = make_float2(Cq.z, Cq.w);
             const float2 g2 = make_float2(Dq.x, Dq.y), b2 = make_float2(Dq.z, Dq.w);
 #pragma unroll
             for (int q = 0; q < NP; q++) {
                 const float2 dy = sub2(fy[q], v2);
-                const float2 e = falloff_exp2_x2(adx2, bp2, cp2, dx2, dy);
+                const float2 e = falloff_exp2_x2(A2, B2, cp2, dy);
                 const float2 a = mul2(o2, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
                 // min(cap, a) >= 1/255 iff a >= 1/255 (cap > 1/255): the cap
                 // is applied to blending pixels only
