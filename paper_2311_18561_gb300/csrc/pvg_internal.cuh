@@ -148,10 +148,18 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // with the conic pre-scaled, (a', b', c') = -log2(e) (a/2, b, c/2).  Every
 // kernel that blends takes its alpha from these terms, so the blending
 // weights agree bit for bit across kernels.
+// The row coefficient c' is kept at most -kMinRowCoef: a pixel moved to
+// the far row (kFarRow, packed compositor) then always gets an exponent of
+// -inf (alpha 0, never blends again), whatever its column; the bound only
+// touches conics with c < 1.4e-20 px^-2 (a footprint over 1e10 pixels
+// tall), and a NaN coefficient stays NaN.
+constexpr float kMinRowCoef = 1e-20f;
+
 __device__ __forceinline__ void record_terms(const float4 *rec, uint32_t m, float4 &s0, float2 &s1, float4 &s2) {
     const float4 a = rec[3 * (size_t)m], b = rec[3 * (size_t)m + 1], c = rec[3 * (size_t)m + 2];
     s0 = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-    s1 = make_float2(-0.5f * kLog2e * b.x, b.y);
+    const float cp = -0.5f * kLog2e * b.x;
+    s1 = make_float2(cp > -kMinRowCoef ? -kMinRowCoef : cp, b.y);
     s2 = make_float4(c.x, c.y, c.z, b.z);
 }
 

@@ -234,13 +234,8 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
                 const float2 a = mul2(o2, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
                 // min(cap, a) >= 1/255 iff a >= 1/255 (cap > 1/255): the cap
                 // is applied to blending pixels only
+                // a done pixel (far row, c' <= -kMinRowCoef) has alpha 0
                 bool bx = a.x >= kAlphaMin, by = a.y >= kAlphaMin;
-                if (!(bx || by)) continue;
-                // a done pixel passes only for a degenerate conic (c = 0,
-                // falloff independent of the row): the done bits decide
-                const uint32_t bits = (done >> (2 * q)) & 3u;
-                bx = bx && !(bits & 1u);
-                by = by && !(bits & 2u);
                 if (!(bx || by)) continue;
                 const float ax = fminf(kAlphaCap, a.x), ay = fminf(kAlphaCap, a.y);
                 const float2 al = make_float2(ax, ay);
