@@ -77,12 +77,13 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
                     const float raw = __fmul_rn(q.y, ex2_approx(e));
                     if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
                     const float alpha = fminf(kAlphaCap, raw);
-                    const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
+                    const float wv = __fmul_rn(alpha, T[p]);
+                    const float Tn = __fsub_rn(T[p], wv);
                     if (Tn < kTStop) {
                         done |= 1u << p;
                         continue;
                     }
-                    w[p] = __fmul_rn(alpha, T[p]);
+                    w[p] = wv;
                     T[p] = Tn;
                     any = true;
                 }

@@ -123,12 +123,12 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
                 if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
                 const float alpha = fminf(kAlphaCap, raw);
                 if constexpr (kStats) nblend[p]++;
-                const float Tn = __fmul_rn(T[p], __fsub_rn(1.0f, alpha));
+                const float w = __fmul_rn(alpha, T[p]);
+                const float Tn = __fsub_rn(T[p], w);
                 if (Tn < kTStop) {
                     done |= 1u << p;
                     continue;
                 }
-                const float w = __fmul_rn(alpha, T[p]);
                 C0[p] = __fmaf_rn(col.x, w, C0[p]);
                 C1[p] = __fmaf_rn(col.y, w, C1[p]);
                 C2[p] = __fmaf_rn(col.z, w, C2[p]);
@@ -239,7 +239,8 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
                 if (!(bx || by)) continue;
                 const float ax = fminf(kAlphaCap, a.x), ay = fminf(kAlphaCap, a.y);
                 const float2 al = make_float2(ax, ay);
-                const float2 Tn = mul2(T[q], sub2(one2, al));
+                const float2 wu = mul2(al, T[q]);
+                const float2 Tn = sub2(T[q], wu);
                 const bool sx = bx && Tn.x < kTStop, sy = by && Tn.y < kTStop;
                 if (sx || sy) {
                     done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
@@ -248,16 +249,15 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
                 }
                 bx = bx && !sx;
                 by = by && !sy;
-                // a pixel that does not blend takes alpha 0: w = +0 and T * (1 - 0) = T,
-                // bit for bit; a blending one gets the scalar kernel's w and T'
-                const float2 am = make_float2(bx ? ax : 0.f, by ? ay : 0.f);
-                const float2 w = mul2(am, T[q]);
+                // a pixel that does not blend takes w = +0 and T - 0 = T, bit
+                // for bit; a blending one gets the scalar kernel's w and T'
+                const float2 w = make_float2(bx ? wu.x : 0.f, by ? wu.y : 0.f);
                 C0[q] = fma2(r2, w, C0[q]);
                 C1[q] = fma2(g2, w, C1[q]);
                 C2[q] = fma2(b2, w, C2[q]);
                 D[q] = fma2(E, w, D[q]);
                 O[q] = add2(O[q], w);
-                T[q] = mul2(T[q], sub2(one2, am));
+                T[q] = sub2(T[q], w);
                 last[2 * q] = bx ? pos : last[2 * q];
                 last[2 * q + 1] = by ? pos : last[2 * q + 1];
             }
