@@ -28,6 +28,10 @@ namespace pvg {
 
 constexpr float kAlphaMin = 1.0f / 255.0f;  // skip gate
 constexpr float kAlphaCap = 0.99f;          // alpha cap
+// an entry whose o~ is at most this never reaches the cap: its alpha
+// o~ 2^e (e <= 0 up to one rounding) stays below kAlphaCap, so the
+// compositors take min(cap, .) only for the rare entries above it
+constexpr float kUncappedOpacity = 0.9899f;
 constexpr float kTStop = 1e-4f;             // transmittance stop
 constexpr float kFarRow = 1e30f;            // row coordinate of a pixel that is done (packed compositor)
 constexpr float kLog2e = 1.4426950408889634f;  // log2(e): e^x = 2^(x log2 e)

@@ -16,6 +16,8 @@
 // pixels per thread share each shared-memory load and the loop overhead.
 // Every pixel's arithmetic is the same expression whatever TW, TH and PX,
 // so images are bit-identical across tile shapes.
+#include <type_traits>
+
 #include "raster_common.cuh"
 
 namespace pvg {
@@ -110,33 +112,39 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
             const uint32_t pos = base + k + 1 - r.x;  // list position after this entry
             const float dx = __fsub_rn(fx, g.x);
             const FalloffColumn fc = falloff_column(g.z, g.w, dx);
+            // entries whose o~ cannot reach the cap skip min(cap, .)
+            auto pixels = [&](auto capped) {
+                constexpr bool kCap = decltype(capped)::value;
 #pragma unroll
-            for (int p = 0; p < PX; p++) {
-                if (done & (1u << p)) continue;
-                const float dy = __fsub_rn(fy[p], g.y);
-                if constexpr (kStats) {
-                    const float2 h = s_half[k];
-                    if (fabsf(dx) <= h.x && fabsf(dy) <= h.y) neval[p]++;
+                for (int p = 0; p < PX; p++) {
+                    if (done & (1u << p)) continue;
+                    const float dy = __fsub_rn(fy[p], g.y);
+                    if constexpr (kStats) {
+                        const float2 h = s_half[k];
+                        if (fabsf(dx) <= h.x && fabsf(dy) <= h.y) neval[p]++;
+                    }
+                    const float e = falloff_exp2(fc, q.x, dy);
+                    const float raw = __fmul_rn(q.y, ex2_approx(e));
+                    if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
+                    const float alpha = kCap ? fminf(kAlphaCap, raw) : raw;
+                    if constexpr (kStats) nblend[p]++;
+                    const float w = __fmul_rn(alpha, T[p]);
+                    const float Tn = __fsub_rn(T[p], w);
+                    if (Tn < kTStop) {
+                        done |= 1u << p;
+                        continue;
+                    }
+                    C0[p] = __fmaf_rn(col.x, w, C0[p]);
+                    C1[p] = __fmaf_rn(col.y, w, C1[p]);
+                    C2[p] = __fmaf_rn(col.z, w, C2[p]);
+                    D[p] = __fmaf_rn(col.w, w, D[p]);
+                    O[p] = __fadd_rn(O[p], w);
+                    T[p] = Tn;
+                    last[p] = pos;
                 }
-                const float e = falloff_exp2(fc, q.x, dy);
-                const float raw = __fmul_rn(q.y, ex2_approx(e));
-                if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
-                const float alpha = fminf(kAlphaCap, raw);
-                if constexpr (kStats) nblend[p]++;
-                const float w = __fmul_rn(alpha, T[p]);
-                const float Tn = __fsub_rn(T[p], w);
-                if (Tn < kTStop) {
-                    done |= 1u << p;
-                    continue;
-                }
-                C0[p] = __fmaf_rn(col.x, w, C0[p]);
-                C1[p] = __fmaf_rn(col.y, w, C1[p]);
-                C2[p] = __fmaf_rn(col.z, w, C2[p]);
-                D[p] = __fmaf_rn(col.w, w, D[p]);
-                O[p] = __fadd_rn(O[p], w);
-                T[p] = Tn;
-                last[p] = pos;
-            }
+            };
+            if (q.y > kUncappedOpacity) pixels(std::true_type{});
+            else pixels(std::false_type{});
         }
     }
     if constexpr (kStats) {
@@ -227,40 +235,46 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
             const float2 v2 = make_float2(A.z, A.w), cp2 = make_float2(B.z, B.w);
             const float2 o2 = make_float2(Cq.x, Cq.y), r2 = make_float2(Cq.z, Cq.w);
             const float2 g2 = make_float2(Dq.x, Dq.y), b2 = make_float2(Dq.z, Dq.w);
+            // entries whose o~ cannot reach the cap skip min(cap, .)
+            auto pairs = [&](auto capped) {
+                constexpr bool kCap = decltype(capped)::value;
 #pragma unroll
-            for (int q = 0; q < NP; q++) {
-                const float2 dy = sub2(fy[q], v2);
-                const float2 e = falloff_exp2_x2(A2, B2, cp2, dy);
-                const float2 a = mul2(o2, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
-                // min(cap, a) >= 1/255 iff a >= 1/255 (cap > 1/255): the cap
-                // is applied to blending pixels only
-                // a done pixel (far row, c' <= -kMinRowCoef) has alpha 0
-                bool bx = a.x >= kAlphaMin, by = a.y >= kAlphaMin;
-                if (!(bx || by)) continue;
-                const float ax = fminf(kAlphaCap, a.x), ay = fminf(kAlphaCap, a.y);
-                const float2 al = make_float2(ax, ay);
-                const float2 wu = mul2(al, T[q]);
-                const float2 Tn = sub2(T[q], wu);
-                const bool sx = bx && Tn.x < kTStop, sy = by && Tn.y < kTStop;
-                if (sx || sy) {
-                    done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
-                    if (sx) fy[q].x = kFarRow;
-                    if (sy) fy[q].y = kFarRow;
+                for (int q = 0; q < NP; q++) {
+                    const float2 dy = sub2(fy[q], v2);
+                    const float2 e = falloff_exp2_x2(A2, B2, cp2, dy);
+                    const float2 a = mul2(o2, make_float2(ex2_approx(e.x), ex2_approx(e.y)));
+                    // min(cap, a) >= 1/255 iff a >= 1/255 (cap > 1/255): the cap
+                    // is applied to blending pixels only
+                    // a done pixel (far row, c' <= -kMinRowCoef) has alpha 0
+                    bool bx = a.x >= kAlphaMin, by = a.y >= kAlphaMin;
+                    if (!(bx || by)) continue;
+                    const float ax = kCap ? fminf(kAlphaCap, a.x) : a.x, ay = kCap ? fminf(kAlphaCap, a.y) : a.y;
+                    const float2 al = make_float2(ax, ay);
+                    const float2 wu = mul2(al, T[q]);
+                    const float2 Tn = sub2(T[q], wu);
+                    const bool sx = bx && Tn.x < kTStop, sy = by && Tn.y < kTStop;
+                    if (sx || sy) {
+                        done |= ((sx ? 1u : 0u) | (sy ? 2u : 0u)) << (2 * q);
+                        if (sx) fy[q].x = kFarRow;
+                        if (sy) fy[q].y = kFarRow;
+                    }
+                    bx = bx && !sx;
+                    by = by && !sy;
+                    // a pixel that does not blend takes w = +0 and T - 0 = T, bit
+                    // for bit; a blending one gets the scalar kernel's w and T'
+                    const float2 w = make_float2(bx ? wu.x : 0.f, by ? wu.y : 0.f);
+                    C0[q] = fma2(r2, w, C0[q]);
+                    C1[q] = fma2(g2, w, C1[q]);
+                    C2[q] = fma2(b2, w, C2[q]);
+                    D[q] = fma2(E, w, D[q]);
+                    O[q] = add2(O[q], w);
+                    T[q] = sub2(T[q], w);
+                    last[2 * q] = bx ? pos : last[2 * q];
+                    last[2 * q + 1] = by ? pos : last[2 * q + 1];
                 }
-                bx = bx && !sx;
-                by = by && !sy;
-                // a pixel that does not blend takes w = +0 and T - 0 = T, bit
-                // for bit; a blending one gets the scalar kernel's w and T'
-                const float2 w = make_float2(bx ? wu.x : 0.f, by ? wu.y : 0.f);
-                C0[q] = fma2(r2, w, C0[q]);
-                C1[q] = fma2(g2, w, C1[q]);
-                C2[q] = fma2(b2, w, C2[q]);
-                D[q] = fma2(E, w, D[q]);
-                O[q] = add2(O[q], w);
-                T[q] = sub2(T[q], w);
-                last[2 * q] = bx ? pos : last[2 * q];
-                last[2 * q + 1] = by ? pos : last[2 * q + 1];
-            }
+            };
+            if (Cq.x > kUncappedOpacity) pairs(std::true_type{});
+            else pairs(std::false_type{});
         }
     }
     float Ts[PX], C0s[PX], C1s[PX], C2s[PX], Ds[PX], Os[PX];

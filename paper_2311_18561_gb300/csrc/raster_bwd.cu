@@ -16,6 +16,8 @@
 // atomic per (Gaussian, tile, term).  Alpha is the forward's expression
 // (explicit roundings), so the blend decisions are the forward's; the rest
 // of this file may contract a*b+c into fused multiply-adds.
+#include <type_traits>
+
 #include "raster_common.cuh"
 
 namespace pvg {
@@ -204,39 +206,45 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
                 const float4 col = s2[k];
                 const float dx = __fsub_rn(fx, g.x);
                 const FalloffColumn fc = falloff_column(g.z, g.w, dx);
+                // entries whose o~ cannot reach the cap skip min(cap, .)
+                auto pixels = [&](auto capped) {
+                    constexpr bool kCap = decltype(capped)::value;
 #pragma unroll
-                for (int p = 0; p < PX; p++) {
-                    if (pos >= last[p]) continue;
-                    const float dy = __fsub_rn(fy[p], g.y);
-                    const float e = falloff_exp2(fc, q.x, dy);
-                    const float G = ex2_approx(e);
-                    const float raw = __fmul_rn(q.y, G);
-                    if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
-                    const float alpha = fminf(kAlphaCap, raw);
-                    contrib = true;
-                    const float inv = rcp_approx(1.0f - alpha);
-                    const float Ti = T[p] * inv;
-                    const float w = alpha * Ti;
-                    float X = gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z;
-                    if constexpr (kAux) X += gD[p] * col.w + gO[p];
-                    const float ga = Ti * X - inv * S[p];
-                    gv[6] += gC0[p] * w;
-                    gv[7] += gC1[p] * w;
-                    gv[8] += gC2[p] * w;
-                    if constexpr (kAux) gv[9] += gD[p] * w;
-                    if (raw <= kAlphaCap) {
-                        // moments of gpow = dL/dpower (d alpha / d power = alpha);
-                        // the conic is applied once per Gaussian in the flush
-                        gv[5] += ga * G;
-                        const float gpow = ga * alpha;
-                        const float my = gpow * dy;
-                        A0 += gpow;
-                        gv[1] += my;
-                        gv[4] += my * dy;
+                    for (int p = 0; p < PX; p++) {
+                        if (pos >= last[p]) continue;
+                        const float dy = __fsub_rn(fy[p], g.y);
+                        const float e = falloff_exp2(fc, q.x, dy);
+                        const float G = ex2_approx(e);
+                        const float raw = __fmul_rn(q.y, G);
+                        if (!(raw >= kAlphaMin)) continue;  // = min(cap, raw) < 1/255, cap > 1/255
+                        const float alpha = kCap ? fminf(kAlphaCap, raw) : raw;
+                        contrib = true;
+                        const float inv = rcp_approx(1.0f - alpha);
+                        const float Ti = T[p] * inv;
+                        const float w = alpha * Ti;
+                        float X = gC0[p] * col.x + gC1[p] * col.y + gC2[p] * col.z;
+                        if constexpr (kAux) X += gD[p] * col.w + gO[p];
+                        const float ga = Ti * X - inv * S[p];
+                        gv[6] += gC0[p] * w;
+                        gv[7] += gC1[p] * w;
+                        gv[8] += gC2[p] * w;
+                        if constexpr (kAux) gv[9] += gD[p] * w;
+                        if (!kCap || raw <= kAlphaCap) {
+                            // moments of gpow = dL/dpower (d alpha / d power = alpha);
+                            // the conic is applied once per Gaussian in the flush
+                            gv[5] += ga * G;
+                            const float gpow = ga * alpha;
+                            const float my = gpow * dy;
+                            A0 += gpow;
+                            gv[1] += my;
+                            gv[4] += my * dy;
+                        }
+                        S[p] += X * w;
+                        T[p] = Ti;
                     }
-                    S[p] += X * w;
-                    T[p] = Ti;
-                }
+                };
+                if (q.y > kUncappedOpacity) pixels(std::true_type{});
+                else pixels(std::false_type{});
                 if (contrib) {
                     gv[0] = dx * A0;
                     gv[2] = dx * gv[0];
