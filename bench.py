@@ -60,14 +60,16 @@ def workload_camera(frame):
 
 
 SM_MAX_MHZ = 2070.0  # nominal maximum SM clock (MEASURED_PEAKS.json's sm_max_mhz when present)
-# Algorithmic FP32 FMA-pipe lane-instructions of the compositor:
-# every in-footprint evaluation: 2 FADD (dx, dy), 4 FMUL + 2 FFMA (falloff
-# exponent, o~ G) = 8; every blended evaluation in addition, forward:
-# 1 - alpha, T (1 - alpha), alpha T, 4 FFMA (r g b z), O += w = 8;
-# backward: 1 - alpha, T / (1 - alpha), alpha T_i, dL/dalpha (13), 4 FFMA
-# (r g b z terms), o~ term, 5 moments (8), 5 suffix sums = 35.
+# Algorithmic FP32 lane-instructions of the compositor:
+# every in-footprint evaluation: dy, the falloff exponent as two FFMA
+# around the terms of the entry's pixel column (a' dx^2 and b' dx, shared
+# by the column's pixels), o~ G, the 1/255 test, min(0.99, .) = 6;
+# every blended evaluation in addition, forward: alpha T, T - alpha T, the
+# stop test, 4 FFMA (r g b depth), O += w = 8; backward: 1 - alpha,
+# T_i, w, X (4), dL/dalpha (2), colour and depth terms (4), opacity term,
+# dL/dpower, 2 moments' bases, 5 moments, suffix sum = 23.
 OPS_PER_LOSS_PIXEL = 207
-OPS_PER_EVAL = 8
+OPS_PER_EVAL = 6
 OPS_PER_BLEND = {"composite": 8, "composite_bwd": 23}
 
 
@@ -306,7 +308,7 @@ def capture_graph(fn, dev):
 
 
 def alu_roof(stage, stage_ms, E, B, fp32, traffic=None):
-    """ALU roofline of a compositing stage: E in-footprint evaluations x 8
+    """ALU roofline of a compositing stage: E in-footprint evaluations x 6
     + B blends x the stage's per-blend FP32 instructions, per launch, over
     the measured lane-FMA rate of the FMA probe."""
     ops = E * OPS_PER_EVAL + B * OPS_PER_BLEND[stage]

@@ -256,36 +256,6 @@ __device__ __forceinline__ bool item_adjoint(const Params &P, const ViewDesc &V,
     return true;
 }
 
-// exclusive scan over the block (blockDim.x = 256) of one value per
-// thread; *total gets the sum.  smem: 33 words.
-__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *smem, uint32_t *total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) smem[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < nw ? smem[lane] : 0u;
-        uint32_t wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < nw) smem[lane] = wi - w;
-        if (lane == 31) smem[32] = wi;
-    }
-    __syncthreads();
-    const uint32_t r = smem[warp] + x - v;
-    *total = smem[32];
-    __syncthreads();
-    return r;
-}
-
 // Several views of one scene: one thread per Gaussian walks the views
 // that see it (found 64 at a time from the inverse map, coalesced across
 // the warp), accumulates the item adjoints over those views -- the 17 small
@@ -349,77 +319,74 @@ __global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P
     }
 }
 
-// One view: every gradient entry is written once.  A block takes chunks
-// of kChunk consecutive items; their visible items are compacted onto the
-// block's threads (so every lane of the heavy path has an item), the 19
-// small gradients of the chunk are staged in shared memory (zeros for the
-// invisible items) and written out coalesced, field by field, so that each
-// 32-byte sector is written whole by one instruction.  SH-coefficient rows
-// (192 bytes at degree 3) are written by the item's thread, zeros for the
+// One view: every gradient entry is written once, with no block barrier.
+// A warp takes chunks of kWarpChunk consecutive items (every gridDim.x *
+// 8-th chunk): their visibility by ballot, the visible items compacted onto
+// its lanes, the 17 small gradients of the chunk staged in the warp's
+// shared memory (zeros for the invisible items) and written out coalesced,
+// field by field, so that each 32-byte sector is written whole by one
+// instruction.  SH-coefficient rows (192 bytes at degree 3) are written by
+// the visible item's lane, and zeroed warp-wide as float4 for the
 // invisible items.
+constexpr int kWarpChunk = 64;
+constexpr int kWarpPer = kWarpChunk / 32;
+
 template <int D>
 __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     constexpr int K = (D + 1) * (D + 1);
-    constexpr int kChunk = 512, kPer = kChunk / 256;
-    __shared__ float s_g[kSmall][kChunk];
-    __shared__ uint16_t s_list[kChunk];
-    __shared__ uint32_t s_mpos[kChunk];  // depth positions of the compacted items
-    __shared__ uint32_t s_scan[33];
-    __shared__ uint32_t s_vis[kChunk / 32];  // visible items of the chunk (bits)
-
+    __shared__ float s_gw[8][kSmall][kWarpChunk];
+    __shared__ uint32_t s_mw[8][kWarpChunk];  // depth positions of the compacted items
+    __shared__ uint8_t s_lw[8][kWarpChunk];   // their places in the chunk
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float(*s_g)[kWarpChunk] = s_gw[warp];
+    uint32_t *s_mpos = s_mw[warp];
+    uint8_t *s_list = s_lw[warp];
     const ViewDesc &V = P.views[0];  // one view: item g is Gaussian g (item_base 0)
-    // SH rows of invisible items are zeroed by the whole block as
-    // consecutive float4 (whole sectors per instruction) when the rows are
-    // whole float4 and aligned; else by each item's thread
     constexpr bool kRows4 = (3 * K) % 4 == 0;
     const bool rows4 = kRows4 && V.g_sh && aligned16(V.g_sh);
     const uint32_t n = P.n_items;
-    const int tid = threadIdx.x;
-    for (uint32_t base = blockIdx.x * kChunk; base < n; base += gridDim.x * kChunk) {
-        // visibility of the chunk's items (kPer consecutive ones per thread)
-        uint32_t mv[kPer];
-        uint32_t cnt = 0;
+    const uint32_t lmask = (1u << lane) - 1u;
+    const uint32_t n_chunks = (n + kWarpChunk - 1) / kWarpChunk;
+    for (uint32_t c = blockIdx.x * 8u + warp; c < n_chunks; c += gridDim.x * 8u) {
+        const uint32_t base = c * kWarpChunk;
+        uint32_t vis[kWarpPer];
+        uint32_t nvis = 0;
 #pragma unroll
-        for (int q = 0; q < kPer; q++) {
-            const uint32_t g = base + tid * kPer + q;
-            mv[q] = g < n ? P.inv[g] : 0xffffffffu;
-            cnt += mv[q] != 0xffffffffu ? 1u : 0u;
-        }
-        if (tid < kChunk / 32) s_vis[tid] = 0u;
-        uint32_t nvis;
-        uint32_t pos = block_excl_scan_u32(cnt, s_scan, &nvis);  // (its barriers order s_vis)
+        for (int q = 0; q < kWarpPer; q++) {
+            const uint32_t g = base + 32 * q + lane;
+            const uint32_t m = g < n ? P.inv[g] : 0xffffffffu;
+            const bool v = m != 0xffffffffu;
+            vis[q] = __ballot_sync(0xffffffffu, v);
+            if (v) {
+                const uint32_t r = nvis + __popc(vis[q] & lmask);
+                s_mpos[r] = m;
+                s_list[r] = (uint8_t)(32 * q + lane);
+            } else {
 #pragma unroll
-        for (int q = 0; q < kPer; q++) {
-            const int idx = tid * kPer + q;
-            if (mv[q] != 0xffffffffu) {
-                s_mpos[pos] = mv[q];
-                s_list[pos++] = (uint16_t)idx;
-                atomicOr(&s_vis[idx >> 5], 1u << (idx & 31));
-            } else if (base + idx < n) {
-#pragma unroll
-                for (int f = 0; f < kSmall; f++) s_g[f][idx] = 0.f;
-                if (V.g_sh && !rows4) {
+                for (int f = 0; f < kSmall; f++) s_g[f][32 * q + lane] = 0.f;
+                if (g < n && V.g_sh && !rows4) {
                     float z[3 * K];
 #pragma unroll
                     for (int k = 0; k < 3 * K; k++) z[k] = 0.f;
-                    store_floats<3 * K>(V.g_sh + (size_t)(base + idx) * 3 * K, z, aligned16(V.g_sh));
+                    store_floats<3 * K>(V.g_sh + (size_t)g * 3 * K, z, aligned16(V.g_sh));
                 }
             }
+            nvis += __popc(vis[q]);
         }
-        __syncthreads();
         if constexpr (kRows4) {
-            if (rows4) {  // zero SH rows of the invisible items, block-wide
+            if (rows4) {  // SH rows of the invisible items, warp-wide
                 constexpr int R4 = 3 * K / 4;
                 float4 *sh4 = reinterpret_cast<float4 *>(V.g_sh + (size_t)base * 3 * K);
-                const uint32_t cn4 = min((uint32_t)kChunk, n - base) * R4;
-                for (uint32_t e = tid; e < cn4; e += 256) {
+                const uint32_t cn4 = min((uint32_t)kWarpChunk, n - base) * R4;
+                for (uint32_t e = lane; e < cn4; e += 32) {
                     const uint32_t item = e / R4;
-                    if (!((s_vis[item >> 5] >> (item & 31)) & 1u)) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!((vis[item >> 5] >> (item & 31)) & 1u)) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
         }
+        __syncwarp();
         // the visible items, compacted
-        for (uint32_t k = tid; k < nvis; k += 256) {
+        for (uint32_t k = lane; k < nvis; k += 32) {
             const int idx = s_list[k];
             const uint32_t i = base + idx;
             SmallGrads q;
@@ -428,7 +395,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
                 if (V.g_sh) {
                     float z[3 * K];
 #pragma unroll
-                    for (int c = 0; c < 3 * K; c++) z[c] = 0.f;
+                    for (int cc = 0; cc < 3 * K; cc++) z[cc] = 0.f;
                     store_floats<3 * K>(V.g_sh + (size_t)i * 3 * K, z, aligned16(V.g_sh));
                 }
             }
@@ -438,24 +405,24 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
 #pragma unroll
             for (int f = 0; f < kSmall; f++) s_g[f][idx] = v[f];
         }
-        __syncthreads();
+        __syncwarp();
         // coalesced write-out of the chunk's small gradients
-        const uint32_t cn = min((uint32_t)kChunk, n - base);
+        const uint32_t cn = min((uint32_t)kWarpChunk, n - base);
         auto out3 = [&](float *dst, int f0) {
             if (!dst) return;
-            for (uint32_t e = tid; e < 3 * cn; e += 256) dst[3 * (size_t)base + e] = s_g[f0 + e % 3][e / 3];
+            for (uint32_t e = lane; e < 3 * cn; e += 32) dst[3 * (size_t)base + e] = s_g[f0 + e % 3][e / 3];
         };
         out3(V.g_mu, 0);
         out3(V.g_vel, 3);
         out3(V.g_scale, 6);
         if (V.g_quat)
-            for (uint32_t e = tid; e < 4 * cn; e += 256) V.g_quat[4 * (size_t)base + e] = s_g[9 + (e & 3)][e >> 2];
+            for (uint32_t e = lane; e < 4 * cn; e += 32) V.g_quat[4 * (size_t)base + e] = s_g[9 + (e & 3)][e >> 2];
         float *const one[4] = {V.g_tau, V.g_beta, V.g_period, V.g_opac};
 #pragma unroll
         for (int f = 0; f < 4; f++)
             if (one[f])
-                for (uint32_t e = tid; e < cn; e += 256) one[f][base + e] = s_g[13 + f][e];
-        __syncthreads();
+                for (uint32_t e = lane; e < cn; e += 32) one[f][base + e] = s_g[13 + f][e];
+        __syncwarp();  // the next chunk restages
     }
 }
 
@@ -479,7 +446,11 @@ void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s) 
         }
         return;
     }
-    const int grid = grid_for((p.n_items + 1) / 2);
+    // persistent: three blocks of 8 warps per SM
+    const uint32_t chunks = (p.n_items + kWarpChunk - 1) / kWarpChunk;
+    int grid = (int)((chunks + 7) / 8);
+    if (grid > 3 * device_sm_count()) grid = 3 * device_sm_count();
+    if (grid < 1) grid = 1;
     switch (p.sh_degree) {
         case 0: k_preprocess_bwd<0><<<grid, 256, 0, s>>>(p); break;
         case 1: k_preprocess_bwd<1><<<grid, 256, 0, s>>>(p); break;
