@@ -786,6 +786,7 @@ extern "C" pvg_status_t pvg_render_fwd_multi(pvg_ctx_t *x, const pvg_scene_t *sc
 
 // zeroes rows [0, *d_m) of a [*, per] array (the visible items' rows)
 __global__ static void k_zero_rows(float *a, const uint32_t *d_m, int per) {
+    pdl_enter();
     const size_t n = (size_t)per * *d_m;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
         a[k] = 0.f;
@@ -881,11 +882,11 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     if (capturing) tm.on = false;
     tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
     note_launch();
-    k_zero_rows<<<device_sm_count() * 4, 256, 0, s>>>(p.g2d, &p.counters[0], 10);
+    pdl_launch(k_zero_rows, device_sm_count() * 4, 256, 0, s, p.g2d, &p.counters[0], 10);
     launch_composite_bwd(p, s);
     if (feat_bwd && f->n_items) {
         note_launch();
-        k_zero_rows<<<device_sm_count() * 4, 256, 0, s>>>(p.gfeat, &p.counters[0], p.n_feat);
+        pdl_launch(k_zero_rows, device_sm_count() * 4, 256, 0, s, p.gfeat, &p.counters[0], p.n_feat);
         launch_composite_feat_bwd(p, s);
     }
     tm.end(PVG_STAGE_COMPOSITE_BWD, s);

@@ -28,6 +28,7 @@ namespace {
 
 template <int NG>
 __global__ void __launch_bounds__(kFeatBlock) k_composite_feat(Params P) {
+    pdl_enter();
     __shared__ float4 s0[kFB];
     __shared__ float2 s1[kFB];
     __shared__ float4 sf[kFB * NG];
@@ -122,15 +123,15 @@ void launch_composite_feat(const Params &p, cudaStream_t s) {
     note_launch();
     const int block = min(kFeatBlock, p.tile_w * p.tile_h / kFwdFPX);
     switch ((p.n_feat + 3) / 4) {
-        case 1: k_composite_feat<1><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 2: k_composite_feat<2><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 3: k_composite_feat<3><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 4: k_composite_feat<4><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 5: k_composite_feat<5><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 6: k_composite_feat<6><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 7: k_composite_feat<7><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 8: k_composite_feat<8><<<p.total_tiles, block, 0, s>>>(p); break;
-        default: k_composite_feat<9><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 1: pdl_launch(k_composite_feat<1>, p.total_tiles, block, 0, s, p); break;
+        case 2: pdl_launch(k_composite_feat<2>, p.total_tiles, block, 0, s, p); break;
+        case 3: pdl_launch(k_composite_feat<3>, p.total_tiles, block, 0, s, p); break;
+        case 4: pdl_launch(k_composite_feat<4>, p.total_tiles, block, 0, s, p); break;
+        case 5: pdl_launch(k_composite_feat<5>, p.total_tiles, block, 0, s, p); break;
+        case 6: pdl_launch(k_composite_feat<6>, p.total_tiles, block, 0, s, p); break;
+        case 7: pdl_launch(k_composite_feat<7>, p.total_tiles, block, 0, s, p); break;
+        case 8: pdl_launch(k_composite_feat<8>, p.total_tiles, block, 0, s, p); break;
+        default: pdl_launch(k_composite_feat<9>, p.total_tiles, block, 0, s, p); break;
     }
 }
 

@@ -56,6 +56,7 @@ __device__ __forceinline__ void reduce_chunk(const float (&gv)[NT], float *s_acc
 
 template <int NG>
 __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
+    pdl_enter();
     constexpr int F4 = 4 * NG;
     constexpr int NT = 6 + F4;  // moments x, y, xx, xy, yy; opacity; channels
     __shared__ float4 s0[kFB];
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kFeatBlock) k_composite_feat_bwd(Params P) {
 
 // dL/d(channel values) of each visible item -> v, beta, l, semantics
 __global__ void k_feat_param_bwd(Params P) {
+    pdl_enter();
     const uint32_t M = P.counters[0];
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         const uint32_t gid = P.sgid[m];
@@ -246,22 +248,22 @@ void launch_composite_feat_bwd(const Params &p, cudaStream_t s) {
     note_launch();
     const int block = min(kFeatBlock, p.tile_w * p.tile_h / kBwdFPX);
     switch ((p.n_feat + 3) / 4) {
-        case 1: k_composite_feat_bwd<1><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 2: k_composite_feat_bwd<2><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 3: k_composite_feat_bwd<3><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 4: k_composite_feat_bwd<4><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 5: k_composite_feat_bwd<5><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 6: k_composite_feat_bwd<6><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 7: k_composite_feat_bwd<7><<<p.total_tiles, block, 0, s>>>(p); break;
-        case 8: k_composite_feat_bwd<8><<<p.total_tiles, block, 0, s>>>(p); break;
-        default: k_composite_feat_bwd<9><<<p.total_tiles, block, 0, s>>>(p); break;
+        case 1: pdl_launch(k_composite_feat_bwd<1>, p.total_tiles, block, 0, s, p); break;
+        case 2: pdl_launch(k_composite_feat_bwd<2>, p.total_tiles, block, 0, s, p); break;
+        case 3: pdl_launch(k_composite_feat_bwd<3>, p.total_tiles, block, 0, s, p); break;
+        case 4: pdl_launch(k_composite_feat_bwd<4>, p.total_tiles, block, 0, s, p); break;
+        case 5: pdl_launch(k_composite_feat_bwd<5>, p.total_tiles, block, 0, s, p); break;
+        case 6: pdl_launch(k_composite_feat_bwd<6>, p.total_tiles, block, 0, s, p); break;
+        case 7: pdl_launch(k_composite_feat_bwd<7>, p.total_tiles, block, 0, s, p); break;
+        case 8: pdl_launch(k_composite_feat_bwd<8>, p.total_tiles, block, 0, s, p); break;
+        default: pdl_launch(k_composite_feat_bwd<9>, p.total_tiles, block, 0, s, p); break;
     }
 }
 
 void launch_feat_param_bwd(const Params &p, cudaStream_t s) {
     if (p.n_items == 0 || p.n_feat <= 0) return;
     note_launch();
-    k_feat_param_bwd<<<4 * device_sm_count(), 256, 0, s>>>(p);
+    pdl_launch(k_feat_param_bwd, 4 * device_sm_count(), 256, 0, s, p);
 }
 
 }  // namespace pvg

@@ -32,6 +32,7 @@ __device__ __forceinline__ float block_sum(float v, float *warp_sum) {
 __global__ void __launch_bounds__(kL1Threads) k_l1(const float *__restrict__ pred, const float *__restrict__ tgt,
                                                    size_t n, float scale, float *__restrict__ dl,
                                                    unsigned int *ticket, float *partials, float *loss) {
+    pdl_enter();
     __shared__ float warp_sum[kL1Threads / 32];
     __shared__ bool is_last;
     float acc = 0.f;
@@ -77,7 +78,7 @@ cudaError_t launch_l1_loss(const float *pred, const float *target, int64_t n, fl
     unsigned int *ticket = (unsigned int *)scratch;
     float *partials = (float *)((char *)scratch + kL1PartialsOffset);
     note_launch();
-    k_l1<<<l1_blocks(n), kL1Threads, 0, s>>>(pred, target, (size_t)n, scale, dl, ticket, partials, loss);
+    pdl_launch(k_l1, l1_blocks(n), kL1Threads, 0, s, pred, target, (size_t)n, scale, dl, ticket, partials, loss);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ cudaError_t set_sh_constants() {
 namespace {
 
 __global__ void __launch_bounds__(256) k_project_count(Params P) {
+    pdl_enter();
     const uint32_t n = P.n_items;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
         const int view = view_of_item(P.views, P.n_views, g);
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(256) k_project_count(Params P) {
 // sectors in any order.
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
+    pdl_enter();
     constexpr int K = (D + 1) * (D + 1);
     const uint32_t M = P.counters[0];
     for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
@@ -113,16 +115,16 @@ __global__ void __launch_bounds__(256, 4) k_finalize(Params P) {
 
 void launch_project_count(const Params &p, cudaStream_t s) {
     note_launch();
-    k_project_count<<<grid_for(p.n_items), 256, 0, s>>>(p);
+    pdl_launch(k_project_count, grid_for(p.n_items), 256, 0, s, p);
 }
 
 void launch_finalize(const Params &p, cudaStream_t s) {
     note_launch();
     switch (p.sh_degree) {
-        case 0: k_finalize<0><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
-        case 1: k_finalize<1><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
-        case 2: k_finalize<2><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
-        default: k_finalize<3><<<grid_for(p.n_items), 256, 0, s>>>(p); break;
+        case 0: pdl_launch(k_finalize<0>, grid_for(p.n_items), 256, 0, s, p); break;
+        case 1: pdl_launch(k_finalize<1>, grid_for(p.n_items), 256, 0, s, p); break;
+        case 2: pdl_launch(k_finalize<2>, grid_for(p.n_items), 256, 0, s, p); break;
+        default: pdl_launch(k_finalize<3>, grid_for(p.n_items), 256, 0, s, p); break;
     }
 }
 

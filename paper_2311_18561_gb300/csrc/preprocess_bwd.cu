@@ -266,6 +266,7 @@ constexpr int kViewsThreads = 128;
 
 template <int D>
 __global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P) {
+    pdl_enter();
     constexpr int K = (D + 1) * (D + 1);
     extern __shared__ float s_sh[];  // [3 K][kViewsThreads]
     const int tid = threadIdx.x;
@@ -333,6 +334,7 @@ constexpr int kWarpPer = kWarpChunk / 32;
 
 template <int D>
 __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
+    pdl_enter();
     constexpr int K = (D + 1) * (D + 1);
     __shared__ float s_gw[8][kSmall][kWarpChunk];
     __shared__ uint32_t s_mw[8][kWarpChunk];  // depth positions of the compacted items
@@ -439,10 +441,10 @@ void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s) 
         if (grid < 1) grid = 1;
         const size_t smem = sizeof(float) * 3 * (p.sh_degree + 1) * (p.sh_degree + 1) * kViewsThreads;
         switch (p.sh_degree) {
-            case 0: k_preprocess_bwd_views<0><<<grid, kViewsThreads, smem, s>>>(p); break;
-            case 1: k_preprocess_bwd_views<1><<<grid, kViewsThreads, smem, s>>>(p); break;
-            case 2: k_preprocess_bwd_views<2><<<grid, kViewsThreads, smem, s>>>(p); break;
-            default: k_preprocess_bwd_views<3><<<grid, kViewsThreads, smem, s>>>(p); break;
+            case 0: pdl_launch(k_preprocess_bwd_views<0>, grid, kViewsThreads, smem, s, p); break;
+            case 1: pdl_launch(k_preprocess_bwd_views<1>, grid, kViewsThreads, smem, s, p); break;
+            case 2: pdl_launch(k_preprocess_bwd_views<2>, grid, kViewsThreads, smem, s, p); break;
+            default: pdl_launch(k_preprocess_bwd_views<3>, grid, kViewsThreads, smem, s, p); break;
         }
         return;
     }
@@ -452,10 +454,10 @@ void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s) 
     if (grid > 3 * device_sm_count()) grid = 3 * device_sm_count();
     if (grid < 1) grid = 1;
     switch (p.sh_degree) {
-        case 0: k_preprocess_bwd<0><<<grid, 256, 0, s>>>(p); break;
-        case 1: k_preprocess_bwd<1><<<grid, 256, 0, s>>>(p); break;
-        case 2: k_preprocess_bwd<2><<<grid, 256, 0, s>>>(p); break;
-        default: k_preprocess_bwd<3><<<grid, 256, 0, s>>>(p); break;
+        case 0: pdl_launch(k_preprocess_bwd<0>, grid, 256, 0, s, p); break;
+        case 1: pdl_launch(k_preprocess_bwd<1>, grid, 256, 0, s, p); break;
+        case 2: pdl_launch(k_preprocess_bwd<2>, grid, 256, 0, s, p); break;
+        default: pdl_launch(k_preprocess_bwd<3>, grid, 256, 0, s, p); break;
     }
 }
 

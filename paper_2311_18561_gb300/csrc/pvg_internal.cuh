@@ -19,6 +19,7 @@
 //   pixels    final transmittance and last blended list position      [sum HW]
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -403,10 +404,42 @@ __device__ __forceinline__ void sky_texels(const ViewDesc &V, int px, int py, si
     idx[3] = 3 * (base + (size_t)y1 * R + x1); w[3] = fx * fy;
 }
 
+// Programmatic dependent launch: a kernel started with pdl_launch may be
+// scheduled while the kernel before it on the stream finishes, so that its
+// launch and block dispatch overlap the previous kernel's last blocks.
+// Every such kernel calls pdl_enter() first, which waits until the previous
+// kernel has completed with all its writes visible (griddepcontrol.wait):
+// no work overlaps.  Kernels do not signal their dependents early (the
+// signal is implicit when their blocks exit): an early signal let waiting
+// blocks of the next kernel sit beside the running one and made the
+// captured steps 6 to 9 % slower.  For a kernel launched without the
+// attribute the wait returns at once.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace pvg
 
 // host-side launchers (one translation unit each)
 namespace pvg {
+
+// kernel<<<grid, block, smem, s>>>(args...) with programmatic stream
+// serialization allowed (the kernel must begin with pdl_enter()); a launch
+// error is left for cudaGetLastError, as with <<<>>>
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // counts every kernel launch of the library (reported by pvg_kernel_launches)
 void note_launch();
 // streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,

@@ -70,6 +70,7 @@ __device__ __forceinline__ void composite_epilogue(const Params &P, const ViewDe
 // alpha >= 1/255 (blended, or stopping the pixel).
 template <int TW, int TH, int PX, bool kStats>
 __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
+    pdl_enter();
     constexpr int BLOCK = TW * TH / PX;
     constexpr uint32_t ALL = (1u << PX) - 1u;
     __shared__ float4 s0[BLOCK];
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
 // kernel's bit for bit.
 template <int TW, int TH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
+    pdl_enter();
     static_assert(PX % 2 == 0, "pairs of pixels");
     constexpr int BLOCK = TW * TH / PX;
     constexpr int NP = PX / 2;
@@ -294,15 +296,15 @@ template <int TW, int TH, int PX>
 void launch_fwd_t(const Params &p, cudaStream_t s) {
     note_launch();
     if constexpr (PX % 2 == 0)
-        k_composite_x2<TW, TH, PX><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+        pdl_launch(k_composite_x2<TW, TH, PX>, p.total_tiles, TW * TH / PX, 0, s, p);
     else
-        k_composite<TW, TH, PX, false><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+        pdl_launch(k_composite<TW, TH, PX, false>, p.total_tiles, TW * TH / PX, 0, s, p);
 }
 
 template <int TW, int TH, int PX>
 void launch_stats_t(const Params &p, cudaStream_t s) {
     note_launch();
-    k_composite<TW, TH, PX, true><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+    pdl_launch(k_composite<TW, TH, PX, true>, p.total_tiles, TW * TH / PX, 0, s, p);
 }
 
 }  // namespace

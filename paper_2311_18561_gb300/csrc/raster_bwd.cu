@@ -145,6 +145,7 @@ __device__ __forceinline__ void flush_entry(float *dst, const float *a, float ap
 // depth term is not reduced (9 terms).
 template <int TW, int TH, int PX, bool kAux>
 __global__ void __launch_bounds__(TW *TH / PX) k_composite_bwd(Params P) {
+    pdl_enter();
     constexpr int BLOCK = TW * TH / PX;
     constexpr int NG = 10;               // shared accumulator stride
     constexpr int NT = kAux ? 10 : 9;    // terms reduced
@@ -271,9 +272,9 @@ template <int TW, int TH, int PX>
 void launch_bwd_t(const Params &p, cudaStream_t s) {
     note_launch();
     if (p.aux)
-        k_composite_bwd<TW, TH, PX, true><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+        pdl_launch(k_composite_bwd<TW, TH, PX, true>, p.total_tiles, TW * TH / PX, 0, s, p);
     else
-        k_composite_bwd<TW, TH, PX, false><<<p.total_tiles, TW * TH / PX, 0, s>>>(p);
+        pdl_launch(k_composite_bwd<TW, TH, PX, false>, p.total_tiles, TW * TH / PX, 0, s, p);
 }
 
 }  // namespace

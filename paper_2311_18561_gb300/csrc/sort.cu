@@ -132,6 +132,7 @@ struct EmitF {
 
 template <class F>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, uint32_t *partials) {
+    pdl_enter();
     __shared__ uint32_t smem[33];
     uint32_t b0, b1;
     segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, uint32_t *par
 // *total = sum; if cap_flag != NULL and total > capacity, set *cap_flag.
 __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int G, uint32_t *total,
                                                         uint32_t capacity, uint32_t *cap_flag) {
+    pdl_enter();
     __shared__ uint32_t smem[33];
     const uint32_t v = threadIdx.x < (unsigned)G ? partials[threadIdx.x] : 0u;
     uint32_t tot;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int 
 
 template <class F>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, const uint32_t *partials) {
+    pdl_enter();
     __shared__ uint32_t smem[33];
     uint32_t b0, b1;
     segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
@@ -207,6 +210,7 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *keys, const uint32_t *d_n,
                                                                 uint32_t cap, int shift, uint32_t mask,
                                                                 uint32_t *hist) {
+    pdl_enter();
     __shared__ uint32_t sh[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) sh[d] = 0;
     __syncthreads();
@@ -222,6 +226,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
 // totals[d].  The downsweep adds the exclusive prefix of the totals over
 // the digits.  G <= 1024.
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, uint32_t *totals, int G) {
+    pdl_enter();
     __shared__ uint32_t smem[33];
     uint32_t *row = hist + (size_t)blockIdx.x * G;
     const uint32_t v = (int)threadIdx.x < G ? row[threadIdx.x] : 0u;
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
                                                               const ViewDesc *views, int nv, const uint32_t *d_m,
                                                               const uint32_t *d_k, uint32_t capacity,
                                                               uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    pdl_enter();
     constexpr int kPer = kEmitChunk / kEmitThreads;  // slots per thread in the scan
     __shared__ uint32_t s_item[kEmitChunk];
     __shared__ uint32_t s_warp[kEmitThreads / 32];
@@ -400,6 +406,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
                                                                   uint32_t mask, const uint32_t *hist,
                                                                   const uint32_t *totals,
                                                                   uint32_t *__restrict__ inv_out) {
+    pdl_enter();
     constexpr int kSortTile = kSortThreads * ITEMS;
     __shared__ SortSmem<kSortTile> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -485,6 +492,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
 // few dependent sweeps remain.
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_k,
                                                 uint32_t capacity, uint2 *__restrict__ ranges) {
+    pdl_enter();
     constexpr uint32_t kNone = 0xffffffffu;  // no tile has this id
     const uint32_t K = min(*d_k, capacity);
     const uint32_t stride = gridDim.x * blockDim.x * 8u;
@@ -536,11 +544,11 @@ void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, vo
     CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, p.n_items};
     const int G = scan_blocks(p.n_items);
     note_launch();
-    k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    pdl_launch(k_scan_reduce<CompactF>, G, kScanThreads, 0, s, f, t.partials);
     note_launch();
-    k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[0], 0xffffffffu, nullptr);
+    pdl_launch(k_scan_partials, 1, 1024, 0, s, t.partials, G, &p.counters[0], 0xffffffffu, nullptr);
     note_launch();
-    k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    pdl_launch(k_scan_apply<CompactF>, G, kScanThreads, 0, s, f, t.partials);
 }
 
 template <int ITEMS>
@@ -574,16 +582,16 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
         note_launch();
-        k_radix_upsweep<ITEMS><<<G, kSortThreads, 0, s>>>(ki, d_count, capacity, b, mask, t.hist);
+        pdl_launch(k_radix_upsweep<ITEMS>, G, kSortThreads, 0, s, ki, d_count, capacity, b, mask, t.hist);
         note_launch();
-        k_radix_scan<<<kRadix, 1024, 0, s>>>(t.hist, t.totals, G);
+        pdl_launch(k_radix_scan, kRadix, 1024, 0, s, t.hist, t.totals, G);
         note_launch();
         uint32_t *inv_pass = b + nb >= end_bit ? inv_out : nullptr;  // the last pass only
         // one ballot per digit bit: the last pass of a sort by fewer than a
         // multiple of 8 bits ranks with fewer ballots
 #define PVG_DOWNSWEEP(NBITS)                                                                                    \
     case NBITS:                                                                                                 \
-        k_radix_downsweep<ITEMS, NBITS><<<G, kSortThreads, 0, s>>>(ki, vi, ko, vo, d_count, capacity, b, mask, \
+        pdl_launch(k_radix_downsweep<ITEMS, NBITS>, G, kSortThreads, 0, s, ki, vi, ko, vo, d_count, capacity, b, mask, \
                                                                    t.hist, t.totals, inv_pass);                \
         break;
         switch (nb) {
@@ -605,9 +613,9 @@ void scan_count_pairs(const Params &p, void *temp, cudaStream_t s) {
     EmitF f{&p.counters[0], p.vis_cnt, p.vis_off, p.chunk_start, p.pair_capacity};
     const int G = scan_blocks(p.n_items);
     note_launch();
-    k_scan_reduce<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    pdl_launch(k_scan_reduce<EmitF>, G, kScanThreads, 0, s, f, t.partials);
     note_launch();
-    k_scan_partials<<<1, 1024, 0, s>>>(t.partials, G, &p.counters[1], p.pair_capacity, &p.counters[2]);
+    pdl_launch(k_scan_partials, 1, 1024, 0, s, t.partials, G, &p.counters[1], p.pair_capacity, &p.counters[2]);
 }
 
 size_t emit_chunks(uint32_t capacity) { return (capacity + kEmitChunk - 1) / kEmitChunk + 1; }
@@ -617,12 +625,12 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     EmitF f{&p.counters[0], p.vis_cnt, p.vis_off, p.chunk_start, p.pair_capacity};
     const int G = scan_blocks(p.n_items);
     note_launch();
-    k_scan_apply<<<G, kScanThreads, 0, s>>>(f, t.partials);
+    pdl_launch(k_scan_apply<EmitF>, G, kScanThreads, 0, s, f, t.partials);
     uint32_t grid = (uint32_t)((p.pair_capacity + kEmitChunk - 1) / kEmitChunk);
     if (grid < 1) grid = 1;
     if (grid > (uint32_t)(8 * device_sm_count())) grid = 8 * device_sm_count();
     note_launch();
-    k_expand_pairs<<<grid, kEmitThreads, 0, s>>>(p.vis_off, p.vis_cnt, p.chunk_start, p.rect, p.rowtab, p.ell,
+    pdl_launch(k_expand_pairs, grid, kEmitThreads, 0, s, p.vis_off, p.vis_cnt, p.chunk_start, p.rect, p.rowtab, p.ell,
                                                  p.tile_w, p.tile_h,
                                                  p.sgid, p.views, p.n_views,
                                                  &p.counters[0], &p.counters[1], p.pair_capacity, p.pair_keys,
@@ -635,6 +643,7 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
 // to the atomics (each tile's result does not depend on when it runs).
 __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
                                                      uint32_t *__restrict__ order) {
+    pdl_enter();
     __shared__ uint32_t cnt[64];
     __shared__ uint32_t smem[33];
     if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
@@ -657,13 +666,13 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
 void launch_tile_order(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0) return;
     note_launch();
-    k_tile_order<<<1, 1024, 0, s>>>(p.ranges, p.total_tiles, p.tile_order);
+    pdl_launch(k_tile_order, 1, 1024, 0, s, p.ranges, p.total_tiles, p.tile_order);
 }
 
 void launch_ranges(const Params &p, cudaStream_t s) {
     cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * (size_t)p.total_tiles, s);
     note_launch();
-    k_ranges<<<8 * device_sm_count(), 256, 0, s>>>(p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
+    pdl_launch(k_ranges, 8 * device_sm_count(), 256, 0, s, p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
 }
 
 }  // namespace pvg

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rgb_loss(const float *__restric
                                                        const float *__restrict__ tgt, int H, int W,
                                                        float lambda_r, float inv_n, float *__restrict__ dl,
                                                        float2 *__restrict__ partial) {
+    pdl_enter();
     extern __shared__ float sm[];
     float *sx = sm + kOffX, *sy = sm + kOffY, *hm = sm + kOffH, *abc = sm + kOffABC, *h2 = sm + kOffH2;
     float *g = sm + kOffG, *red = sm + kOffRed;
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_rgb_loss(const float *__restric
 // fixed order in double precision
 __global__ void __launch_bounds__(1024) k_rgb_loss_finish(const float2 *__restrict__ partial, int n,
                                                           double inv_n, float lambda_r, float *loss) {
+    pdl_enter();
     __shared__ double ss[1024], sl[1024];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -275,10 +277,10 @@ cudaError_t launch_rgb_loss(const float *pred, const float *target, int channels
     const dim3 grid((width + kT - 1) / kT, (height + kT - 1) / kT, channels);
     const double n = (double)channels * height * width;
     note_launch();
-    k_rgb_loss<<<grid, kThreads, smem, s>>>(pred, target, height, width, lambda_r, (float)(1.0 / n), dl,
+    pdl_launch(k_rgb_loss, grid, kThreads, smem, s, pred, target, height, width, lambda_r, (float)(1.0 / n), dl,
                                             reinterpret_cast<float2 *>(partials));
     note_launch();
-    k_rgb_loss_finish<<<1, 1024, 0, s>>>(reinterpret_cast<const float2 *>(partials),
+    pdl_launch(k_rgb_loss_finish, 1, 1024, 0, s, reinterpret_cast<const float2 *>(partials),
                                          (int)rgb_loss_partials(channels, height, width), 1.0 / n, lambda_r, loss);
     return cudaGetLastError();
 }
