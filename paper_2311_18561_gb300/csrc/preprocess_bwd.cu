@@ -324,23 +324,54 @@ __global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P
 // A warp takes chunks of kWarpChunk consecutive items (every gridDim.x *
 // 8-th chunk): their visibility by ballot, the visible items compacted onto
 // its lanes, the 17 small gradients of the chunk staged in the warp's
-// shared memory (zeros for the invisible items) and written out coalesced,
-// field by field, so that each 32-byte sector is written whole by one
-// instruction.  SH-coefficient rows (192 bytes at degree 3) are written by
-// the visible item's lane, and zeroed warp-wide as float4 for the
-// invisible items.
+// shared memory in the global arrays' own layout (zeros for the invisible
+// items) and copied out as float4, so that each 32-byte sector is written
+// whole and no index is divided.  SH-coefficient rows (192 bytes at degree
+// 3) are written by the visible item's lane, and zeroed warp-wide as float4
+// for the invisible items.
 constexpr int kWarpChunk = 64;
 constexpr int kWarpPer = kWarpChunk / 32;
+// offsets of the staged fields in a warp's buffer (floats): mu, v, s (3 per
+// item), q (4), tau, beta, l, o (1)
+constexpr int kStMu = 0, kStVel = 3 * kWarpChunk, kStScale = 6 * kWarpChunk, kStQuat = 9 * kWarpChunk,
+              kStOne = 13 * kWarpChunk;
+
+// dst[0, n) = src[0, n) by one warp (float4 where both allow it)
+__device__ __forceinline__ void warp_copy_out(float *dst, const float *src, uint32_t n, int lane) {
+    if (!dst) return;
+    if (aligned16(dst) && (n & 3u) == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (uint32_t e = lane; e < n / 4; e += 32) d4[e] = s4[e];
+    } else {
+        for (uint32_t e = lane; e < n; e += 32) dst[e] = src[e];
+    }
+}
+
+__device__ __forceinline__ void stage_small(float *st, int idx, const SmallGrads &q) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        st[kStMu + 3 * idx + c] = q.mu[c];
+        st[kStVel + 3 * idx + c] = q.vel[c];
+        st[kStScale + 3 * idx + c] = q.scale[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) st[kStQuat + 4 * idx + c] = q.quat[c];
+    st[kStOne + idx] = q.tau;
+    st[kStOne + kWarpChunk + idx] = q.beta;
+    st[kStOne + 2 * kWarpChunk + idx] = q.period;
+    st[kStOne + 3 * kWarpChunk + idx] = q.opac;
+}
 
 template <int D>
 __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     pdl_enter();
     constexpr int K = (D + 1) * (D + 1);
-    __shared__ float s_gw[8][kSmall][kWarpChunk];
+    __shared__ __align__(16) float s_gw[8][kSmall * kWarpChunk];
     __shared__ uint32_t s_mw[8][kWarpChunk];  // depth positions of the compacted items
     __shared__ uint8_t s_lw[8][kWarpChunk];   // their places in the chunk
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float(*s_g)[kWarpChunk] = s_gw[warp];
+    float *st = s_gw[warp];
     uint32_t *s_mpos = s_mw[warp];
     uint8_t *s_list = s_lw[warp];
     const ViewDesc &V = P.views[0];  // one view: item g is Gaussian g (item_base 0)
@@ -349,23 +380,24 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     const uint32_t n = P.n_items;
     const uint32_t lmask = (1u << lane) - 1u;
     const uint32_t n_chunks = (n + kWarpChunk - 1) / kWarpChunk;
+    const SmallGrads zero{};
     for (uint32_t c = blockIdx.x * 8u + warp; c < n_chunks; c += gridDim.x * 8u) {
         const uint32_t base = c * kWarpChunk;
-        uint32_t vis[kWarpPer];
+        uint64_t vis = 0;  // bit k: item base + k is visible
         uint32_t nvis = 0;
 #pragma unroll
         for (int q = 0; q < kWarpPer; q++) {
             const uint32_t g = base + 32 * q + lane;
             const uint32_t m = g < n ? P.inv[g] : 0xffffffffu;
             const bool v = m != 0xffffffffu;
-            vis[q] = __ballot_sync(0xffffffffu, v);
+            const uint32_t b = __ballot_sync(0xffffffffu, v);
+            vis |= (uint64_t)b << (32 * q);
             if (v) {
-                const uint32_t r = nvis + __popc(vis[q] & lmask);
+                const uint32_t r = nvis + __popc(b & lmask);
                 s_mpos[r] = m;
                 s_list[r] = (uint8_t)(32 * q + lane);
             } else {
-#pragma unroll
-                for (int f = 0; f < kSmall; f++) s_g[f][32 * q + lane] = 0.f;
+                stage_small(st, 32 * q + lane, zero);
                 if (g < n && V.g_sh && !rows4) {
                     float z[3 * K];
 #pragma unroll
@@ -373,16 +405,22 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
                     store_floats<3 * K>(V.g_sh + (size_t)g * 3 * K, z, aligned16(V.g_sh));
                 }
             }
-            nvis += __popc(vis[q]);
+            nvis += __popc(b);
         }
         if constexpr (kRows4) {
-            if (rows4) {  // SH rows of the invisible items, warp-wide
-                constexpr int R4 = 3 * K / 4;
+            if (rows4) {  // SH rows of the invisible items, warp-wide; float4 e is row e / R4
+                constexpr uint32_t R4 = 3 * K / 4;
                 float4 *sh4 = reinterpret_cast<float4 *>(V.g_sh + (size_t)base * 3 * K);
                 const uint32_t cn4 = min((uint32_t)kWarpChunk, n - base) * R4;
+                uint32_t item = (uint32_t)lane / R4, rem = (uint32_t)lane % R4;
                 for (uint32_t e = lane; e < cn4; e += 32) {
-                    const uint32_t item = e / R4;
-                    if (!((vis[item >> 5] >> (item & 31)) & 1u)) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!((vis >> item) & 1u)) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    item += 32u / R4;
+                    rem += 32u % R4;
+                    if (rem >= R4) {
+                        rem -= R4;
+                        item++;
+                    }
                 }
             }
         }
@@ -393,7 +431,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
             const uint32_t i = base + idx;
             SmallGrads q;
             if (!item_adjoint<D>(P, V, i, s_mpos[k], false, q)) {  // culled after all: zeros
-                q = SmallGrads{};
+                q = zero;
                 if (V.g_sh) {
                     float z[3 * K];
 #pragma unroll
@@ -401,29 +439,19 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
                     store_floats<3 * K>(V.g_sh + (size_t)i * 3 * K, z, aligned16(V.g_sh));
                 }
             }
-            const float v[kSmall] = {q.mu[0], q.mu[1], q.mu[2], q.vel[0], q.vel[1], q.vel[2],
-                                     q.scale[0], q.scale[1], q.scale[2], q.quat[0], q.quat[1], q.quat[2], q.quat[3],
-                                     q.tau, q.beta, q.period, q.opac};
-#pragma unroll
-            for (int f = 0; f < kSmall; f++) s_g[f][idx] = v[f];
+            stage_small(st, idx, q);
         }
         __syncwarp();
-        // coalesced write-out of the chunk's small gradients
+        // the chunk's small gradients, copied out
         const uint32_t cn = min((uint32_t)kWarpChunk, n - base);
-        auto out3 = [&](float *dst, int f0) {
-            if (!dst) return;
-            for (uint32_t e = lane; e < 3 * cn; e += 32) dst[3 * (size_t)base + e] = s_g[f0 + e % 3][e / 3];
-        };
-        out3(V.g_mu, 0);
-        out3(V.g_vel, 3);
-        out3(V.g_scale, 6);
-        if (V.g_quat)
-            for (uint32_t e = lane; e < 4 * cn; e += 32) V.g_quat[4 * (size_t)base + e] = s_g[9 + (e & 3)][e >> 2];
+        warp_copy_out(V.g_mu ? V.g_mu + 3 * (size_t)base : nullptr, st + kStMu, 3 * cn, lane);
+        warp_copy_out(V.g_vel ? V.g_vel + 3 * (size_t)base : nullptr, st + kStVel, 3 * cn, lane);
+        warp_copy_out(V.g_scale ? V.g_scale + 3 * (size_t)base : nullptr, st + kStScale, 3 * cn, lane);
+        warp_copy_out(V.g_quat ? V.g_quat + 4 * (size_t)base : nullptr, st + kStQuat, 4 * cn, lane);
         float *const one[4] = {V.g_tau, V.g_beta, V.g_period, V.g_opac};
 #pragma unroll
         for (int f = 0; f < 4; f++)
-            if (one[f])
-                for (uint32_t e = lane; e < cn; e += 32) one[f][base + e] = s_g[13 + f][e];
+            warp_copy_out(one[f] ? one[f] + base : nullptr, st + kStOne + f * kWarpChunk, cn, lane);
         __syncwarp();  // the next chunk restages
     }
 }
