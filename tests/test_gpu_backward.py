@@ -235,3 +235,56 @@ def test_backward_of_70_views_sums_the_views():
     r.backward(st, cams, fr, dls, grads=grads)
     torch.cuda.synchronize()
     _compare_grads(grads, ref)
+
+
+@pytest.mark.parametrize("deg", [3, 2])
+def test_backward_into_unaligned_and_partial_gradient_buffers(deg):
+    """The per-item adjoint writes every gradient entry, float4-wide where
+    the arrays allow it.  Gradient arrays that start 4 bytes past a 16-byte
+    boundary, a Gaussian count that leaves a partial last chunk (1,037 =
+    16 x 64 + 13), SH rows that are not whole float4 (degree 2: 27 floats)
+    and arrays left out (NULL) must give the values of aligned arrays
+    (equal up to the order of the compositor adjoint's float atomics, which
+    differs between calls; exact zeros for the culled Gaussians) and must
+    write nothing else."""
+    scene = synth.make_fd_scene(seed=21, n=1037, sh_degree=deg)
+    scene["mu"][::3, 0] += 1000.0  # every third Gaussian far off to the side: culled
+    cam = synth.fd_camera(64, 48, t=0.4)
+    H, W = cam["height"], cam["width"]
+    w_rgb, w_d, w_a = _weights(H, W, 23)
+    dl = dict(rgb=torch.tensor(w_rgb, dtype=torch.float32, device="cuda"),
+              depth=torch.tensor(w_d, dtype=torch.float32, device="cuda"),
+              alpha=torch.tensor(w_a, dtype=torch.float32, device="cuda"))
+    r = R.Renderer()
+    fr = R.Frame()
+    st = R.scene_to_device(scene)
+    r.forward(st, [cam], frame=fr)
+    ref = r.backward(st, [cam], fr, [dl])
+    assert int((ref["opacity"] != 0).sum()) > 300 and int((ref["opacity"] == 0).sum()) >= 346
+    # each array one float past its buffer's (aligned) start, guarded on both sides
+    bufs, grads = {}, {}
+    for k in NAMES:
+        n = st[k].numel()
+        bufs[k] = torch.full((n + 2,), 7.0, device="cuda")
+        grads[k] = bufs[k][1:1 + n].view(st[k].shape)
+        assert grads[k].data_ptr() % 16 == 4
+    culled = torch.zeros(st["mu"].shape[0], dtype=torch.bool, device="cuda")
+    culled[::3] = True
+
+    def same(a, b, k):
+        assert torch.all(a[culled] == 0) and torch.all(b[culled] == 0), k
+        assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max()), k
+
+    got = r.backward(st, [cam], fr, [dl], grads=grads)
+    torch.cuda.synchronize()
+    for k in NAMES:
+        same(got[k], ref[k], k)
+        assert float(bufs[k][0]) == 7.0 and float(bufs[k][-1]) == 7.0, k
+    # only some arrays asked for: those match, nothing else is touched
+    some = {k: (torch.full_like(st[k], 7.0) if k in ("mu", "opacity", "sh") else None) for k in NAMES}
+    got = r.backward(st, [cam], fr, [dl], grads=some)
+    torch.cuda.synchronize()
+    for k in ("mu", "opacity", "sh"):
+        same(got[k], ref[k], k)
+    r.close()
+    fr.close()
