@@ -605,13 +605,14 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
         launch_project_count(p, s);
         tm.end(PVG_STAGE_PROJECT, s);
         tm.begin(PVG_STAGE_DEPTH_SORT, s);
-        compact_visible(p, p.szkey, p.sgid, x->temp.p, s);
+        // the inverse map inv[gid] = depth position: 0xffffffff for the
+        // invisible items from the compaction, the visible ones' from the
+        // sort's last pass; the compaction also counts the sort's first
+        // digit histogram
+        compact_visible(p, p.szkey, p.sgid, p.inv, x->temp.p, s);
         bool in_alt = false;
-        // the sort's last pass also writes the inverse map inv[gid] = depth
-        // position (0xffffffff stays for the invisible items)
-        PVG_CUDA(cudaMemsetAsync(p.inv, 0xff, sizeof(uint32_t) * NV, s));
         radix_sort_pairs(p.szkey, p.sgid, ptr<uint32_t>(x->alt_keys), ptr<uint32_t>(x->alt_vals), &p.counters[0], NV,
-                         0, 31, x->temp.p, s, &in_alt, p.inv);
+                         0, 31, x->temp.p, s, &in_alt, p.inv, true);
         if (in_alt) {  // 31 bits = 4 passes: never taken, kept for safety
             PVG_CUDA(cudaMemcpyAsync(p.szkey, x->alt_keys.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
             PVG_CUDA(cudaMemcpyAsync(p.sgid, x->alt_vals.p, sizeof(uint32_t) * NV, cudaMemcpyDeviceToDevice, s));
@@ -655,7 +656,9 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
         tm.end(PVG_STAGE_PAIRS, s);
         tm.begin(PVG_STAGE_TILE_SORT, s);
         bool t_alt = false;
-        radix_sort_pairs(E_keys, E_vals, F_keys, F_vals, &p.counters[1], pair_cap, 0, tbits, x->temp.p, s, &t_alt);
+        // the first digit pass's histogram was counted by the expansion
+        radix_sort_pairs(E_keys, E_vals, F_keys, F_vals, &p.counters[1], pair_cap, 0, tbits, x->temp.p, s, &t_alt,
+                         nullptr, true);
         p.pair_keys = t_alt ? F_keys : E_keys;
         p.pair_vals = ptr<uint32_t>(f->pair_vals);
         launch_ranges(p, s);

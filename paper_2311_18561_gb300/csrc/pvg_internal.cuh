@@ -459,12 +459,18 @@ void launch_finalize(const Params &p, cudaStream_t s);
 void launch_preprocess_bwd(const Params &p, bool several_views, cudaStream_t s);
 // sort / scan
 size_t sort_temp_bytes();  // kSortTempBytes
-void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s);
+// Compaction of the visible items (count > 0) into (depth key, gid) pairs
+// in gid order; also writes inv[i] = 0xffffffff for the invisible items
+// and the first digit pass's histogram of the depth sort that follows
+// (radix_sort_pairs over capacity n_items, bits from 0, first_hist = true).
+void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, uint32_t *inv, void *temp,
+                     cudaStream_t s);
 // inv_out (optional): the last pass also writes inv_out[value] = the
-// value's final position
+// value's final position.  first_hist: the first pass's digit histogram is
+// already in the scratch (counted by the keys' producer), no upsweep.
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out = nullptr);
+                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out = nullptr, bool first_hist = false);
 void scan_count_pairs(const Params &p, void *temp, cudaStream_t s);
 void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
 size_t emit_chunks(uint32_t capacity);

@@ -96,9 +96,11 @@ __device__ __forceinline__ void segment_of(uint32_t n, int G, int align, uint32_
 
 // Functor protocol: n() element count, value(i) item's count,
 // apply(i, offset) consumes the exclusive prefix.
+// inv: set to 0xffffffff for the invisible items (the depth sort's last
+// pass writes the visible ones' positions)
 struct CompactF {
     const uint32_t *cnt, *zkey;
-    uint32_t *keys_out, *vals_out;
+    uint32_t *keys_out, *vals_out, *inv;
     uint32_t n_items;
     __device__ uint32_t n() const { return n_items; }
     __device__ uint32_t value(uint32_t i) const { return cnt[i] > 0u ? 1u : 0u; }
@@ -106,6 +108,8 @@ struct CompactF {
         if (v) {
             keys_out[off] = zkey[i];
             vals_out[off] = i;
+        } else {
+            inv[i] = 0xffffffffu;
         }
     }
 };
@@ -130,10 +134,17 @@ struct EmitF {
     }
 };
 
+// zero (optional): nzero words that a later kernel of the sequence
+// accumulates into or fills sparsely, zeroed here grid-wide (saving a
+// memset node between kernel launches)
 template <class F>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, uint32_t *partials) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(F f, uint32_t *partials, uint32_t *zero,
+                                                              uint32_t nzero) {
     pdl_enter();
     __shared__ uint32_t smem[33];
+    if (zero)
+        for (uint32_t i = blockIdx.x * kScanThreads + threadIdx.x; i < nzero; i += gridDim.x * kScanThreads)
+            zero[i] = 0u;
     uint32_t b0, b1;
     segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
     uint32_t acc = 0;
@@ -160,9 +171,13 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, int 
 }
 
 template <class F>
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, const uint32_t *partials) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, const uint32_t *partials, uint32_t *zero,
+                                                             uint32_t nzero) {
     pdl_enter();
     __shared__ uint32_t smem[33];
+    if (zero)
+        for (uint32_t i = blockIdx.x * kScanThreads + threadIdx.x; i < nzero; i += gridDim.x * kScanThreads)
+            zero[i] = 0u;
     uint32_t b0, b1;
     segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
     uint32_t base = partials[blockIdx.x];
@@ -186,6 +201,66 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(F f, const uint32_t
             off += v[k];
         }
         base += total;
+    }
+}
+
+// k_scan_apply for the compaction of the visible items, which also writes
+// inv[i] = 0xffffffff for the invisible items and counts the first digit
+// pass of the depth sort that follows: hist[d * sort_G + b] = keys with
+// low byte d in the sort block b that owns their output position (the
+// sort's partition of M keys into sort_G segments of whole tiles of
+// sort_tile keys).  A block's outputs are contiguous, so its counts are
+// summed in shared memory and added with at most 256 atomics per sort
+// block they touch.  hist is zeroed by the compaction's reduce kernel.
+constexpr int kCompactSpan = 4;  // sort blocks one apply block's outputs can touch (checked; else direct atomics)
+__global__ void __launch_bounds__(kScanThreads) k_compact_apply(CompactF f, const uint32_t *partials,
+                                                               const uint32_t *d_m, uint32_t *hist, int sort_G,
+                                                               uint32_t sort_tile) {
+    pdl_enter();
+    __shared__ uint32_t smem[33];
+    __shared__ uint32_t s_hist[kCompactSpan][kRadix];
+    for (int k = threadIdx.x; k < kCompactSpan * kRadix; k += kScanThreads) (&s_hist[0][0])[k] = 0u;
+    uint32_t b0, b1;
+    segment_of(f.n(), gridDim.x, kScanChunk, &b0, &b1);
+    const uint32_t M = *d_m;
+    const uint32_t seg = ((M + sort_G - 1) / sort_G + sort_tile - 1) / sort_tile * sort_tile;
+    const uint32_t block_base = partials[blockIdx.x];
+    const uint32_t sb0 = block_base / max(seg, 1u);  // first sort block of this block's outputs
+    uint32_t base = block_base;
+    __syncthreads();
+    for (uint32_t c0 = b0; c0 < b1; c0 += kScanChunk) {
+        uint32_t v[kScanItems];
+        uint32_t sum = 0;
+        const uint32_t first = c0 + threadIdx.x * kScanItems;
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const uint32_t i = first + k;
+            v[k] = i < b1 ? f.value(i) : 0u;
+            sum += v[k];
+        }
+        uint32_t total;
+        uint32_t off = base + block_excl_scan(sum, smem, &total);
+#pragma unroll
+        for (int k = 0; k < kScanItems; k++) {
+            const uint32_t i = first + k;
+            if (i < b1) {
+                f.apply(i, off, v[k]);
+                if (v[k]) {
+                    const uint32_t d = f.zkey[i] & (kRadix - 1u);
+                    const uint32_t sb = off / seg - sb0;
+                    if (sb < (uint32_t)kCompactSpan) atomicAdd(&s_hist[sb][d], 1u);
+                    else atomicAdd(&hist[(size_t)d * sort_G + sb0 + sb], 1u);
+                }
+            }
+            off += v[k];
+        }
+        base += total;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kCompactSpan * kRadix; k += kScanThreads) {
+        const uint32_t c = (&s_hist[0][0])[k];
+        const uint32_t sb = sb0 + (uint32_t)(k / kRadix), d = (uint32_t)(k % kRadix);
+        if (c) atomicAdd(&hist[(size_t)d * sort_G + sb], c);
     }
 }
 
@@ -244,7 +319,10 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, uint32_t *t
 // row, of the rectangle tiles that its footprint ellipse meets: read from
 // the item's packed row table when it has one (at most kTabRows rows),
 // else recomputed from the stored ellipse, 32 rows at a time by the whole
-// warp, for one such item after another.
+// warp, for one such item after another.  The kernel also counts the
+// first digit pass of the tile sort that follows (hist, zeroed by the
+// scan before it): each chunk's outputs are contiguous, so their counts
+// are summed in shared memory per sort block and added with atomics.
 __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *__restrict__ vis_off,
                                                               const uint32_t *__restrict__ vis_cnt,
                                                               const uint32_t *__restrict__ chunk_start,
@@ -254,21 +332,28 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
                                                               int tile_h, const uint32_t *__restrict__ sgid,
                                                               const ViewDesc *views, int nv, const uint32_t *d_m,
                                                               const uint32_t *d_k, uint32_t capacity,
-                                                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                                              uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                              uint32_t *__restrict__ hist, int sort_G,
+                                                              uint32_t sort_tile) {
     pdl_enter();
     constexpr int kPer = kEmitChunk / kEmitThreads;  // slots per thread in the scan
     __shared__ uint32_t s_item[kEmitChunk];
     __shared__ uint32_t s_warp[kEmitThreads / 32];
+    __shared__ uint32_t s_hist[kCompactSpan][kRadix];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t M = *d_m;
     const uint32_t K = min(*d_k, capacity);
     const uint32_t nchunks = (K + kEmitChunk - 1) / kEmitChunk;
+    // the tile sort's partition of the K pairs (its segment of whole tiles)
+    const uint32_t seg = max(((K + sort_G - 1) / sort_G + sort_tile - 1) / sort_tile * sort_tile, 1u);
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const uint32_t j0 = c * kEmitChunk;
         const uint32_t m_lo = chunk_start[c];
         const uint32_t m_hi = (c + 1 < nchunks) ? chunk_start[c + 1] : M - 1;
+        const uint32_t sb0 = j0 / seg;  // first sort block of the chunk's outputs
         __syncthreads();
         for (int q = threadIdx.x; q < (int)kEmitChunk; q += kEmitThreads) s_item[q] = 0u;
+        for (int q = threadIdx.x; q < kCompactSpan * kRadix; q += kEmitThreads) (&s_hist[0][0])[q] = 0u;
         __syncthreads();
         // marks: slot 0 holds the item containing j0 (chunk_start); a
         // non-empty item starting inside the chunk marks its first slot
@@ -377,9 +462,18 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
             }
             if (valid) {
                 const int view = nv == 1 ? 0 : view_of_item(views, nv, sgid[m]);
-                keys[j] = views[view].tile_base + ty * (uint32_t)views[view].tiles_x + tx;
+                const uint32_t key = views[view].tile_base + ty * (uint32_t)views[view].tiles_x + tx;
+                keys[j] = key;
                 vals[j] = m;
+                const uint32_t d = key & (kRadix - 1u), sb = j / seg - sb0;
+                if (sb < (uint32_t)kCompactSpan) atomicAdd(&s_hist[sb][d], 1u);
+                else atomicAdd(&hist[(size_t)d * sort_G + sb0 + sb], 1u);
             }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < kCompactSpan * kRadix; q += kEmitThreads) {
+            const uint32_t cnt = (&s_hist[0][0])[q];
+            if (cnt) atomicAdd(&hist[(size_t)(q % kRadix) * sort_G + sb0 + (uint32_t)(q / kRadix)], cnt);
         }
     }
 }
@@ -539,38 +633,43 @@ static_assert(kSortTempBytes >= sizeof(uint32_t) * ((size_t)kRadix * kMaxSortBlo
               "sort scratch layout");
 size_t sort_temp_bytes() { return kSortTempBytes; }
 
-void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, void *temp, cudaStream_t s) {
+void compact_visible(const Params &p, uint32_t *keys_out, uint32_t *vals_out, uint32_t *inv, void *temp,
+                     cudaStream_t s) {
     TempLayout t = temp_layout(temp);
-    CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, p.n_items};
+    CompactF f{p.item_cnt, p.item_zkey, keys_out, vals_out, inv, p.n_items};
     const int G = scan_blocks(p.n_items);
+    // the depth sort's partition (radix_sort_pairs with capacity n_items)
+    const int sort_items = p.n_items <= kSmallSort ? kSmallItems : kSortItems;
+    const int sort_G = sort_blocks(p.n_items, kSortThreads * sort_items);
     note_launch();
-    pdl_launch(k_scan_reduce<CompactF>, G, kScanThreads, 0, s, f, t.partials);
+    pdl_launch(k_scan_reduce<CompactF>, G, kScanThreads, 0, s, f, t.partials, t.hist, (uint32_t)(kRadix * sort_G));
     note_launch();
     pdl_launch(k_scan_partials, 1, 1024, 0, s, t.partials, G, &p.counters[0], 0xffffffffu, nullptr);
     note_launch();
-    pdl_launch(k_scan_apply<CompactF>, G, kScanThreads, 0, s, f, t.partials);
+    pdl_launch(k_compact_apply, G, kScanThreads, 0, s, f, (const uint32_t *)t.partials,
+               (const uint32_t *)&p.counters[0], t.hist, sort_G, (uint32_t)(kSortThreads * sort_items));
 }
 
 template <int ITEMS>
 void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_count,
                   uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt,
-                  uint32_t *inv_out);
+                  uint32_t *inv_out, bool first_hist);
 
 void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *d_count, uint32_t capacity, int begin_bit, int end_bit, void *temp,
-                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out) {
+                      cudaStream_t s, bool *result_in_alt, uint32_t *inv_out, bool first_hist) {
     if (capacity <= kSmallSort)
         radix_passes<kSmallItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
-                                  result_in_alt, inv_out);
+                                  result_in_alt, inv_out, first_hist);
     else
         radix_passes<kSortItems>(keys, vals, keys_alt, vals_alt, d_count, capacity, begin_bit, end_bit, temp, s,
-                                 result_in_alt, inv_out);
+                                 result_in_alt, inv_out, first_hist);
 }
 
 template <int ITEMS>
 void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const uint32_t *d_count,
                   uint32_t capacity, int begin_bit, int end_bit, void *temp, cudaStream_t s, bool *result_in_alt,
-                  uint32_t *inv_out) {
+                  uint32_t *inv_out, bool first_hist) {
     TempLayout t = temp_layout(temp);
     const int G = sort_blocks(capacity, kSortThreads * ITEMS);
     bool alt = false;
@@ -581,8 +680,10 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
         const uint32_t *vi = alt ? vals_alt : vals;
         uint32_t *ko = alt ? keys : keys_alt;
         uint32_t *vo = alt ? vals : vals_alt;
-        note_launch();
-        pdl_launch(k_radix_upsweep<ITEMS>, G, kSortThreads, 0, s, ki, d_count, capacity, b, mask, t.hist);
+        if (!(first_hist && b == begin_bit)) {  // else counted by the producer of the keys
+            note_launch();
+            pdl_launch(k_radix_upsweep<ITEMS>, G, kSortThreads, 0, s, ki, d_count, capacity, b, mask, t.hist);
+        }
         note_launch();
         pdl_launch(k_radix_scan, kRadix, 1024, 0, s, t.hist, t.totals, G);
         note_launch();
@@ -612,8 +713,11 @@ void scan_count_pairs(const Params &p, void *temp, cudaStream_t s) {
     TempLayout t = temp_layout(temp);
     EmitF f{&p.counters[0], p.vis_cnt, p.vis_off, p.chunk_start, p.pair_capacity};
     const int G = scan_blocks(p.n_items);
+    // the tile ranges are zeroed here for k_ranges, which writes only the
+    // non-empty tiles' (no memset node in the launch sequence)
     note_launch();
-    pdl_launch(k_scan_reduce<EmitF>, G, kScanThreads, 0, s, f, t.partials);
+    pdl_launch(k_scan_reduce<EmitF>, G, kScanThreads, 0, s, f, t.partials, reinterpret_cast<uint32_t *>(p.ranges),
+               (uint32_t)(2 * p.total_tiles));
     note_launch();
     pdl_launch(k_scan_partials, 1, 1024, 0, s, t.partials, G, &p.counters[1], p.pair_capacity, &p.counters[2]);
 }
@@ -624,8 +728,13 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
     TempLayout t = temp_layout(temp);
     EmitF f{&p.counters[0], p.vis_cnt, p.vis_off, p.chunk_start, p.pair_capacity};
     const int G = scan_blocks(p.n_items);
+    // the tile sort's partition (radix_sort_pairs with capacity pair_capacity);
+    // its first histogram is zeroed here and counted by the expansion
+    const int sort_items = p.pair_capacity <= kSmallSort ? kSmallItems : kSortItems;
+    const int sort_G = sort_blocks(p.pair_capacity, kSortThreads * sort_items);
     note_launch();
-    pdl_launch(k_scan_apply<EmitF>, G, kScanThreads, 0, s, f, t.partials);
+    pdl_launch(k_scan_apply<EmitF>, G, kScanThreads, 0, s, f, (const uint32_t *)t.partials, t.hist,
+               (uint32_t)(kRadix * sort_G));
     uint32_t grid = (uint32_t)((p.pair_capacity + kEmitChunk - 1) / kEmitChunk);
     if (grid < 1) grid = 1;
     if (grid > (uint32_t)(8 * device_sm_count())) grid = 8 * device_sm_count();
@@ -634,7 +743,7 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
                                                  p.tile_w, p.tile_h,
                                                  p.sgid, p.views, p.n_views,
                                                  &p.counters[0], &p.counters[1], p.pair_capacity, p.pair_keys,
-                                                 p.pair_vals);
+                                                 p.pair_vals, t.hist, sort_G, (uint32_t)(kSortThreads * sort_items));
 }
 
 // Tile order for the compositor: heaviest lists first (64 log-spaced
@@ -669,8 +778,8 @@ void launch_tile_order(const Params &p, cudaStream_t s) {
     pdl_launch(k_tile_order, 1, 1024, 0, s, p.ranges, p.total_tiles, p.tile_order);
 }
 
+// ranges: zeroed by the pair count scan (scan_count_pairs)
 void launch_ranges(const Params &p, cudaStream_t s) {
-    cudaMemsetAsync(p.ranges, 0, sizeof(uint2) * (size_t)p.total_tiles, s);
     note_launch();
     pdl_launch(k_ranges, 8 * device_sm_count(), 256, 0, s, p.pair_keys, &p.counters[1], p.pair_capacity, p.ranges);
 }
