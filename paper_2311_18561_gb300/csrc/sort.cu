@@ -350,10 +350,13 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
         const uint32_t j0 = c * kEmitChunk;
         const uint32_t m_lo = chunk_start[c];
         const uint32_t m_hi = (c + 1 < nchunks) ? chunk_start[c + 1] : M - 1;
-        const uint32_t sb0 = j0 / seg;  // first sort block of the chunk's outputs
+        // sort blocks of the chunk's outputs: sb0 .. sb0 + nsb - 1 counted in
+        // shared memory (any beyond kCompactSpan straight into hist)
+        const uint32_t sb0 = j0 / seg;
+        const int nsb = (int)min((min(j0 + kEmitChunk, K) - 1) / seg - sb0 + 1, (uint32_t)kCompactSpan);
         __syncthreads();
         for (int q = threadIdx.x; q < (int)kEmitChunk; q += kEmitThreads) s_item[q] = 0u;
-        for (int q = threadIdx.x; q < kCompactSpan * kRadix; q += kEmitThreads) (&s_hist[0][0])[q] = 0u;
+        for (int q = threadIdx.x; q < nsb * kRadix; q += kEmitThreads) (&s_hist[0][0])[q] = 0u;
         __syncthreads();
         // marks: slot 0 holds the item containing j0 (chunk_start); a
         // non-empty item starting inside the chunk marks its first slot
@@ -466,12 +469,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_expand_pairs(const uint32_t *_
                 keys[j] = key;
                 vals[j] = m;
                 const uint32_t d = key & (kRadix - 1u), sb = j / seg - sb0;
-                if (sb < (uint32_t)kCompactSpan) atomicAdd(&s_hist[sb][d], 1u);
+                if (sb < (uint32_t)nsb) atomicAdd(&s_hist[sb][d], 1u);
                 else atomicAdd(&hist[(size_t)d * sort_G + sb0 + sb], 1u);
             }
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < kCompactSpan * kRadix; q += kEmitThreads) {
+        for (int q = threadIdx.x; q < nsb * kRadix; q += kEmitThreads) {
             const uint32_t cnt = (&s_hist[0][0])[q];
             if (cnt) atomicAdd(&hist[(size_t)(q % kRadix) * sort_G + sb0 + (uint32_t)(q / kRadix)], cnt);
         }
