@@ -261,8 +261,11 @@ pvg_status_t pvg_render_fwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_
  * may be captured when the context was created with sync_sizes = 0 and the
  * same call (same sizes, same frame) has run once uncaptured, so that no
  * buffer has to grow; otherwise PVG_ERR_INVALID.  The view descriptors are
- * copied from pinned staging owned by the frame: a replayed graph renders
- * the cameras given at capture time. */
+ * copied from pinned staging owned by the frame, a copy per capture that
+ * nothing writes afterwards: a replayed graph renders the cameras and into
+ * the images given at capture time, whatever later calls or captures on the
+ * frame use (graphs of one frame share its device state, so they replay one
+ * after another).  A graph is valid while its frame lives. */
 pvg_status_t pvg_render_fwd_multi(pvg_ctx_t *ctx, const pvg_scene_t *scenes, const pvg_camera_t *cams,
                                   int32_t n_views, const pvg_image_t *out, pvg_frame_t *frame, void *stream);
 

@@ -426,37 +426,71 @@ static pvg_status_t build_views(const pvg_ctx *x, const pvg_scene_t *scenes, int
 
 // Copies the view descriptors to the device through pinned staging owned
 // by `stage` (so that the copy can be captured in a CUDA graph).  Outside
-// capture, waits for the previous copy from the same staging first.
+// capture, waits for the previous copy from the same staging first.  A
+// captured copy reads its source at every replay, so each capture stages
+// into a pinned buffer of its own that nothing writes afterwards: later
+// uncaptured calls on the frame and later captures (other cameras or
+// output images) do not change what an earlier graph renders.  An
+// uncaptured call keeps one spare buffer of its size ready, which the next
+// capture takes (a capture must follow an uncaptured call of the same
+// size); the taken buffers (a few hundred bytes per view) are freed with
+// the frame.
 struct ViewStage {
-    ViewDesc *host = nullptr;  // pinned
+    ViewDesc *host = nullptr;  // pinned, uncaptured calls
     size_t cap = 0;
+    ViewDesc *spare = nullptr;  // pinned, for the next capture
+    size_t spare_cap = 0;
+    std::vector<ViewDesc *> captured;  // pinned, one per capture taken so far
     DevBuf dev;
     cudaEvent_t done = nullptr;
     bool pending = false;
 };
 
+static pvg_status_t pinned_views(ViewDesc **p, size_t n) {
+    if (cudaMallocHost(p, sizeof(ViewDesc) * n) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return PVG_ERR_OOM;
+    }
+    return PVG_OK;
+}
+
 static pvg_status_t stage_views(ViewStage &st, const std::vector<ViewDesc> &views, cudaStream_t s,
                                 bool capturing) {
     const size_t n = views.size();
-    if (st.pending && !capturing) {
-        PVG_CUDA(cudaEventSynchronize(st.done));
-        st.pending = false;
-    }
-    if (st.cap < n) {
-        if (capturing) return PVG_ERR_INVALID;  // no allocation while capturing
-        if (st.host) cudaFreeHost(st.host);
-        st.host = nullptr;
-        st.cap = 0;
-        if (cudaMallocHost(&st.host, sizeof(ViewDesc) * n) != cudaSuccess) {
-            cudaGetLastError();
-            return PVG_ERR_OOM;
+    const size_t bytes = sizeof(ViewDesc) * n;
+    ViewDesc *src;
+    if (capturing) {  // no allocation while capturing
+        if (!st.spare || st.spare_cap < n || st.dev.bytes < bytes || !st.done) return PVG_ERR_INVALID;
+        src = st.spare;
+        st.captured.push_back(st.spare);
+        st.spare = nullptr;
+        st.spare_cap = 0;
+    } else {
+        if (st.pending) {
+            PVG_CUDA(cudaEventSynchronize(st.done));
+            st.pending = false;
         }
-        st.cap = n;
+        if (st.cap < n) {
+            if (st.host) cudaFreeHost(st.host);
+            st.host = nullptr;
+            st.cap = 0;
+            PVG_TRY(pinned_views(&st.host, n));
+            st.cap = n;
+        }
+        if (st.spare_cap < n) {
+            if (st.spare) cudaFreeHost(st.spare);
+            st.spare = nullptr;
+            st.spare_cap = 0;
+            PVG_TRY(pinned_views(&st.spare, n));
+            st.spare_cap = n;
+        }
+        PVG_TRY(ensure(st.dev, bytes));
+        if (!st.done) PVG_CUDA(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming));
+        src = st.host;
     }
-    PVG_TRY(ensure(st.dev, sizeof(ViewDesc) * n));
-    if (!st.done) PVG_CUDA(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming));
-    std::memcpy(st.host, views.data(), sizeof(ViewDesc) * n);
-    PVG_CUDA(cudaMemcpyAsync(st.dev.p, st.host, sizeof(ViewDesc) * n, cudaMemcpyHostToDevice, s));
+    std::memcpy(src, views.data(), bytes);
+    PVG_CUDA(cudaMemcpyAsync(st.dev.p, src, bytes, cudaMemcpyHostToDevice, s));
     if (!capturing) {
         PVG_CUDA(cudaEventRecord(st.done, s));
         st.pending = true;
@@ -476,6 +510,8 @@ void free_stage_ptr(ViewStage *st) {
 static void free_stage(ViewStage &st) {
     if (st.pending) cudaEventSynchronize(st.done);
     if (st.host) cudaFreeHost(st.host);
+    if (st.spare) cudaFreeHost(st.spare);
+    for (ViewDesc *c : st.captured) cudaFreeHost(c);
     if (st.done) cudaEventDestroy(st.done);
     release(st.dev);
     st = ViewStage();

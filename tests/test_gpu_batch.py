@@ -110,3 +110,40 @@ def test_multi_scene_call_equals_per_scene_calls():
         one = r.forward(scenes[which[v]], [cam])[0]
         for k in ("rgb", "depth", "alpha"):
             assert torch.equal(many[v][k], one[k]), (v, k)
+
+
+def test_graph_keeps_its_view_descriptors_after_later_calls_on_the_frame():
+    """A captured forward replays with the cameras and images of its
+    capture after a later capture and a later uncaptured call on the same
+    frame with other cameras and images (each capture keeps its own copy of
+    the view descriptors)."""
+    scene = synth.make_urban_scene(40_000, seed=8)
+    st = R.scene_to_device(scene)
+    cams_a = _cams()[:2]
+    cams_b = [synth.street_camera(0.7, 320, 200, lateral=-1.0), synth.street_camera(0.1, 248, 75, fx=144.0)]
+    r = R.Renderer(sync_sizes=False, pair_capacity=1 << 22)
+    fr = R.Frame()
+    outs_a, outs_b, outs_c = r.alloc_images(cams_a), r.alloc_images(cams_b), r.alloc_images(cams_b)
+    graphs = []
+    for cams, outs in ((cams_a, outs_a), (cams_b, outs_b)):
+        r.forward(st, cams, outs=outs, frame=fr)  # uncaptured first: buffers at their final sizes
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            r.forward(st, cams, outs=outs, frame=fr)
+        graphs.append(g)
+    ref_a = [o["rgb"].clone() for o in outs_a]
+    ref_b = [o["rgb"].clone() for o in outs_b]
+    for o in outs_a + outs_b:
+        o["rgb"].zero_()
+    r.forward(st, cams_b, outs=outs_c, frame=fr)
+    graphs[1].replay()
+    graphs[0].replay()
+    torch.cuda.synchronize()
+    for o, ref in zip(outs_a, ref_a):
+        assert torch.equal(o["rgb"], ref)
+    for o, ref in zip(outs_b, ref_b):
+        assert torch.equal(o["rgb"], ref)
+    assert not torch.equal(ref_a[0], ref_b[0])
+    r.close()
+    fr.close()

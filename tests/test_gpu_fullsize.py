@@ -63,6 +63,37 @@ def test_urban_frame_sampled_pixels_match_oracle(urban, cfg):
     fr.close()
 
 
+def test_urban_frame_wide_sort_paths_render_identically(urban):
+    """The sorts take 16 keys per thread above 4M keys, with their first
+    digit histogram counted by the kernel that writes the keys (the
+    compaction, the pair expansion).  The urban frame rendered with an 8M
+    pair capacity (the tile sort's wide path) and as three identical views
+    in one call (4.5M items: the depth sort's wide path) must give the
+    single-view images bit for bit (the per-tile lists are the same)."""
+    scene, cam, _, _ = urban
+    st = R.scene_to_device(scene)
+    r = R.Renderer(tile=(32, 32), pixels_per_thread=4)
+    fr = R.Frame()
+    ref = r.forward(st, [cam], frame=fr)[0]
+    m, k, ov = fr.stats()
+    assert ov == 0 and k < (4 << 20) < 8_000_000
+    wide = R.Renderer(tile=(32, 32), pixels_per_thread=4, sync_sizes=False, pair_capacity=8_000_000)
+    fr2 = R.Frame()
+    out = wide.forward(st, [cam], frame=fr2)[0]
+    m2, k2, ov2 = fr2.stats()
+    assert (m2, k2, ov2) == (m, k, 0)
+    fr3 = R.Frame()
+    outs = r.forward(st, [cam, cam, cam], frame=fr3)
+    m3, k3, ov3 = fr3.stats()
+    assert (m3, k3, ov3) == (3 * m, 3 * k, 0) and 3 * 1_500_000 > (4 << 20)
+    torch.cuda.synchronize()
+    for got in [out] + list(outs):
+        for key in ("rgb", "depth", "alpha"):
+            assert torch.equal(got[key], ref[key]), key
+    for x in (r, wide, fr, fr2, fr3):
+        x.close()
+
+
 @pytest.fixture(scope="module")
 def training():
     scene = synth.make_urban_scene(1_000_000, seed=0)
