@@ -21,6 +21,7 @@
 // (stability across blocks); inside a block, tiles are taken in order and
 // ranked stably within each warp with __match_any_sync.
 #include <algorithm>
+#include <atomic>
 #include "pvg_internal.cuh"
 
 namespace pvg {
@@ -271,9 +272,16 @@ int scan_blocks(uint32_t capacity) {
     return (int)g;
 }
 
+// CTAs of the 16-keys-per-thread downsweep that fit on one SM (its
+// registers and 43 KB of shared memory), at most 4: the grid of the wide
+// sorts stays one wave, since a block's tiles run one after another and a
+// second wave of blocks would double the pass.  Read once.
+int wide_sort_blocks_per_sm();
+
 int sort_blocks(uint32_t capacity, int tile) {
     uint32_t g = (capacity + tile - 1) / tile;
-    const uint32_t cap = (uint32_t)std::min(kMaxSortBlocks, 4 * device_sm_count());
+    const int per_sm = tile == kSortThreads * kSortItems ? wide_sort_blocks_per_sm() : 4;
+    const uint32_t cap = (uint32_t)std::min(kMaxSortBlocks, per_sm * device_sm_count());
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return (int)g;
@@ -614,6 +622,21 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ key
             if (k[2 + i] != t) ranges[t].y = j0 + i + 1;
         }
     }
+}
+
+int wide_sort_blocks_per_sm() {
+    static std::atomic<int> cached{0};
+    int n = cached.load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_radix_downsweep<kSortItems, 8>, kSortThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        occ = 4;
+    }
+    n = std::max(1, std::min(occ, 4));
+    cached.store(n, std::memory_order_relaxed);
+    return n;
 }
 
 struct TempLayout {
