@@ -39,6 +39,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSmallItems = 4;
 constexpr uint32_t kSmallSort = 4u << 20;
+constexpr uint32_t kLateSortKeys = 12u << 20;  // capacity from which the wide sort reads values late
 constexpr int kRadix = kSortRadix;
 
 constexpr uint32_t kEmitChunk = 2048;  // pair outputs per expansion chunk
@@ -272,15 +273,16 @@ int scan_blocks(uint32_t capacity) {
     return (int)g;
 }
 
-// CTAs of the 16-keys-per-thread downsweep that fit on one SM (its
-// registers and 43 KB of shared memory), at most 4: the grid of the wide
-// sorts stays one wave, since a block's tiles run one after another and a
-// second wave of blocks would double the pass.  Read once.
-int wide_sort_blocks_per_sm();
+// CTAs of the 16-keys-per-thread downsweep (late: the variant with late
+// value reads) that fit on one SM (its registers and 43 KB of shared
+// memory), at most 4: the grid of the wide sorts stays one wave, since a
+// block's tiles run one after another and a second wave of blocks would
+// double the pass.  Read once.
+int wide_sort_blocks_per_sm(bool late);
 
 int sort_blocks(uint32_t capacity, int tile) {
     uint32_t g = (capacity + tile - 1) / tile;
-    const int per_sm = tile == kSortThreads * kSortItems ? wide_sort_blocks_per_sm() : 4;
+    const int per_sm = tile == kSortThreads * kSortItems ? wide_sort_blocks_per_sm(capacity >= kLateSortKeys) : 4;
     const uint32_t cap = (uint32_t)std::min(kMaxSortBlocks, per_sm * device_sm_count());
     if (g < 1) g = 1;
     if (g > cap) g = cap;
@@ -502,16 +504,12 @@ struct SortSmem {
 };
 
 // NB: ballots per key in the ranking (the pass's digit width, or 8)
-template <int ITEMS, int NB>
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
-                                                                  const uint32_t *__restrict__ vals_in,
-                                                                  uint32_t *__restrict__ keys_out,
-                                                                  uint32_t *__restrict__ vals_out,
-                                                                  const uint32_t *d_n, uint32_t cap, int shift,
-                                                                  uint32_t mask, const uint32_t *hist,
-                                                                  const uint32_t *totals,
-                                                                  uint32_t *__restrict__ inv_out) {
-    pdl_enter();
+template <int ITEMS, int NB, bool kLateVals>
+__device__ __forceinline__ void radix_downsweep(const uint32_t *__restrict__ keys_in,
+                                                const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+                                                uint32_t *__restrict__ vals_out, const uint32_t *d_n, uint32_t cap,
+                                                int shift, uint32_t mask, const uint32_t *hist,
+                                                const uint32_t *totals, uint32_t *__restrict__ inv_out) {
     constexpr int kSortTile = kSortThreads * ITEMS;
     __shared__ SortSmem<kSortTile> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -527,14 +525,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
     for (uint32_t t0 = b0; t0 < b1; t0 += kSortTile) {
         for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&S.warp_hist[0][0])[k] = 0;
         __syncthreads();
-        uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
+        // kLateVals: the values are read only when they are placed (below),
+        // so that a thread holds its keys and ranks but not its values
+        // meanwhile (64 registers: four CTAs per SM)
+        uint32_t key[ITEMS], val[kLateVals ? 1 : ITEMS], rank[ITEMS];
         bool valid[ITEMS];
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
             const uint32_t pos = t0 + warp * (32 * ITEMS) + j * 32 + lane;
             valid[j] = pos < b1;
             key[j] = valid[j] ? keys_in[pos] : 0u;
-            val[j] = valid[j] ? vals_in[pos] : 0u;
+            if constexpr (!kLateVals) val[j] = valid[j] ? vals_in[pos] : 0u;
         }
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
@@ -574,7 +575,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
             const uint32_t d = (key[j] >> shift) & mask;
             const uint32_t p = S.tile_start[d] + S.warp_hist[warp][d] + rank[j];
             S.keys[p] = key[j];
-            S.vals[p] = val[j];
+            if constexpr (kLateVals) S.vals[p] = vals_in[t0 + warp * (32 * ITEMS) + j * 32 + lane];
+            else S.vals[p] = val[j];
         }
         __syncthreads();
         const uint32_t nvalid = (b1 - t0) < (uint32_t)kSortTile ? (b1 - t0) : (uint32_t)kSortTile;
@@ -590,6 +592,42 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
         S.base[tid] += tile_cnt;
         __syncthreads();
     }
+}
+
+// The downsweep for ITEMS keys per thread, values read with the keys; and
+// the wide one for long sorts (kLateSortKeys and more), with late value
+// reads, held to 64 registers: four CTAs of 43 KB per SM instead of three.
+// A block of a long sort walks tens of tiles, where the extra CTA per SM
+// pays (64M random keys: 2.09 vs 2.40 ms); with a few tiles per block the
+// late reads' latency shows instead (a 3.3M-pair tile sort: 0.070 vs 0.061
+// ms).
+template <int ITEMS, int NB>
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
+                                                                  const uint32_t *__restrict__ vals_in,
+                                                                  uint32_t *__restrict__ keys_out,
+                                                                  uint32_t *__restrict__ vals_out,
+                                                                  const uint32_t *d_n, uint32_t cap, int shift,
+                                                                  uint32_t mask, const uint32_t *hist,
+                                                                  const uint32_t *totals,
+                                                                  uint32_t *__restrict__ inv_out) {
+    pdl_enter();
+    radix_downsweep<ITEMS, NB, false>(keys_in, vals_in, keys_out, vals_out, d_n, cap, shift, mask, hist, totals,
+                                      inv_out);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kSortThreads, 4) k_radix_downsweep_wide(const uint32_t *__restrict__ keys_in,
+                                                                           const uint32_t *__restrict__ vals_in,
+                                                                           uint32_t *__restrict__ keys_out,
+                                                                           uint32_t *__restrict__ vals_out,
+                                                                           const uint32_t *d_n, uint32_t cap,
+                                                                           int shift, uint32_t mask,
+                                                                           const uint32_t *hist,
+                                                                           const uint32_t *totals,
+                                                                           uint32_t *__restrict__ inv_out) {
+    pdl_enter();
+    radix_downsweep<kSortItems, NB, true>(keys_in, vals_in, keys_out, vals_out, d_n, cap, shift, mask, hist, totals,
+                                          inv_out);
 }
 
 // [start, end) of every tile's run in the sorted keys.  Eight keys per
@@ -624,18 +662,20 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ key
     }
 }
 
-int wide_sort_blocks_per_sm() {
-    static std::atomic<int> cached{0};
-    int n = cached.load(std::memory_order_relaxed);
+int wide_sort_blocks_per_sm(bool late) {
+    static std::atomic<int> cached[2] = {{0}, {0}};
+    int n = cached[late].load(std::memory_order_relaxed);
     if (n > 0) return n;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_radix_downsweep<kSortItems, 8>, kSortThreads, 0) !=
-        cudaSuccess) {
+    const cudaError_t e =
+        late ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_radix_downsweep_wide<8>, kSortThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_radix_downsweep<kSortItems, 8>, kSortThreads, 0);
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        occ = 4;
+        occ = 3;
     }
     n = std::max(1, std::min(occ, 4));
-    cached.store(n, std::memory_order_relaxed);
+    cached[late].store(n, std::memory_order_relaxed);
     return n;
 }
 
@@ -718,8 +758,12 @@ void radix_passes(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *
         // multiple of 8 bits ranks with fewer ballots
 #define PVG_DOWNSWEEP(NBITS)                                                                                    \
     case NBITS:                                                                                                 \
-        pdl_launch(k_radix_downsweep<ITEMS, NBITS>, G, kSortThreads, 0, s, ki, vi, ko, vo, d_count, capacity, b, mask, \
-                                                                   t.hist, t.totals, inv_pass);                \
+        if (ITEMS == kSortItems && capacity >= kLateSortKeys)                                                  \
+            pdl_launch(k_radix_downsweep_wide<NBITS>, G, kSortThreads, 0, s, ki, vi, ko, vo, d_count, capacity, b, \
+                       mask, t.hist, t.totals, inv_pass);                                                       \
+        else                                                                                                    \
+            pdl_launch(k_radix_downsweep<ITEMS, NBITS>, G, kSortThreads, 0, s, ki, vi, ko, vo, d_count, capacity, b, \
+                       mask, t.hist, t.totals, inv_pass);                                                       \
         break;
         switch (nb) {
             PVG_DOWNSWEEP(1) PVG_DOWNSWEEP(2) PVG_DOWNSWEEP(3) PVG_DOWNSWEEP(4)

@@ -64,3 +64,14 @@ def test_sort_tile_keys_full_size(renderer):
     rng = np.random.default_rng(2)
     keys = rng.integers(0, 9600, 12_000_000).astype(np.uint32)
     _check(renderer, keys, np.arange(keys.size, dtype=np.uint32), 0, 14)
+
+
+@pytest.mark.parametrize("n,bits", [(13_000_000, (0, 17)), (20_000_017, (0, 32))])
+def test_sort_long_with_late_value_reads(renderer, n, bits):
+    """Sorts of 12M keys and more run the wide downsweep that reads the
+    values late (four CTAs per SM): tile ids of a 64-view batch (17 bits,
+    many equal keys) and full 32-bit keys with a ragged last tile."""
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 2 ** bits[1], n, dtype=np.uint64).astype(np.uint32)
+    keys[::9] = keys[4]
+    _check(renderer, keys, np.arange(n, dtype=np.uint32), *bits)
