@@ -15,11 +15,15 @@
 // The result is ordered by (tile, depth, gid) -- the per-tile front-to-back
 // lists -- while the wide K-sized sort only moves the tile bits.
 //
-// Partitioning: a fixed grid of G blocks; block b owns the contiguous
-// segment [b*seg, (b+1)*seg) with seg = ceil(n / G) rounded up to the tile
-// size, so a block's output for a digit always precedes block b+1's
-// (stability across blocks); inside a block, tiles are taken in order and
-// ranked stably within each warp with __match_any_sync.
+// Partitioning: a fixed grid of G blocks (one wave: G is the SM count times
+// the CTAs of the pass that fit on an SM, at most 4); block b owns the
+// contiguous segment [b*seg, (b+1)*seg) with seg = ceil(n / G) rounded up
+// to the tile size, so a block's output for a digit always precedes block
+// b+1's (stability across blocks); inside a block, tiles are taken in order
+// and each key is ranked stably within its warp by one ballot per digit
+// bit (the lanes holding the same digit, then those before it).  The first
+// digit pass's histogram can be counted by the kernel that writes the keys
+// (compaction, pair expansion), which saves that pass's upsweep.
 #include <algorithm>
 #include <atomic>
 #include "pvg_internal.cuh"
