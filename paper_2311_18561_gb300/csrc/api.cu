@@ -188,6 +188,8 @@ struct pvg_frame {
     DevBuf pair_vals;           // [K]
     DevBuf ranges;              // [tiles]
     DevBuf tile_order;          // [tiles] compositor launch order
+    DevBuf tile_walk;           // [tiles] largest last-blend position per tile (forward)
+    DevBuf tile_order_bwd;      // [tiles] adjoint launch order (by walk)
     DevBuf pix_T, pix_last;     // [pixels]
     DevBuf pix_neval;           // [pixels]
     DevBuf g2d;                 // [NV * 10] image-space gradients by depth position
@@ -290,7 +292,7 @@ extern "C" void pvg_frame_destroy(pvg_frame_t *f) {
     if (!f) return;
     if (f->stream) cudaStreamSynchronize(f->stream);
     for (DevBuf *b : {&f->counters, &f->sgid, &f->inv, &f->szkey, &f->rec, &f->ell, &f->rowtab, &f->rect, &f->vis_cnt, &f->pair_vals,
-                      &f->ranges, &f->tile_order, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d, &f->gfeat})
+                      &f->ranges, &f->tile_order, &f->tile_walk, &f->tile_order_bwd, &f->pix_T, &f->pix_last, &f->pix_neval, &f->g2d, &f->gfeat})
         release(*b);
     if (f->h_counters) cudaFreeHost(f->h_counters);
     free_stage_ptr(f->stage_fwd);
@@ -564,6 +566,8 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
     PVG_TRY(ensure_c(f->vis_cnt, sizeof(uint32_t) * NV, capturing));
     PVG_TRY(ensure_c(f->ranges, sizeof(uint2) * tiles, capturing));
     PVG_TRY(ensure_c(f->tile_order, sizeof(uint32_t) * tiles, capturing));
+    PVG_TRY(ensure_c(f->tile_walk, sizeof(uint32_t) * tiles, capturing));
+    PVG_TRY(ensure_c(f->tile_order_bwd, sizeof(uint32_t) * tiles, capturing));
     PVG_TRY(ensure_c(f->pix_T, sizeof(float) * pix, capturing));
     PVG_TRY(ensure_c(f->pix_last, sizeof(uint32_t) * pix, capturing));
     PVG_TRY(ensure_c(f->pix_neval, sizeof(uint32_t) * 2 * (size_t)pix, capturing));
@@ -707,6 +711,8 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
     f->pair_capacity = pair_cap;
     p.pair_vals = ptr<uint32_t>(f->pair_vals);
     if (!keep_state) p.pix_T = nullptr;  // inference only: no state for a backward pass
+    // with state: each tile's walk length, from which the adjoint orders its tiles
+    p.tile_walk = keep_state ? ptr<uint32_t>(f->tile_walk) : nullptr;
     tm.begin(PVG_STAGE_COMPOSITE, s);
     launch_composite(p, s);
     if (n_feat) launch_composite_feat(p, s);
@@ -784,6 +790,8 @@ pvg_status_t serve_reserve(pvg_ctx_t *x, pvg_frame_t *f, uint64_t items, uint64_
     PVG_TRY(ensure(f->rect, sizeof(uint2) * items));
     PVG_TRY(ensure(f->ranges, sizeof(uint2) * tiles));
     PVG_TRY(ensure(f->tile_order, sizeof(uint32_t) * tiles));
+    PVG_TRY(ensure(f->tile_walk, sizeof(uint32_t) * tiles));
+    PVG_TRY(ensure(f->tile_order_bwd, sizeof(uint32_t) * tiles));
     PVG_TRY(ensure(f->pix_T, sizeof(float) * pix));
     PVG_TRY(ensure(f->pix_last, sizeof(uint32_t) * pix));
     PVG_TRY(ensure(f->pix_neval, sizeof(uint32_t) * 2 * pix));
@@ -920,8 +928,10 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     const bool timer_on = tm.on;
     if (capturing) tm.on = false;
     tm.begin(PVG_STAGE_COMPOSITE_BWD, s);
-    note_launch();
-    pdl_launch(k_zero_rows, device_sm_count() * 4, 256, 0, s, p.g2d, &p.counters[0], 10);
+    // g2d zeroed, and the adjoint's tiles ordered longest walk first (the
+    // forward recorded each tile's largest last-blend position)
+    launch_bwd_prep(p, ptr<uint32_t>(f->tile_walk), ptr<uint32_t>(f->tile_order_bwd), s);
+    p.tile_order = ptr<uint32_t>(f->tile_order_bwd);
     launch_composite_bwd(p, s);
     if (feat_bwd && f->n_items) {
         note_launch();

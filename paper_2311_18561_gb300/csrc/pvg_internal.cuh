@@ -110,6 +110,7 @@ struct Params {
     uint32_t *pair_vals;     // [K]
     uint2 *ranges;           // [total_tiles]
     uint32_t *tile_order;    // [total_tiles] tiles by decreasing list length (compositor launch order)
+    uint32_t *tile_walk;     // [total_tiles] forward: largest pixel_last of the tile (the adjoint's walk)
     float *pix_T;            // [sum HW]
     uint32_t *pix_last;      // [sum HW] list position after the last blend
     uint32_t *pix_neval;     // [2][sum HW] stats pass: in-footprint entries up to the stop, and blended ones
@@ -476,6 +477,9 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s);
 size_t emit_chunks(uint32_t capacity);
 void launch_ranges(const Params &p, cudaStream_t s);
 void launch_tile_order(const Params &p, cudaStream_t s);
+// the adjoint's first kernel: p.g2d rows of the visible items zeroed, and
+// the adjoint's tile order by walk[tile] (longest first) into order
+void launch_bwd_prep(const Params &p, const uint32_t *walk, uint32_t *order, cudaStream_t s);
 // raster
 bool composite_supported(int tw, int th, int px);
 void launch_composite(const Params &p, cudaStream_t s);

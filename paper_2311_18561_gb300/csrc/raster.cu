@@ -64,6 +64,22 @@ __device__ __forceinline__ void composite_epilogue(const Params &P, const ViewDe
     }
 }
 
+// The tile's largest last-blend position (how far its adjoint walks),
+// by every thread of the CTA once its pixels are written.
+template <int PX>
+__device__ __forceinline__ void tile_walk_record(const Params &P, const uint32_t (&last)[PX]) {
+    __shared__ uint32_t s_walk;
+    uint32_t m = last[0];
+#pragma unroll
+    for (int p = 1; p < PX; p++) m = max(m, last[p]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (threadIdx.x == 0) s_walk = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_walk, m);
+    __syncthreads();
+    if (threadIdx.x == 0) P.tile_walk[P.tile_order ? P.tile_order[blockIdx.x] : blockIdx.x] = s_walk;
+}
+
 // kStats: instead of images, write per pixel the number of list entries
 // whose footprint box contains the pixel, up to and including the one
 // that stopped it (the compositing work E), and the number of those with
@@ -160,6 +176,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite(Params P) {
         }
     } else {
         composite_epilogue<PX>(P, V, G, T, C0, C1, C2, D, O, last);
+        if (P.tile_walk) tile_walk_record<PX>(P, last);
     }
 }
 
@@ -290,6 +307,7 @@ __global__ void __launch_bounds__(TW *TH / PX) k_composite_x2(Params P) {
         Os[2 * q] = O[q].x; Os[2 * q + 1] = O[q].y;
     }
     composite_epilogue<PX>(P, V, G, Ts, C0s, C1s, C2s, Ds, Os, last);
+    if (P.tile_walk) tile_walk_record<PX>(P, last);
 }
 
 template <int TW, int TH, int PX>

@@ -824,15 +824,17 @@ void scan_emit_pairs(const Params &p, void *temp, cudaStream_t s) {
 // length buckets, longest bucket first), so the long tiles start at once
 // and the short ones fill in behind them.  Order within a bucket is left
 // to the atomics (each tile's result does not depend on when it runs).
-__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
-                                                     uint32_t *__restrict__ order) {
-    pdl_enter();
+// walk (optional): order by the tiles' walk lengths instead (the adjoint:
+// each tile's largest last-blend position, which the forward recorded).
+// One block, any multiple of 64 threads.
+__device__ __forceinline__ void tile_order_block(const uint2 *__restrict__ ranges, const uint32_t *walk,
+                                                 uint32_t n_tiles, uint32_t *__restrict__ order) {
     __shared__ uint32_t cnt[64];
     __shared__ uint32_t smem[33];
     if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
     __syncthreads();
     auto bucket = [&](uint32_t t) {
-        const uint32_t len = ranges[t].y - ranges[t].x;
+        const uint32_t len = walk ? walk[t] : ranges[t].y - ranges[t].x;
         const int b = min(63, (int)(log2f((float)len + 1.0f) * 3.0f));
         return 63 - b;  // longest first
     };
@@ -846,10 +848,38 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
     for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&cnt[bucket(t)], 1u)] = t;
 }
 
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                     uint32_t *__restrict__ order) {
+    pdl_enter();
+    tile_order_block(ranges, nullptr, n_tiles, order);
+}
+
+// The adjoint's first kernel: rows [0, *d_m) of a [*, per] array zeroed
+// (the visible items' image-space gradients, which the adjoint accumulates)
+// by all blocks but the last, which orders the tiles by their walk lengths.
+__global__ void __launch_bounds__(256) k_bwd_prep(float *__restrict__ a, const uint32_t *d_m, int per,
+                                                  const uint32_t *walk, uint32_t n_tiles,
+                                                  uint32_t *__restrict__ order) {
+    pdl_enter();
+    if (blockIdx.x == gridDim.x - 1) {
+        tile_order_block(nullptr, walk, n_tiles, order);
+        return;
+    }
+    const size_t n = (size_t)per * *d_m;
+    const size_t stride = (size_t)(gridDim.x - 1) * blockDim.x;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += stride) a[k] = 0.f;
+}
+
 void launch_tile_order(const Params &p, cudaStream_t s) {
     if (p.total_tiles == 0) return;
     note_launch();
     pdl_launch(k_tile_order, 1, 1024, 0, s, p.ranges, p.total_tiles, p.tile_order);
+}
+
+void launch_bwd_prep(const Params &p, const uint32_t *walk, uint32_t *order, cudaStream_t s) {
+    note_launch();
+    pdl_launch(k_bwd_prep, 4 * device_sm_count() + 1, 256, 0, s, p.g2d, (const uint32_t *)&p.counters[0], 10,
+               walk, p.total_tiles, order);
 }
 
 // ranges: zeroed by the pair count scan (scan_count_pairs)
