@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
 // The adjoint's first kernel: rows [0, *d_m) of a [*, per] array zeroed
 // (the visible items' image-space gradients, which the adjoint accumulates)
 // by all blocks but the last, which orders the tiles by their walk lengths.
-__global__ void __launch_bounds__(256) k_bwd_prep(float *__restrict__ a, const uint32_t *d_m, int per,
+__global__ void __launch_bounds__(1024) k_bwd_prep(float *__restrict__ a, const uint32_t *d_m, int per,
                                                   const uint32_t *walk, uint32_t n_tiles,
                                                   uint32_t *__restrict__ order) {
     pdl_enter();
@@ -878,8 +878,8 @@ void launch_tile_order(const Params &p, cudaStream_t s) {
 
 void launch_bwd_prep(const Params &p, const uint32_t *walk, uint32_t *order, cudaStream_t s) {
     note_launch();
-    pdl_launch(k_bwd_prep, 4 * device_sm_count() + 1, 256, 0, s, p.g2d, (const uint32_t *)&p.counters[0], 10,
-               walk, p.total_tiles, order);
+    pdl_launch(k_bwd_prep, device_sm_count() + 1, 1024, 0, s, p.g2d, (const uint32_t *)&p.counters[0], 10, walk,
+               p.total_tiles, order);
 }
 
 // ranges: zeroed by the pair count scan (scan_count_pairs)
