@@ -272,7 +272,10 @@ pvg_status_t pvg_render_fwd_multi(pvg_ctx_t *ctx, const pvg_scene_t *scenes, con
 /* Adjoint of the forward pass saved in `frame` (which must have been
  * rendered from the same scene values and cameras): zeroes `grads` and
  * writes dL/dparam for L = sum over views of <dL[v], image[v]>.
- * dL is a host array of n_views device-gradient descriptors. */
+ * dL is a host array of n_views device-gradient descriptors.  `frame`
+ * must be the frame the forward pass was given: with NULL, or a frame
+ * whose last forward kept no state (a served frame), the call returns
+ * PVG_ERR_INVALID and enqueues nothing. */
 pvg_status_t pvg_render_bwd(pvg_ctx_t *ctx, const pvg_scene_t *scene, const pvg_camera_t *cams,
                             int32_t n_views, pvg_frame_t *frame, const pvg_image_grad_t *dL,
                             const pvg_scene_grad_t *grads, void *stream);

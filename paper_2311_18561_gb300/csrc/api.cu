@@ -204,6 +204,7 @@ struct pvg_frame {
     float dilation = 0.f;
     cudaStream_t stream = nullptr;
     bool valid = false;
+    bool has_state = false;     // the last forward kept what the backward needs
     uint32_t *h_counters = nullptr;  // pinned
 };
 
@@ -597,6 +598,7 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
     f->dilation = x->cfg.dilation;
     f->stream = s;
     f->valid = false;
+    f->has_state = false;
     f->feat_mask = fmask;
     f->n_feat = n_feat;
     f->n_sem = nsem;
@@ -720,6 +722,7 @@ static pvg_status_t enqueue_forward(pvg_ctx_t *x, pvg_frame *f, std::vector<View
     tm.on = timer_on;
     PVG_CUDA(cudaGetLastError());
     f->valid = true;
+    f->has_state = keep_state;
     return PVG_OK;
 }
 
@@ -845,7 +848,9 @@ extern "C" pvg_status_t pvg_render_bwd(pvg_ctx_t *x, const pvg_scene_t *scene, c
     if (!x || !dL || !grads) return PVG_ERR_INVALID;
     PVG_TRY(validate_scene(scene));
     pvg_frame *f = frame ? frame : x->own_frame;
-    if (!f->valid || !f->one_scene || f->n != scene->n || f->sh_degree != scene->sh_degree ||
+    // the forward must have kept its state (a frame passed to it; NULL
+    // rendered into the context's own frame for inference only)
+    if (!f->valid || !f->has_state || !f->one_scene || f->n != scene->n || f->sh_degree != scene->sh_degree ||
         (int)f->views.size() != n_views)
         return PVG_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream_;

@@ -61,6 +61,25 @@ def test_bad_arguments_are_rejected():
     assert torch.isfinite(out["rgb"]).all()
 
 
+def test_backward_without_saved_state_is_rejected():
+    st = R.scene_to_device(synth.make_plain_scene(seed=0, n=200))
+    cam = synth.plain_camera(64, 48)
+    r = R.Renderer()
+    r.forward(st, [cam])  # inference only: no frame, no state for a backward pass
+
+    class _NoFrame:
+        handle = None
+
+    dl = [dict(rgb=torch.ones(3, 48, 64, device="cuda"))]
+    assert _status(lambda: r.backward(st, [cam], _NoFrame(), dl)) == INVALID
+    # with a frame the same call works
+    fr = R.Frame()
+    r.forward(st, [cam], frame=fr)
+    g = r.backward(st, [cam], fr, dl)
+    torch.cuda.synchronize()
+    assert torch.isfinite(g["mu"]).all() and g["mu"].abs().sum().item() > 0
+
+
 def test_empty_scene_renders_the_background():
     scene = {k: v[:0] for k, v in synth.make_plain_scene(seed=0, n=4).items()}
     st = R.scene_to_device(scene)
