@@ -10,12 +10,13 @@
   hardly reach: tile lists of thousands of entries, the heaviest-first tile
   order, the 16-keys-per-thread path of the tile sort and float atomics
   over thousands of tiles per Gaussian in the adjoint.
-* The training frame (1M Gaussians, SH-3, 1242x375, f = 720) backward with
-  dL/dimage non-zero on 2,000 sampled pixels only (the oracle's pixels the
-  oracle does not flag), against the oracle's reverse mode restricted to
-  those pixels: all nine parameter groups at the gradient tolerance
-  (Sec. 3.2, Eq. 8: the render function is differentiable), for a colour
-  loss (the training step's L1 path) and with depth and opacity weights.
+* The training frame (1M Gaussians, SH-3, 1242x375, f = 720) and the urban
+  frame (in the benchmarked 32x32, 4-pixel configuration) backward with
+  dL/dimage non-zero on 2,000 sampled pixels only (pixels the oracle does
+  not flag), against the oracle's reverse mode restricted to those pixels:
+  all nine parameter groups at the gradient tolerance (Sec. 3.2, Eq. 8: the
+  render function is differentiable), for a colour loss (the training
+  step's L1 path) and with depth and opacity weights.
 """
 import numpy as np
 import pytest
@@ -109,10 +110,9 @@ def training():
     return scene, cam, pix
 
 
-@pytest.mark.parametrize("cfg", [(16, 8, 1), (32, 32, 4)])
-@pytest.mark.parametrize("colour_only", [True, False])
-def test_training_frame_backward_on_sampled_pixels(training, cfg, colour_only):
-    scene, cam, pix = training
+def _sampled_backward(scene, cam, pix, cfg, colour_only):
+    """dL/dimage non-zero on the sampled pixels only; the nine gradient
+    groups against the oracle's reverse mode restricted to those pixels."""
     W, H = cam["width"], cam["height"]
     P = pix.shape[0]
     rng = np.random.default_rng(4)
@@ -146,3 +146,26 @@ def test_training_frame_backward_on_sampled_pixels(training, cfg, colour_only):
     _compare_grads(grads, ref)
     r.close()
     fr.close()
+
+
+@pytest.mark.parametrize("cfg", [(16, 8, 1), (32, 32, 4)])
+@pytest.mark.parametrize("colour_only", [True, False])
+def test_training_frame_backward_on_sampled_pixels(training, cfg, colour_only):
+    scene, cam, pix = training
+    _sampled_backward(scene, cam, pix, cfg, colour_only)
+
+
+@pytest.mark.parametrize("colour_only", [True, False])
+def test_urban_frame_backward_on_sampled_pixels(urban, colour_only):
+    """The benchmarked step's backward: the urban frame in the autotuner's
+    configuration (32x32 tiles, 4 pixels per thread), colour-only (the L1
+    path the benchmark times) and with depth and opacity weights, on 2,000
+    of the sampled pixels where the oracle flags no gate decision."""
+    scene, cam, pix, ref = urban
+    pix = pix[ref["flag"] == 0]
+    # distinct pixels: the oracle sums over the list, the image holds one
+    # weight per pixel, so a repeated pixel would count twice on one side
+    _, first = np.unique(pix[:, 1] * cam["width"] + pix[:, 0], return_index=True)
+    pix = pix[np.sort(first)][:2000]
+    assert pix.shape[0] == 2000
+    _sampled_backward(scene, cam, pix, (32, 32, 4), colour_only)
