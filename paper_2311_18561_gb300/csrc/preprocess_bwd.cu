@@ -381,14 +381,30 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     const uint32_t lmask = (1u << lane) - 1u;
     const uint32_t n_chunks = (n + kWarpChunk - 1) / kWarpChunk;
     const SmallGrads zero{};
-    for (uint32_t c = blockIdx.x * 8u + warp; c < n_chunks; c += gridDim.x * 8u) {
+    // the inverse map of a warp's next chunk is loaded while it works on the
+    // current one (its depth positions start the chunk's dependent loads)
+    const uint32_t stride = gridDim.x * 8u;
+    uint32_t m_next[kWarpPer];
+    auto load_inv = [&](uint32_t c, uint32_t (&m)[kWarpPer]) {
+#pragma unroll
+        for (int q = 0; q < kWarpPer; q++) {
+            const uint32_t g = c * kWarpChunk + 32 * q + lane;
+            m[q] = g < n ? P.inv[g] : 0xffffffffu;
+        }
+    };
+    load_inv(blockIdx.x * 8u + warp, m_next);
+    for (uint32_t c = blockIdx.x * 8u + warp; c < n_chunks; c += stride) {
         const uint32_t base = c * kWarpChunk;
+        uint32_t m_cur[kWarpPer];
+#pragma unroll
+        for (int q = 0; q < kWarpPer; q++) m_cur[q] = m_next[q];
+        if (c + stride < n_chunks) load_inv(c + stride, m_next);
         uint64_t vis = 0;  // bit k: item base + k is visible
         uint32_t nvis = 0;
 #pragma unroll
         for (int q = 0; q < kWarpPer; q++) {
             const uint32_t g = base + 32 * q + lane;
-            const uint32_t m = g < n ? P.inv[g] : 0xffffffffu;
+            const uint32_t m = m_cur[q];
             const bool v = m != 0xffffffffu;
             const uint32_t b = __ballot_sync(0xffffffffu, v);
             vis |= (uint64_t)b << (32 * q);
