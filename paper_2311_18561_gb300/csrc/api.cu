@@ -178,7 +178,7 @@ ViewStage *new_stage();
 struct pvg_frame {
     int device = -1;
     ViewStage *stage_fwd = nullptr, *stage_bwd = nullptr;
-    DevBuf counters;            // u32 [4]: M, K, overflow
+    DevBuf counters;            // u32 [4]: M, K, overflow, the per-item adjoint's chunk ticket
     DevBuf sgid, szkey;         // [NV]
     DevBuf inv;                 // [NV] depth position per item
     DevBuf rec;                 // [NV * 3] float4

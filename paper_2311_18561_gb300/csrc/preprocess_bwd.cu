@@ -381,9 +381,12 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
     const uint32_t lmask = (1u << lane) - 1u;
     const uint32_t n_chunks = (n + kWarpChunk - 1) / kWarpChunk;
     const SmallGrads zero{};
-    // the inverse map of a warp's next chunk is loaded while it works on the
-    // current one (its depth positions start the chunk's dependent loads)
-    const uint32_t stride = gridDim.x * 8u;
+    // A warp's first chunk is blockIdx.x * 8 + warp; after that it takes
+    // the next untaken one from a ticket (counters[3], reset by the
+    // adjoint's first kernel), so that warps whose chunks hold fewer visible
+    // items take more of them.  The inverse map of a warp's next chunk is
+    // loaded while it works on the current one (its depth positions start
+    // the chunk's dependent loads).
     uint32_t m_next[kWarpPer];
     auto load_inv = [&](uint32_t c, uint32_t (&m)[kWarpPer]) {
 #pragma unroll
@@ -392,13 +395,20 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
             m[q] = g < n ? P.inv[g] : 0xffffffffu;
         }
     };
-    load_inv(blockIdx.x * 8u + warp, m_next);
-    for (uint32_t c = blockIdx.x * 8u + warp; c < n_chunks; c += stride) {
+    auto take = [&]() {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&P.counters[3], 1u);
+        return __shfl_sync(0xffffffffu, t, 0) + gridDim.x * 8u;
+    };
+    uint32_t c = blockIdx.x * 8u + warp;
+    if (c < n_chunks) load_inv(c, m_next);
+    while (c < n_chunks) {
         const uint32_t base = c * kWarpChunk;
         uint32_t m_cur[kWarpPer];
 #pragma unroll
         for (int q = 0; q < kWarpPer; q++) m_cur[q] = m_next[q];
-        if (c + stride < n_chunks) load_inv(c + stride, m_next);
+        const uint32_t c_next = take();
+        if (c_next < n_chunks) load_inv(c_next, m_next);
         uint64_t vis = 0;  // bit k: item base + k is visible
         uint32_t nvis = 0;
 #pragma unroll
@@ -469,6 +479,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(Params P) {
         for (int f = 0; f < 4; f++)
             warp_copy_out(one[f] ? one[f] + base : nullptr, st + kStOne + f * kWarpChunk, cn, lane);
         __syncwarp();  // the next chunk restages
+        c = c_next;
     }
 }
 

@@ -88,7 +88,8 @@ struct Params {
     uint32_t total_tiles;
     uint32_t total_pix;
     uint32_t pair_capacity;
-    // device counters: [0] visible M, [1] pairs K, [2] overflow flag
+    // device counters: [0] visible M, [1] pairs K, [2] overflow flag, [3] the
+    // per-item adjoint's chunk ticket
     uint32_t *counters;
     // per-item scratch
     uint32_t *item_cnt;      // [NV] tiles touched (0 = invisible)

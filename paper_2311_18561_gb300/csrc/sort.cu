@@ -856,12 +856,14 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2 *__restrict__ r
 
 // The adjoint's first kernel: rows [0, *d_m) of a [*, per] array zeroed
 // (the visible items' image-space gradients, which the adjoint accumulates)
-// by all blocks but the last, which orders the tiles by their walk lengths.
+// by all blocks but the last, which orders the tiles by their walk lengths
+// and resets the per-item adjoint's chunk ticket (counters[3]).
 __global__ void __launch_bounds__(1024) k_bwd_prep(float *__restrict__ a, const uint32_t *d_m, int per,
                                                   const uint32_t *walk, uint32_t n_tiles,
-                                                  uint32_t *__restrict__ order) {
+                                                  uint32_t *__restrict__ order, uint32_t *ticket) {
     pdl_enter();
     if (blockIdx.x == gridDim.x - 1) {
+        if (threadIdx.x == 0) *ticket = 0u;  // the per-item adjoint's chunk ticket
         tile_order_block(nullptr, walk, n_tiles, order);
         return;
     }
@@ -879,7 +881,7 @@ void launch_tile_order(const Params &p, cudaStream_t s) {
 void launch_bwd_prep(const Params &p, const uint32_t *walk, uint32_t *order, cudaStream_t s) {
     note_launch();
     pdl_launch(k_bwd_prep, device_sm_count() + 1, 1024, 0, s, p.g2d, (const uint32_t *)&p.counters[0], 10, walk,
-               p.total_tiles, order);
+               p.total_tiles, order, &p.counters[3]);
 }
 
 // ranges: zeroed by the pair count scan (scan_count_pairs)
