@@ -321,12 +321,12 @@ __global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P
 }
 
 // One view: every gradient entry is written once, with no block barrier.
-// A warp takes chunks of kWarpChunk consecutive items (every gridDim.x *
-// 8-th chunk): their visibility by ballot, the visible items compacted onto
-// its lanes, the 17 small gradients of the chunk staged in the warp's
-// shared memory in the global arrays' own layout (zeros for the invisible
-// items) and copied out as float4, so that each 32-byte sector is written
-// whole and no index is divided.  SH-coefficient rows (192 bytes at degree
+// A warp takes chunks of kWarpChunk consecutive items (its first by its
+// index, the others from a ticket): their visibility by ballot, the
+// visible items compacted onto its lanes, the 17 small gradients of the
+// chunk staged in the warp's shared memory in the global arrays' own
+// layout (zeros for the invisible items) and copied out as float4, so that
+// each 32-byte sector is written whole and no index is divided.  SH-coefficient rows (192 bytes at degree
 // 3) are written by the visible item's lane, and zeroed warp-wide as float4
 // for the invisible items.
 constexpr int kWarpChunk = 64;
