@@ -273,7 +273,21 @@ __global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P
     const ViewDesc &V0 = P.views[0];  // every view renders the same scene (gradient pointers too)
     const uint32_t n = V0.n;
     float *col = V0.g_sh ? s_sh + tid : nullptr;
-    for (uint32_t i = blockIdx.x * kViewsThreads + tid; i < n; i += gridDim.x * kViewsThreads) {
+    // a warp's first 32 Gaussians by its index, the next ones from a ticket
+    // (counters[3], reset by the adjoint's first kernel): the Gaussians seen
+    // by more views cost more, and the warps done first take more
+    constexpr uint32_t kWarps = kViewsThreads / 32;
+    const int lane = tid & 31;
+    uint32_t w = blockIdx.x * kWarps + (uint32_t)(tid >> 5);
+    for (;;) {
+        const uint32_t i = w * 32u + (uint32_t)lane;
+        if (w * 32u >= n) break;
+        {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(&P.counters[3], 1u);
+            w = __shfl_sync(0xffffffffu, t, 0) + gridDim.x * kWarps;
+        }
+        if (i >= n) continue;
         SmallGrads acc = SmallGrads{};
         if (col)
 #pragma unroll
