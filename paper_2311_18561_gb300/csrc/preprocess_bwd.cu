@@ -261,7 +261,7 @@ __device__ __forceinline__ bool item_adjoint(const Params &P, const ViewDesc &V,
 // the warp), accumulates the item adjoints over those views -- the 17 small
 // gradients in registers, the SH-coefficient gradients in a column of
 // shared memory -- and writes every gradient entry once: no atomics and no
-// zeroing pass.
+// zeroing pass.  Warps take 32 consecutive Gaussians at a time.
 constexpr int kViewsThreads = 128;
 
 template <int D>
