@@ -340,9 +340,9 @@ __global__ void __launch_bounds__(kViewsThreads) k_preprocess_bwd_views(Params P
 // visible items compacted onto its lanes, the 17 small gradients of the
 // chunk staged in the warp's shared memory in the global arrays' own
 // layout (zeros for the invisible items) and copied out as float4, so that
-// each 32-byte sector is written whole and no index is divided.  SH-coefficient rows (192 bytes at degree
-// 3) are written by the visible item's lane, and zeroed warp-wide as float4
-// for the invisible items.
+// each 32-byte sector is written whole and no index is divided.
+// SH-coefficient rows (192 bytes at degree 3) are written by the visible
+// item's lane, and zeroed warp-wide as float4 for the invisible items.
 constexpr int kWarpChunk = 64;
 constexpr int kWarpPer = kWarpChunk / 32;
 // offsets of the staged fields in a warp's buffer (floats): mu, v, s (3 per
