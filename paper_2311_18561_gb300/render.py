@@ -156,7 +156,10 @@ class Renderer:
 
     def backward(self, scene_t, cams, frame, grads_out, stream=None, grads=None):
         """dL/d(images) ``grads_out`` (list of dicts, entries may be None) ->
-        dict of parameter gradients (allocated if ``grads`` is None)."""
+        dict of parameter gradients (allocated if ``grads`` is None).
+        ``frame`` is the :class:`Frame` the forward pass filled."""
+        if frame is None:
+            raise ValueError("backward needs the Frame that its forward pass filled")
         sc = abi_scene(scene_t)
         ca = abi.cameras(cams)
         if grads is None:
